@@ -1,0 +1,430 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle (``oracle/qdse_oracle.cpp``) against something other than itself:
+explicit 4x4 Euclidean gamma-matrix traces, the Ward-Takahashi identity, library quadrature rules,
+closed forms (Gaussian moments, Bessel functions, logarithms), exact invariants of the equations
+(chiral limit, rainbow/constant-input identity, homogeneity in D), UV asymptotics and central finite
+differences.  A plausible slip in the oracle (a dropped term, a wrong sign or index, a transposed
+operand, a wrong measure or colour factor) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import oracle as O
+
+KAPPA = (4.0 / 3.0) / (8.0 * math.pi ** 3)
+
+
+# --------------------------------------------------------------------------------------------
+# Explicit Euclidean Dirac algebra (hermitian gamma matrices, {g_mu, g_nu} = 2 delta_mu nu).
+# --------------------------------------------------------------------------------------------
+def _gammas():
+    I2 = np.eye(2); Z2 = np.zeros((2, 2))
+    sig = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]]),
+           np.array([[1, 0], [0, -1]], complex)]
+    g = [np.block([[Z2, -1j * s], [1j * s, Z2]]) for s in sig] + [np.block([[Z2, I2], [I2, Z2]])]
+    return np.array(g)
+
+
+G = _gammas()
+ONE = np.eye(4)
+
+
+def slash(v):
+    return np.einsum("m,mab->ab", v, G)
+
+
+def bc_vertex(p, q, Ap, Bp, Aq, Bq):
+    """Ball-Chiu vertex of Eq. bcvtxmu with the lambda_i of Eq. 2 (reading R4 for lambda_1)."""
+    P, Q = p @ p, q @ q
+    t = p + q
+    l1 = 0.5 * (Ap + Aq)
+    l2 = -1j * (Bp - Bq) / (P - Q)
+    l3 = 0.5 * (Ap - Aq) / (P - Q)
+    return [l1 * G[n] + l2 * t[n] * ONE + l3 * t[n] * slash(t) for n in range(4)]
+
+
+def trace_projections(p, q, Ap, Bp, Aq, Bq, vertex=O.BC):
+    """tr[-i g.p Sigma]/(4P) and tr[Sigma]/4 of the integrand T_mu nu(k) g_mu S(q) Gamma_nu,
+    S(q) = (-i g.q A_q + B_q)/(Q A_q^2 + B_q^2), k = p - q (Eqs. gendse, KernelAnsatz)."""
+    P, Q = p @ p, q @ q
+    k = p - q
+    S = (-1j * slash(q) * Aq + Bq * ONE) / (Q * Aq ** 2 + Bq ** 2)
+    Gam = bc_vertex(p, q, Ap, Bp, Aq, Bq) if vertex == O.BC else list(G)
+    T = np.eye(4) - np.outer(k, k) / (k @ k)
+    Sig = sum(T[m, n] * G[m] @ S @ Gam[n] for m in range(4) for n in range(4))
+    return (np.trace(-1j * slash(p) @ Sig) / (4 * P)).real, (np.trace(Sig) / 4).real
+
+
+def test_gamma_algebra_sanity():
+    for m in range(4):
+        for n in range(4):
+            assert np.allclose(G[m] @ G[n] + G[n] @ G[m], 2 * (m == n) * ONE)
+
+
+@pytest.mark.parametrize("vertex", [O.BC, O.RL])
+def test_point_integrand_equals_gamma_traces(vertex):
+    """P1: the reduced integrand (g_T, g_3, g_0 kernels) equals brute-force Dirac traces."""
+    rng = np.random.default_rng(7)
+    for _ in range(150):
+        p = rng.normal(size=4) * rng.uniform(0.1, 3)
+        q = rng.normal(size=4) * rng.uniform(0.1, 3)
+        Ap, Bp, Aq, Bq = rng.uniform(0.3, 2.5, 4) * np.array([1, rng.choice([-1, 1]), 1, 1])
+        P, Q = p @ p, q @ q
+        z = (p @ q) / math.sqrt(P * Q)
+        DA = (Aq - Ap) / (Q - P)
+        DB = (Bq - Bp) / (Q - P)
+        ia, ib = O.point_integrand(P, Q, z, Ap, Bp, Aq, Bq, DA, DB, vertex)
+        ta, tb = trace_projections(p, q, Ap, Bp, Aq, Bq, vertex)
+        assert ia == pytest.approx(ta, rel=1e-10, abs=1e-12 * (abs(ta) + 1))
+        assert ib == pytest.approx(tb, rel=1e-10, abs=1e-12 * (abs(tb) + 1))
+
+
+def test_bc_vertex_ward_takahashi():
+    """P2: i k.Gamma = S^-1(q) - S^-1(p), k = q - p, for the vertex the traces use."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        p = rng.normal(size=4); q = rng.normal(size=4)
+        Ap, Bp, Aq, Bq = rng.uniform(0.3, 2.5, 4)
+        Gam = bc_vertex(p, q, Ap, Bp, Aq, Bq)
+        kk = q - p
+        lhs = 1j * sum(kk[n] * Gam[n] for n in range(4))
+        rhs = (1j * slash(q) * Aq + Bq * ONE) - (1j * slash(p) * Ap + Bp * ONE)
+        assert np.abs(lhs - rhs).max() < 1e-12
+
+
+# --------------------------------------------------------------------------------------------
+# Quadrature.
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [3, 8, 64, 128, 512])
+def test_gauss_legendre_matches_library_and_is_exact(n):
+    """P3: GL nodes/weights equal numpy's and integrate x^k exactly for k <= 2n-1."""
+    t, v = O.gauss_legendre(n)
+    tr, vr = np.polynomial.legendre.leggauss(n)
+    assert np.abs(t - tr).max() < 1e-14
+    assert np.abs(v - vr).max() < 1e-14 * max(1.0, vr.max())
+    assert v.sum() == pytest.approx(2.0, abs=1e-13)
+    for k in range(0, min(2 * n, 40)):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert np.dot(v, t ** k) == pytest.approx(exact, abs=1e-13)
+
+
+@pytest.mark.parametrize("m", [4, 32, 128])
+def test_gauss_chebyshev_second_kind_exact(m):
+    """P3: int_0^pi sin^2(th) cos^{2j}(th) dth = B(j+1/2, 3/2) for 2j <= 2m-1 (reading R10)."""
+    z, y, w = O.angular_grid(m)
+    assert np.abs(y - (1 - z)).max() < 1e-15
+    assert w.sum() == pytest.approx(math.pi / 2, rel=1e-14)
+    for j in range(0, m):
+        exact = special.beta(j + 0.5, 1.5)
+        assert np.dot(w, z ** (2 * j)) == pytest.approx(exact, rel=1e-12, abs=1e-300)
+
+
+def test_four_dimensional_measure_gaussian():
+    """P3: int d^4q/(2pi)^4 exp(-q^2/w^2) = w^4/(16 pi^2) with the log-mapped GL radial rule and
+    the angular rule, i.e. (1/8pi^3) sum_j W_j sum_k w_k f.  The grid starts at s_min, so the
+    closed form is w^4/(16 pi^2) e^{-a}(1 + a), a = s_min/w^2."""
+    for w in (0.4, 0.5, 0.678):
+        sp, sq, W, _ = O.radial_grid(128)
+        z, y, wk = O.angular_grid(32)
+        val = (W * np.exp(-sq / w ** 2)).sum() * wk.sum() / (8 * math.pi ** 3)
+        a = 1e-4 / w ** 2
+        assert val == pytest.approx(w ** 4 / (16 * math.pi ** 2) * math.exp(-a) * (1 + a),
+                                    rel=1e-11)
+
+
+def test_condensate_closed_form():
+    """Condensate measure: for A = 1, B = b, N_c/(4pi^2) int ds s b/(s + b^2) has the closed form
+    N_c/(4pi^2) b [s - b^2 ln(s + b^2)] between the grid ends."""
+    n, b = 256, 0.37
+    pr = O.Problem(n=n, s_min=1e-4, s_max=10.0)
+    val = O.condensate(pr, np.ones(n), np.full(n, b))
+    F = lambda s: b * (s - b * b * math.log(s + b * b))
+    exact = 3.0 / (4 * math.pi ** 2) * (F(10.0) - F(1e-4))
+    assert val == pytest.approx(exact, rel=1e-10)
+
+
+# --------------------------------------------------------------------------------------------
+# Angular kernels.
+# --------------------------------------------------------------------------------------------
+def test_scalar_kernel_is_bessel_closed_form():
+    """P4: with the bare vertex and A = 1, B = b, one sweep gives
+    B_i = m + C_F/(8pi^3) sum_j W_j 3b/(Q_j + b^2) (8pi^2 D/w^4) pi I_1(c)/c e^{-(P+Q)/w^2},
+    c = 2 sqrt(PQ)/w^2: the angular integral of the Gaussian in closed form."""
+    n, nt, D, w, m, b = 24, 96, 0.93, 0.5, 0.005, 0.4
+    pr = O.Problem(n=n, n_theta=nt, s_min=1e-4, s_max=4.0, vertex=O.RL, D=D, omega=w, m=m)
+    sp, sq, W, _ = O.radial_grid(n, 1e-4, 4.0)
+    Ao, Bo = O.sweep(pr, np.ones(n), np.full(n, b))
+    P = sp[:, None]; Q = sq[None, :]
+    c = 2 * np.sqrt(P * Q) / w ** 2
+    ang = math.pi * special.ive(1, c) / c * np.exp(-(np.sqrt(P) - np.sqrt(Q)) ** 2 / w ** 2)
+    expect = m + KAPPA * (8 * math.pi ** 2 * D / w ** 4) * (ang * (W * 3 * b / (sq + b * b))).sum(1)
+    assert np.abs(Bo - expect).max() / np.abs(expect).max() < 1e-12
+
+
+def test_kernels_symmetric_in_p_q():
+    """P4: the angular kernels are symmetric, K(P_i, Q_j) = K(Q_j, P_i).  They are read off the
+    oracle's complex-step Jacobian of the bare-vertex sweep at A = 1, B = b:
+      dF^B_i/dB_j = C_F/(8pi^3) W_j 3 (Q_j - b^2)/(Q_j + b^2)^2 K0_ij
+      dF^A_i/dA_j = C_F/(8pi^3) W_j (b^2 - Q_j)/(Q_j + b^2)^2 K3_ij / P_i."""
+    n, b = 20, 0.3
+    pr = O.Problem(n=n, n_theta=24, s_min=1e-2, s_max=10.0, vertex=O.RL)
+    sp, sq, W, _ = O.radial_grid(n, 1e-2, 10.0)
+    J = O.jacobian(pr, np.ones(n), np.full(n, b))
+    d = sq + b * b
+    K0 = J[n:, n:] / (KAPPA * W * 3 * (sq - b * b) / d ** 2)[None, :]
+    K3 = J[:n, :n] * sp[:, None] / (KAPPA * W * (b * b - sq) / d ** 2)[None, :]
+    for K in (K0, K3):
+        off = ~np.eye(n, dtype=bool)
+        scale = np.abs(K).max()
+        assert np.abs((K - K.T)[off]).max() < 1e-11 * scale
+
+
+# --------------------------------------------------------------------------------------------
+# Invariants of the equations.
+# --------------------------------------------------------------------------------------------
+def test_chiral_limit_wigner_solution():
+    """P5: with m = 0 and B_0 = 0, B stays exactly zero on every sweep; A converges (Wigner)."""
+    pr = O.Problem(n=32, n_theta=16, m=0.0, D=0.55, omega=0.678)
+    A = np.ones(32); B = np.zeros(32)
+    for _ in range(5):
+        A, B = O.sweep(pr, A, B)
+        assert np.all(B == 0.0)
+    A, B, it, ch, st = O.solve(pr, A0=1.0, B0=0.0, tol=1e-12)
+    assert st == 0 and np.all(B == 0.0) and np.all(np.isfinite(A))
+
+
+@pytest.mark.parametrize("mode", [O.COLLOCATED, O.STAGGERED])
+def test_rainbow_constant_input_identity(mode):
+    """P6: on A = a, B = b (Delta = 0, Sigma_A = a) one BC sweep satisfies
+    F_BC(x) - x0 = a (F_RL(x) - x0), x0 = (1, m); at a = 1 the two sweeps coincide."""
+    n = 24
+    for a, b in ((1.7, 0.45), (1.0, 0.3)):
+        bc = O.Problem(n=n, n_theta=16, grid_mode=mode, vertex=O.BC)
+        rl = O.Problem(n=n, n_theta=16, grid_mode=mode, vertex=O.RL)
+        Ab, Bb = O.sweep(bc, np.full(n, a), np.full(n, b))
+        Ar, Br = O.sweep(rl, np.full(n, a), np.full(n, b))
+        assert np.abs((Ab - 1) - a * (Ar - 1)).max() < 1e-13 * np.abs(Ab - 1).max() + 1e-15
+        assert np.abs((Bb - bc.m) - a * (Br - rl.m)).max() < 1e-13 * np.abs(Bb).max()
+
+
+def test_homogeneity_in_D_and_linearity_in_m():
+    """dF/dD = (F - x0)/D exactly (D is an overall factor of the interaction) and dF/dm = e_B."""
+    n = 16
+    pr = O.Problem(n=n, n_theta=12, D=0.55, omega=0.678)
+    rng = np.random.default_rng(0)
+    A = 1 + rng.uniform(0, 1, n); B = rng.uniform(0.05, 0.6, n)
+    Fa, Fb = O.sweep(pr, A, B)
+    dF = O.param_jacobian(pr, A, B)
+    np.testing.assert_allclose(dF[0, :n], 0.0, atol=1e-15)
+    np.testing.assert_allclose(dF[0, n:], 1.0, rtol=1e-15)
+    # F - x0 is formed after rounding F, so compare on the scale of the largest entry
+    sa = np.abs(Fa - 1).max(); sb = np.abs(Fb - pr.m).max()
+    np.testing.assert_allclose(dF[1, :n], (Fa - 1) / pr.D, rtol=1e-12, atol=1e-14 * sa)
+    np.testing.assert_allclose(dF[1, n:], (Fb - pr.m) / pr.D, rtol=1e-12, atol=1e-14 * sb)
+
+
+def test_uv_asymptotics_fix_normalisation():
+    """P7: for P >> w^2 and A = 1, B = m: P (A - 1) -> D and P (B - m)/m -> 2D, from
+    int d^4k/(2pi)^4 8pi^2 D/w^4 e^{-k^2/w^2} = D/2, C_F = 4/3 and the angular averages
+    <g_3> = 3P/2, <3> = 3.  Without C_F the limits would be 3D/4 and 3D/2."""
+    n, D, w, m = 160, 0.93, 0.5, 0.01
+    pr = O.Problem(n=n, n_theta=400, s_min=20.0, s_max=900.0, D=D, omega=w, m=m)
+    sp, _, _, _ = O.radial_grid(n, 20.0, 900.0)
+    Ao, Bo = O.sweep(pr, np.ones(n), np.full(n, m))
+    sel = (sp > 100) & (sp < 300)
+    ra = sp[sel] * (Ao[sel] - 1) / D
+    rb = sp[sel] * (Bo[sel] - m) / (2 * D * m)
+    # corrections are O(w^2/P) ~ 0.2-0.5 % here; a wrong colour factor or measure is >= 25 % off
+    assert np.all(np.abs(ra - 1) < 0.02), ra
+    assert np.all(np.abs(rb - 1) < 0.02), rb
+
+
+def test_removable_limit_stencil_is_second_order():
+    """P8: the diagonal quotient (reading R8) tends to A'(P) for A(s) = 1 + 1/(1+s) with O(h^2)
+    error in u = ln s, interior and one-sided ends alike."""
+    errs = []
+    for n in (32, 64, 128):
+        sp, _, _, _ = O.radial_grid(n, 1e-2, 1e2)
+        F = 1 + 1 / (1 + sp)
+        exact = -1 / (1 + sp) ** 2
+        e = max(abs(O.diag_quotient(sp, F, i) - exact[i]) / abs(exact[i]) for i in range(n))
+        errs.append(e)
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+    # the difference quotient off the diagonal approaches the same limit
+    sp, _, _, _ = O.radial_grid(64, 1e-2, 1e2)
+    Af = lambda s: 1 + 1 / (1 + s)
+    P = sp[30]
+    for eps in (1e-3, 1e-5):
+        dq = (Af(P * (1 + eps)) - Af(P)) / (P * eps)
+        assert dq == pytest.approx(-1 / (1 + P) ** 2, rel=3 * eps)
+
+
+def test_staggered_grid_interleaving_and_interpolation():
+    """Eqs. pqrelationship / chazhiresult: p_1 < q_1 < p_2 < ... < p_N < q_N, the traditional
+    bracket search returns j for q_j, and the modified interpolation reproduces any F linear in
+    |p| exactly, with F(q_N) = F(p_N)."""
+    n = 40
+    sp, sq, W, br = O.radial_grid(n, 1e-4, 1e4, O.STAGGERED)
+    inter = np.empty(2 * n); inter[0::2] = sp; inter[1::2] = sq
+    assert np.all(np.diff(inter) > 0)
+    assert sp[0] == pytest.approx(1e-4, rel=1e-14)
+    assert np.array_equal(br, np.arange(n))
+    F = 0.3 + 1.7 * np.sqrt(sp)
+    Fq = O.values_at_q(F, 1e-4, 1e4, O.STAGGERED)
+    np.testing.assert_allclose(Fq[:-1], 0.3 + 1.7 * np.sqrt(sq[:-1]), rtol=1e-13)
+    assert Fq[-1] == F[-1]
+    spc, sqc, Wc, _ = O.radial_grid(n, 1e-4, 1e4, O.COLLOCATED)
+    np.testing.assert_array_equal(spc, sqc)
+    np.testing.assert_array_equal(O.values_at_q(F, 1e-4, 1e4, O.COLLOCATED), F)
+
+
+# --------------------------------------------------------------------------------------------
+# Brute force on tiny inputs: the whole sweep from gamma-matrix traces.
+# --------------------------------------------------------------------------------------------
+def _brute_force_sweep(n, nt, s_min, s_max, mode, D, w, m, A, B):
+    """One sweep with every ingredient rebuilt independently: numpy GL nodes, the Chebyshev rule
+    from its definition, quadratic fits for the diagonal, and Dirac traces in explicit momenta."""
+    t, v = np.polynomial.legendre.leggauss(n)
+    u0, u1 = math.log(s_min), math.log(s_max)
+    uq = 0.5 * (u1 + u0) + 0.5 * (u1 - u0) * t
+    sq = np.exp(uq)
+    W = 0.5 * (u1 - u0) * v * sq ** 2
+    if mode == O.COLLOCATED:
+        sp = sq.copy(); up = uq.copy()
+    else:
+        up = np.concatenate([[u0], 0.5 * (uq[:-1] + uq[1:])]); sp = np.exp(up)
+    th = np.arange(1, nt + 1) * math.pi / (nt + 1)
+    zk, wk = np.cos(th), math.pi / (nt + 1) * np.sin(th) ** 2
+
+    def at_q(F, j):
+        if mode == O.COLLOCATED:
+            return F[j]
+        if j == n - 1:
+            return F[n - 1]
+        a, b = math.sqrt(sp[j]), math.sqrt(sp[j + 1])
+        return F[j] + (math.sqrt(sq[j]) - a) * (F[j + 1] - F[j]) / (b - a)
+
+    def dds(F, i):
+        a = min(max(i - 1, 0), n - 3)
+        c = np.polyfit(up[a:a + 3], F[a:a + 3], 2)
+        return (2 * c[0] * up[i] + c[1]) / sp[i]
+
+    Ao = np.zeros(n); Bo = np.zeros(n)
+    for i in range(n):
+        SA = SB = 0.0
+        for j in range(n):
+            Aq, Bq = at_q(A, j), at_q(B, j)
+            for k in range(nt):
+                p = np.array([0, 0, 0, math.sqrt(sp[i])])
+                q = math.sqrt(sq[j]) * np.array([0, 0, math.sqrt(1 - zk[k] ** 2), zk[k]])
+                kk = p - q
+                Dk = 8 * math.pi ** 2 * D / w ** 4 * math.exp(-(kk @ kk) / w ** 2)
+                if sp[i] == sq[j]:
+                    # removable limit: evaluate the BC vertex with the derivative quotients
+                    dA, dB = dds(A, i), dds(B, i)
+                    P, Q = sp[i], sq[j]
+                    S = (-1j * slash(q) * Aq + Bq * ONE) / (Q * Aq ** 2 + Bq ** 2)
+                    tt = p + q
+                    Gam = [0.5 * (A[i] + Aq) * G[nn] + 0.5 * tt[nn] * slash(tt) * dA
+                           - 1j * tt[nn] * dB * ONE for nn in range(4)]
+                    T = np.eye(4) - np.outer(kk, kk) / (kk @ kk)
+                    Sig = sum(T[a, b] * G[a] @ S @ Gam[b] for a in range(4) for b in range(4))
+                    ia = (np.trace(-1j * slash(p) @ Sig) / (4 * P)).real
+                    ib = (np.trace(Sig) / 4).real
+                else:
+                    ia, ib = trace_projections(p, q, A[i], B[i], Aq, Bq)
+                SA += W[j] * wk[k] * Dk * ia
+                SB += W[j] * wk[k] * Dk * ib
+        Ao[i] = 1 + KAPPA * SA
+        Bo[i] = m + KAPPA * SB
+    return Ao, Bo
+
+
+@pytest.mark.parametrize("mode", [O.COLLOCATED, O.STAGGERED])
+def test_sweep_matches_brute_force_traces(mode):
+    n, nt = 5, 4
+    rng = np.random.default_rng(11)
+    A = 1 + rng.uniform(0, 1.5, n); B = rng.uniform(0.05, 0.8, n)
+    pr = O.Problem(n=n, n_theta=nt, s_min=1e-2, s_max=5.0, grid_mode=mode, D=0.93, omega=0.5,
+                   m=0.005)
+    Ao, Bo = O.sweep(pr, A, B)
+    Ar, Br = _brute_force_sweep(n, nt, 1e-2, 5.0, mode, 0.93, 0.5, 0.005, A, B)
+    np.testing.assert_allclose(Ao, Ar, rtol=1e-11)
+    np.testing.assert_allclose(Bo, Br, rtol=1e-11)
+
+
+# --------------------------------------------------------------------------------------------
+# Derivatives: Jacobian and adjoint.
+# --------------------------------------------------------------------------------------------
+def test_complex_step_jacobian_matches_central_differences():
+    """P10: J e_c = Im F(x + i h e_c)/h against central differences of the real sweep."""
+    n = 12
+    pr = O.Problem(n=n, n_theta=10, s_min=1e-3, s_max=1e3)
+    rng = np.random.default_rng(5)
+    A = 1 + rng.uniform(0, 1, n); B = rng.uniform(0.05, 0.6, n)
+    J = O.jacobian(pr, A, B)
+    x = np.concatenate([A, B]); h = 1e-6
+    for c in range(2 * n):
+        xp = x.copy(); xp[c] += h; xm = x.copy(); xm[c] -= h
+        fd = (np.concatenate(O.sweep(pr, xp[:n], xp[n:]))
+              - np.concatenate(O.sweep(pr, xm[:n], xm[n:]))) / (2 * h)
+        assert np.abs(J[:, c] - fd).max() < 1e-7 * (np.abs(fd).max() + 1e-3)
+    dF = O.param_jacobian(pr, A, B)
+    hw = 1e-6
+    Fp = np.concatenate(O.sweep(O.Problem(**{**pr.__dict__, "omega": pr.omega + hw}), A, B))
+    Fm = np.concatenate(O.sweep(O.Problem(**{**pr.__dict__, "omega": pr.omega - hw}), A, B))
+    np.testing.assert_allclose(dF[2], (Fp - Fm) / (2 * hw), rtol=1e-6, atol=1e-9)
+
+
+def test_adjoint_matches_finite_differences_of_solve():
+    """Implicit-function adjoint: dL/d(m, D, omega) for L = gA.A + gB.B at the converged solution
+    against central differences (h = 1e-5) of solves converged to 1e-14."""
+    n = 16
+    base = dict(n=n, n_theta=16, s_min=1e-4, s_max=1e4, D=0.55, omega=0.678, m=0.02)
+    pr = O.Problem(**base)
+    A, B, it, ch, st = O.solve(pr, tol=1e-14, max_iter=5000)
+    assert st == 0
+    rng = np.random.default_rng(2)
+    gA = rng.normal(size=n); gB = rng.normal(size=n)
+    gp, lam = O.adjoint(pr, A, B, gA, gB)
+    h = 1e-5
+    for t, key in enumerate(("m", "D", "omega")):
+        Lp = Lm = None
+        for sgn in (1, -1):
+            prh = O.Problem(**{**base, key: base[key] + sgn * h})
+            Ah, Bh, _, _, sth = O.solve(prh, A0=A, B0=B, tol=1e-14, max_iter=5000)
+            assert sth == 0
+            L = gA @ Ah + gB @ Bh
+            if sgn == 1:
+                Lp = L
+            else:
+                Lm = L
+        fd = (Lp - Lm) / (2 * h)
+        assert gp[t] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    assert gp[3] == 0.0
+
+
+# --------------------------------------------------------------------------------------------
+# Solution-level checks (parity of later stages is against these).
+# --------------------------------------------------------------------------------------------
+def test_paper_parameters_give_physical_solution():
+    """Sec. IV parameters (D = 0.55, w = 0.678): the Nambu solution, A(0) > 1, M(0) ~ 0.3 GeV
+    (values themselves are not printed in the paper: sanity range only)."""
+    pr = O.Problem(D=0.55, omega=0.678)
+    A, B, it, ch, st = O.solve(pr, tol=1e-10)
+    assert st == 0 and it < 200
+    assert A[0] > 1.0 and 0.2 < B[0] / A[0] < 0.6
+    assert np.all(np.diff(B / A) < 1e-12)  # M(p^2) decreases monotonically
+
+
+def test_solution_is_a_fixed_point():
+    pr = O.Problem()  # 64 x 32, D = 0.93, w = 0.5, m = 5 MeV
+    A, B, it, ch, st = O.solve(pr, tol=1e-12, max_iter=5000, nthreads=O.max_threads())
+    assert st == 0
+    Fa, Fb = O.sweep(pr, A, B)
+    assert np.abs(Fa - A).max() < 1e-11 * np.abs(A).max()
+    assert np.abs(Fb - B).max() < 1e-11 * np.abs(B).max()
