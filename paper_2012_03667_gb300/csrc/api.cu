@@ -1,0 +1,660 @@
+// api.cu -- the C interface of libqdse (declared in include/qdse.h): argument checking, context
+// set-up, and the host drivers of the batched successive approximation (Eqs. jifen14-jifen122),
+// its mixed-precision refinement and the implicit adjoint.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qdse_internal.h"
+
+using namespace qdse;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+qdse_status fail(qdse_ctx* c, qdse_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+qdse_status cuda_fail(qdse_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? QDSE_ERR_OOM : QDSE_ERR_CUDA, m);
+}
+
+#define QCHECK(c, expr, where)                                  \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return cuda_fail((c), _e, where); \
+    } while (0)
+
+bool finite(double x) { return std::isfinite(x); }
+
+qdse_status check_options(const qdse_options* o, std::string& why) {
+    if (!o) { why = "options: null pointer"; return QDSE_ERR_ARG; }
+    if (o->precision < QDSE_FP64 || o->precision > QDSE_FP32) { why = "options.precision out of range"; return QDSE_ERR_ARG; }
+    if (o->vertex != QDSE_VERTEX_BC && o->vertex != QDSE_VERTEX_RL) { why = "options.vertex out of range"; return QDSE_ERR_ARG; }
+    if (!finite(o->cf) || o->cf <= 0) { why = "options.cf must be finite and > 0"; return QDSE_ERR_ARG; }
+    if (!finite(o->tol) || o->tol < 0) { why = "options.tol must be finite and >= 0"; return QDSE_ERR_ARG; }
+    if (!finite(o->alpha) || o->alpha <= 0 || o->alpha > 1) { why = "options.alpha must be in (0, 1]"; return QDSE_ERR_ARG; }
+    if (o->max_iter < 1) { why = "options.max_iter must be >= 1"; return QDSE_ERR_ARG; }
+    if (std::isnan(o->time_limit)) { why = "options.time_limit is NaN"; return QDSE_ERR_ARG; }
+    return QDSE_OK;
+}
+
+qdse_status check_grid(const qdse_grid& g, std::string& why) {
+    if (g.n_p < 3 || g.n_p > kMaxN) { why = "grid.n_p must be in [3, 1024]"; return QDSE_ERR_ARG; }
+    if (g.n_theta < 1 || g.n_theta > kMaxTheta) { why = "grid.n_theta must be in [1, 512]"; return QDSE_ERR_ARG; }
+    if (!finite(g.s_min) || !finite(g.s_max) || g.s_min <= 0 || g.s_max <= g.s_min) {
+        why = "grid: need 0 < s_min < s_max, both finite";
+        return QDSE_ERR_ARG;
+    }
+    if (g.grid_mode != QDSE_COLLOCATED && g.grid_mode != QDSE_STAGGERED) { why = "grid.grid_mode out of range"; return QDSE_ERR_ARG; }
+    return QDSE_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
+}
+
+void free_ctx(qdse_ctx* c) {
+    if (!c) return;
+    void* ptrs[] = {c->d_inst, c->d_state, c->d_ctl, c->grid.sp, c->grid.sq, c->grid.W,
+                    c->grid.rsp, c->grid.rsq, c->grid.wt, c->grid.stc, c->grid.sta,
+                    c->grid.sp32, c->grid.sq32, c->grid.z, c->grid.y, c->grid.s2, c->grid.wz,
+                    c->grid.row_inst, c->work.xn64, c->work.r64, c->work.d64, c->work.vec64,
+                    c->work.dia64, c->work.x32, c->work.xn32, c->work.vec32, c->work.dia32,
+                    c->work.dvec32, c->work.ddia32, c->work.d32, c->work.dvec64, c->work.ddia64,
+                    c->work.lam, c->work.lamn, c->d_Khi, c->d_Klo, c->d_Kwhi, c->d_Kwlo,
+                    c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_count) cudaFreeHost(c->h_count);
+    if (c->h_inst_pinned) cudaFreeHost(c->h_inst_pinned);
+    delete c;
+}
+
+// Upload per-instance parameters; reports whether the kernels must be rebuilt.
+qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
+    if (!p) return fail(c, QDSE_ERR_ARG, "params: null pointer");
+    rebuild = !(c->opt.reuse_kernels && c->k_valid_for);
+    for (int b = 0; b < c->n_inst; ++b) {
+        const qdse_params& q = p[b];
+        if (!finite(q.D) || q.D < 0 || !finite(q.omega) || q.omega <= 0 || !finite(q.m) ||
+            !finite(q.mu)) {
+            return fail(c, QDSE_ERR_ARG, "params[" + std::to_string(b) +
+                                             "]: need finite D >= 0, omega > 0, m, mu");
+        }
+        if (q.mu != 0.0)
+            return fail(c, QDSE_ERR_UNSUPPORTED, "params[" + std::to_string(b) +
+                                                     "]: the vacuum solver needs mu = 0");
+        if (c->k_omega[b] != q.omega) rebuild = true;
+    }
+    for (int b = 0; b < c->n_inst; ++b) {
+        const HostInst& h = c->hinst[b];
+        DevInst& d = c->h_inst_pinned[b];
+        d.n = h.g.n_p;
+        d.nt = h.g.n_theta;
+        d.x_off = h.x_off;
+        d.t_off = h.t_off;
+        d.k_off = h.k_off;
+        d.ld = h.ld;
+        d.mode = h.g.grid_mode;
+        d.D = p[b].D;
+        d.omega = p[b].omega;
+        d.m = p[b].m;
+    }
+    QCHECK(c, cudaMemcpyAsync(c->d_inst, c->h_inst_pinned, sizeof(DevInst) * c->n_inst,
+                              cudaMemcpyHostToDevice, c->stream),
+           "upload parameters");
+    return QDSE_OK;
+}
+
+qdse_status ensure_kernels(qdse_ctx* c, const qdse_params* p, bool rebuild) {
+    if (!rebuild) return QDSE_OK;
+    QCHECK(c, launch_precompute(c, false), "precompute kernels");
+    for (int b = 0; b < c->n_inst; ++b) c->k_omega[b] = p[b].omega;
+    c->k_valid_for = 1;
+    c->kw_valid = 0;
+    return QDSE_OK;
+}
+
+Ctl make_ctl(const qdse_ctx* c) {
+    Ctl t{};
+    t.kappa = c->opt.cf / (8.0 * kPi * kPi * kPi);
+    t.tol = c->opt.tol;
+    t.sw_tol = std::fmax(1e-5, c->opt.tol);
+    t.inner_tol = 1e-3;
+    t.alpha = c->opt.alpha;
+    t.max_iter = c->opt.max_iter;
+    t.max_inner = 400;
+    t.max_fp32 = c->opt.max_iter;
+    t.vertex = c->opt.vertex;
+    t.precision = c->opt.precision;
+    t.final_phase = (c->opt.precision == QDSE_FP32) ? PH_PICARD32 : PH_PICARD64;
+    t.never_converge = 0;
+    return t;
+}
+
+void reset_stats(qdse_ctx* c) {
+    c->launches = 0;
+    c->sweeps32 = 0;
+    c->sweeps64 = 0;
+    c->polls = 0;
+}
+
+// The batched successive approximation: ticks of (sweep rows, update instances) with the number
+// of unfinished instances polled every `chunk` ticks.  n_ticks < 0 means "until every instance
+// has finished"; otherwise exactly n_ticks ticks without polling.
+qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool& timed_out) {
+    timed_out = false;
+    const bool otf = (c->opt.precision == QDSE_FP64);
+    const auto t0 = std::chrono::steady_clock::now();
+    long long done_ticks = 0;
+    int chunk = 4;
+    while (true) {
+        const long long todo = (n_ticks >= 0) ? n_ticks - done_ticks : chunk;
+        if (n_ticks >= 0 && todo <= 0) break;
+        for (long long t = 0; t < todo; ++t) {
+            if (otf) {
+                QCHECK(c, launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1),
+                       "fp64 sweep");
+            } else {
+                QCHECK(c, launch_tick(c, A, B), "sweep");
+            }
+            if (t == todo - 1)
+                QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
+            QCHECK(c, launch_update(c, A, B), "update");
+        }
+        done_ticks += todo;
+        if (n_ticks >= 0) break;
+        QCHECK(c, cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost,
+                                  c->stream),
+               "poll");
+        QCHECK(c, cudaStreamSynchronize(c->stream), "poll sync");
+        c->polls++;
+        if (*c->h_count == 0) break;
+        if (c->opt.time_limit > 0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > c->opt.time_limit) {
+                timed_out = true;
+                break;
+            }
+        }
+        if (chunk < 64) chunk *= 2;
+    }
+    return QDSE_OK;
+}
+
+qdse_status check_ptr(qdse_ctx* c, const void* p, const char* name) {
+    if (!p) return fail(c, QDSE_ERR_ARG, std::string(name) + ": null pointer");
+    return QDSE_OK;
+}
+
+qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_options* o,
+                        qdse_ctx** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, QDSE_ERR_ARG, "out: null pointer");
+    *out = nullptr;
+    if (!g) return fail(nullptr, QDSE_ERR_ARG, "grid: null pointer");
+    if (n_inst < 1) return fail(nullptr, QDSE_ERR_ARG, "n_inst must be >= 1");
+    std::string why;
+    if (check_options(o, why) != QDSE_OK) return fail(nullptr, QDSE_ERR_ARG, why);
+    for (int b = 0; b < (ragged ? n_inst : 1); ++b)
+        if (check_grid(g[b], why) != QDSE_OK)
+            return fail(nullptr, QDSE_ERR_ARG, "instance " + std::to_string(b) + ": " + why);
+
+    qdse_ctx* c = new (std::nothrow) qdse_ctx();
+    if (!c) return fail(nullptr, QDSE_ERR_OOM, "host allocation");
+    c->opt = *o;
+    c->stream = (cudaStream_t)o->stream;
+    c->n_inst = n_inst;
+    c->hinst.resize(n_inst);
+    c->k_omega.assign(n_inst, NAN);
+    std::map<int, int> t_of;  // angular node count -> offset of its shared table
+    long long k = 0;
+    int x = 0, t = 0;
+    for (int b = 0; b < n_inst; ++b) {
+        HostInst& h = c->hinst[b];
+        h.g = ragged ? g[b] : g[0];
+        h.x_off = x;
+        h.ld = (h.g.n_p + 3) & ~3;
+        h.k_off = k;
+        x += h.g.n_p;
+        k += 3LL * h.g.n_p * h.ld;
+        if (!t_of.count(h.g.n_theta)) {
+            t_of[h.g.n_theta] = t;
+            t += h.g.n_theta;
+        }
+        h.t_off = t_of[h.g.n_theta];
+        if (h.g.n_p > c->max_n) c->max_n = h.g.n_p;
+        if (h.g.n_theta > c->max_nt) c->max_nt = h.g.n_theta;
+        if (h.g.grid_mode == QDSE_STAGGERED) c->any_staggered = true;
+    }
+    c->n_total = x;
+    c->t_total = t;
+    c->k_total = k;
+
+    // host grids
+    const int N = c->n_total;
+    std::vector<double> sp(N), sq(N), W(N), wt(N), stc(3 * (size_t)N), rsp(N), rsq(N);
+    std::vector<int> sta(N), row_inst(N);
+    std::vector<float> sp32(N), sq32(N);
+    for (int b = 0; b < n_inst; ++b) {
+        const HostInst& h = c->hinst[b];
+        const int o0 = h.x_off;
+        build_instance_grid(h.g, &sp[o0], &sq[o0], &W[o0], &wt[o0], &stc[3 * (size_t)o0],
+                            &sta[o0]);
+        for (int j = 0; j < h.g.n_p; ++j) row_inst[o0 + j] = b;
+    }
+    for (int j = 0; j < N; ++j) {
+        rsp[j] = std::sqrt(sp[j]);
+        rsq[j] = std::sqrt(sq[j]);
+        sp32[j] = (float)sp[j];
+        sq32[j] = (float)sq[j];
+    }
+    std::vector<double> z(t), y(t), s2(t), wz(t);
+    for (auto& kv : t_of) build_angular(kv.first, &z[kv.second], &y[kv.second], &s2[kv.second], &wz[kv.second]);
+    c->h_sp = sp;
+    c->h_sq = sq;
+    c->h_W = W;
+
+#define CALLOC(ptr, n)                                                      \
+    do {                                                                    \
+        cudaError_t _e = dalloc(&(ptr), (n));                               \
+        if (_e != cudaSuccess) {                                            \
+            qdse_status _s = cuda_fail(nullptr, _e, "allocate " #ptr);      \
+            free_ctx(c);                                                    \
+            return _s;                                                      \
+        }                                                                   \
+    } while (0)
+    CALLOC(c->d_inst, n_inst);
+    CALLOC(c->d_state, n_inst);
+    CALLOC(c->d_ctl, 1);
+    CALLOC(c->grid.sp, N);
+    CALLOC(c->grid.sq, N);
+    CALLOC(c->grid.W, N);
+    CALLOC(c->grid.rsp, N);
+    CALLOC(c->grid.rsq, N);
+    CALLOC(c->grid.wt, N);
+    CALLOC(c->grid.stc, 3 * (size_t)N);
+    CALLOC(c->grid.sta, N);
+    CALLOC(c->grid.sp32, N);
+    CALLOC(c->grid.sq32, N);
+    CALLOC(c->grid.z, t);
+    CALLOC(c->grid.y, t);
+    CALLOC(c->grid.s2, t);
+    CALLOC(c->grid.wz, t);
+    CALLOC(c->grid.row_inst, N);
+    CALLOC(c->work.xn64, 2 * (size_t)N);
+    CALLOC(c->work.r64, 2 * (size_t)N);
+    CALLOC(c->work.d64, 2 * (size_t)N);
+    CALLOC(c->work.vec64, 5 * (size_t)N);
+    CALLOC(c->work.dia64, 2 * (size_t)N);
+    CALLOC(c->work.x32, 2 * (size_t)N);
+    CALLOC(c->work.xn32, 2 * (size_t)N);
+    CALLOC(c->work.vec32, 5 * (size_t)N);
+    CALLOC(c->work.dia32, 2 * (size_t)N);
+    CALLOC(c->work.dvec32, 5 * (size_t)N);
+    CALLOC(c->work.ddia32, 2 * (size_t)N);
+    CALLOC(c->work.d32, 2 * (size_t)N);
+    CALLOC(c->work.dvec64, 5 * (size_t)N);
+    CALLOC(c->work.ddia64, 2 * (size_t)N);
+    CALLOC(c->work.lam, 2 * (size_t)N);
+    CALLOC(c->work.lamn, 2 * (size_t)N);
+    CALLOC(c->d_Khi, (size_t)k);
+    CALLOC(c->d_Klo, (size_t)k);
+    CALLOC(c->d_count, 1);
+    CALLOC(c->d_sweeps, 2);
+    CALLOC(c->d_hostA, 2 * (size_t)N);
+    CALLOC(c->d_hostI, 2 * (size_t)n_inst);
+#undef CALLOC
+    cudaError_t e = cudaMallocHost((void**)&c->h_count, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_inst_pinned, sizeof(DevInst) * n_inst);
+    if (e != cudaSuccess) {
+        qdse_status s = cuda_fail(nullptr, e, "pinned host allocation");
+        free_ctx(c);
+        return s;
+    }
+    struct Up { void* d; const void* h; size_t bytes; } ups[] = {
+        {c->grid.sp, sp.data(), sizeof(double) * N}, {c->grid.sq, sq.data(), sizeof(double) * N},
+        {c->grid.W, W.data(), sizeof(double) * N}, {c->grid.rsp, rsp.data(), sizeof(double) * N},
+        {c->grid.rsq, rsq.data(), sizeof(double) * N}, {c->grid.wt, wt.data(), sizeof(double) * N},
+        {c->grid.stc, stc.data(), sizeof(double) * 3 * (size_t)N},
+        {c->grid.sta, sta.data(), sizeof(int) * N}, {c->grid.sp32, sp32.data(), sizeof(float) * N},
+        {c->grid.sq32, sq32.data(), sizeof(float) * N}, {c->grid.z, z.data(), sizeof(double) * t},
+        {c->grid.y, y.data(), sizeof(double) * t}, {c->grid.s2, s2.data(), sizeof(double) * t},
+        {c->grid.wz, wz.data(), sizeof(double) * t},
+        {c->grid.row_inst, row_inst.data(), sizeof(int) * N}};
+    for (auto& u : ups) {
+        e = cudaMemcpy(u.d, u.h, u.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            qdse_status s = cuda_fail(nullptr, e, "upload grid");
+            free_ctx(c);
+            return s;
+        }
+    }
+    *out = c;
+    return QDSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qdse_options qdse_default_options(void) {
+    qdse_options o;
+    o.precision = QDSE_MIXED;
+    o.vertex = QDSE_VERTEX_BC;
+    o.cf = 4.0 / 3.0;
+    o.tol = 1e-10;
+    o.alpha = 1.0;
+    o.max_iter = 20000;
+    o.time_limit = 0.0;
+    o.reuse_kernels = 0;
+    o.stream = nullptr;
+    return o;
+}
+
+qdse_status qdse_create(const qdse_grid* g, int n_inst, const qdse_options* o, qdse_ctx** out) {
+    try {
+        return create_impl(g, n_inst, false, o, out);
+    } catch (...) {
+        return fail(nullptr, QDSE_ERR_OOM, "host exception during create");
+    }
+}
+
+qdse_status qdse_create_ragged(const qdse_grid* g, int n_inst, const qdse_options* o,
+                               qdse_ctx** out) {
+    try {
+        return create_impl(g, n_inst, true, o, out);
+    } catch (...) {
+        return fail(nullptr, QDSE_ERR_OOM, "host exception during create");
+    }
+}
+
+void qdse_destroy(qdse_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+const char* qdse_last_error(const qdse_ctx* c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+qdse_status qdse_sizes(const qdse_ctx* c, int* n_inst, int* n_total) {
+    if (!c) return QDSE_ERR_ARG;
+    if (n_inst) *n_inst = c->n_inst;
+    if (n_total) *n_total = c->n_total;
+    return QDSE_OK;
+}
+
+qdse_status qdse_layout(const qdse_ctx* c, int* x_off) {
+    if (!c || !x_off) return QDSE_ERR_ARG;
+    for (int b = 0; b < c->n_inst; ++b) x_off[b] = c->hinst[b].x_off;
+    x_off[c->n_inst] = c->n_total;
+    return QDSE_OK;
+}
+
+qdse_status qdse_grid_nodes(const qdse_ctx* c, double* s_p, double* s_q, double* W) {
+    if (!c) return QDSE_ERR_ARG;
+    const size_t bytes = sizeof(double) * c->n_total;
+    if (s_p) std::memcpy(s_p, c->h_sp.data(), bytes);
+    if (s_q) std::memcpy(s_q, c->h_sq.data(), bytes);
+    if (W) std::memcpy(W, c->h_W.data(), bytes);
+    return QDSE_OK;
+}
+
+qdse_status qdse_set_options(qdse_ctx* c, const qdse_options* o) {
+    if (!c) return QDSE_ERR_ARG;
+    std::string why;
+    if (check_options(o, why) != QDSE_OK) return fail(c, QDSE_ERR_ARG, why);
+    c->opt = *o;
+    c->stream = (cudaStream_t)o->stream;
+    return QDSE_OK;
+}
+
+qdse_status qdse_iterate(qdse_ctx* c, const qdse_params* p, double* A, double* B, int n_sweeps,
+                         double* max_rel_change) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    reset_stats(c);
+    if (n_sweeps < 0) return fail(c, QDSE_ERR_ARG, "n_sweeps must be >= 0");
+    if (check_ptr(c, A, "A") || check_ptr(c, B, "B")) return QDSE_ERR_ARG;
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    if (n_sweeps == 0) return QDSE_OK;
+    if (c->opt.precision != QDSE_FP64) {
+        s = ensure_kernels(c, p, rebuild);
+        if (s != QDSE_OK) return s;
+    }
+    Ctl ctl = make_ctl(c);
+    ctl.never_converge = 1;
+    ctl.max_iter = n_sweeps;
+    ctl.final_phase = (c->opt.precision == QDSE_MIXED || c->opt.precision == QDSE_FP32) ? PH_PICARD32 : PH_PICARD64;
+    const int phase0 = ctl.final_phase;
+    QCHECK(c, launch_init_state(c, ctl, A, B, phase0), "init");
+    bool to = false;
+    s = run_ticks(c, A, B, n_sweeps, to);
+    if (s != QDSE_OK) return s;
+    QCHECK(c, launch_finish(c, A, B, max_rel_change, nullptr, nullptr), "finish");
+    return QDSE_OK;
+}
+
+qdse_status qdse_solve(qdse_ctx* c, const qdse_params* p, double* A, double* B, int* iters,
+                       int* inst_status) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    reset_stats(c);
+    if (check_ptr(c, A, "A") || check_ptr(c, B, "B")) return QDSE_ERR_ARG;
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    if (c->opt.precision != QDSE_FP64) {
+        s = ensure_kernels(c, p, rebuild);
+        if (s != QDSE_OK) return s;
+    }
+    Ctl ctl = make_ctl(c);
+    const int phase0 = (c->opt.precision == QDSE_MIXED || c->opt.precision == QDSE_FP32) ? PH_PICARD32 : PH_PICARD64;
+    QCHECK(c, launch_init_state(c, ctl, A, B, phase0), "init");
+    bool timed_out = false;
+    s = run_ticks(c, A, B, -1, timed_out);
+    if (s != QDSE_OK) return s;
+    if (timed_out) {
+        QCHECK(c, launch_finish_timeout(c, A, B, nullptr, iters, inst_status), "finish");
+        QCHECK(c, cudaStreamSynchronize(c->stream), "sync");
+        return fail(c, QDSE_ERR_TIMEOUT, "time limit reached before every instance finished");
+    }
+    QCHECK(c, launch_finish(c, A, B, nullptr, iters, inst_status), "finish");
+    QCHECK(c, cudaStreamSynchronize(c->stream), "sync");
+    return QDSE_OK;
+}
+
+qdse_status qdse_solve_host(qdse_ctx* c, const qdse_params* p, double* A, double* B, int* iters,
+                            int* inst_status) {
+    if (!c) return QDSE_ERR_ARG;
+    if (check_ptr(c, A, "A") || check_ptr(c, B, "B")) return QDSE_ERR_ARG;
+    const size_t bytes = sizeof(double) * c->n_total;
+    double* dA = c->d_hostA;
+    double* dB = c->d_hostA + c->n_total;
+    QCHECK(c, cudaMemcpyAsync(dA, A, bytes, cudaMemcpyHostToDevice, c->stream), "copy A in");
+    QCHECK(c, cudaMemcpyAsync(dB, B, bytes, cudaMemcpyHostToDevice, c->stream), "copy B in");
+    qdse_status s = qdse_solve(c, p, dA, dB, c->d_hostI, c->d_hostI + c->n_inst);
+    if (s != QDSE_OK && s != QDSE_ERR_TIMEOUT) return s;
+    QCHECK(c, cudaMemcpyAsync(A, dA, bytes, cudaMemcpyDeviceToHost, c->stream), "copy A out");
+    QCHECK(c, cudaMemcpyAsync(B, dB, bytes, cudaMemcpyDeviceToHost, c->stream), "copy B out");
+    if (iters)
+        QCHECK(c, cudaMemcpyAsync(iters, c->d_hostI, sizeof(int) * c->n_inst,
+                                  cudaMemcpyDeviceToHost, c->stream), "copy iters");
+    if (inst_status)
+        QCHECK(c, cudaMemcpyAsync(inst_status, c->d_hostI + c->n_inst, sizeof(int) * c->n_inst,
+                                  cudaMemcpyDeviceToHost, c->stream), "copy status");
+    QCHECK(c, cudaStreamSynchronize(c->stream), "sync");
+    return s;
+}
+
+qdse_status qdse_residual(qdse_ctx* c, const qdse_params* p, const double* A, const double* B,
+                          double* FA, double* FB, double* rel_res) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    reset_stats(c);
+    if (check_ptr(c, A, "A") || check_ptr(c, B, "B")) return QDSE_ERR_ARG;
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    Ctl ctl = make_ctl(c);
+    QCHECK(c, cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream), "ctl");
+    double* oA = FA ? FA : c->work.xn64;
+    double* oB = FB ? FB : c->work.xn64 + c->n_total;
+    if (c->opt.precision == QDSE_FP64) {
+        QCHECK(c, launch_prep64(c, A, B, nullptr, nullptr), "prep");
+        QCHECK(c, launch_sweep_otf(c, A, B, oA, oB, 0), "fp64 sweep");
+        if (rel_res) QCHECK(c, launch_rel64(c, A, B, oA, oB, rel_res), "rel");
+    } else {
+        s = ensure_kernels(c, p, rebuild);
+        if (s != QDSE_OK) return s;
+        QCHECK(c, launch_residual_fp64(c, A, B, oA, oB, rel_res, 0, c->d_Khi, c->d_Klo), "residual");
+    }
+    return QDSE_OK;
+}
+
+qdse_status qdse_jvp(qdse_ctx* c, const qdse_params* p, const double* A, const double* B,
+                     const double* vA, const double* vB, double* JvA, double* JvB) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    reset_stats(c);
+    const void* ptrs[] = {A, B, vA, vB, JvA, JvB};
+    for (const void* q : ptrs)
+        if (!q) return fail(c, QDSE_ERR_ARG, "jvp: null pointer");
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    s = ensure_kernels(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    Ctl ctl = make_ctl(c);
+    QCHECK(c, cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream), "ctl");
+    QCHECK(c, launch_jvp(c, A, B, vA, vB, JvA, JvB), "jvp");
+    return QDSE_OK;
+}
+
+qdse_status qdse_vjp(qdse_ctx* c, const qdse_params* p, const double* A, const double* B,
+                     const double* wA, const double* wB, double* JtA, double* JtB) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    reset_stats(c);
+    const void* ptrs[] = {A, B, wA, wB, JtA, JtB};
+    for (const void* q : ptrs)
+        if (!q) return fail(c, QDSE_ERR_ARG, "vjp: null pointer");
+    if (c->any_staggered)
+        return fail(c, QDSE_ERR_UNSUPPORTED, "transposed sweep: collocated grids only");
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    s = ensure_kernels(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    Ctl ctl = make_ctl(c);
+    QCHECK(c, cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream), "ctl");
+    QCHECK(c, launch_vjp(c, A, B, wA, wB, JtA, JtB, 0, nullptr, nullptr), "vjp");
+    return QDSE_OK;
+}
+
+qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, const double* B,
+                         const double* gA, const double* gB, double* g_params,
+                         double* lambda_out, int* inst_status) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    reset_stats(c);
+    const void* ptrs[] = {A, B, gA, gB, g_params};
+    for (const void* q : ptrs)
+        if (!q) return fail(c, QDSE_ERR_ARG, "adjoint: null pointer");
+    if (c->any_staggered)
+        return fail(c, QDSE_ERR_UNSUPPORTED, "adjoint: collocated grids only");
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    if (!c->d_Kwhi) {
+        cudaError_t e = dalloc(&c->d_Kwhi, (size_t)c->k_total);
+        if (e == cudaSuccess) e = dalloc(&c->d_Kwlo, (size_t)c->k_total);
+        if (e != cudaSuccess) return cuda_fail(c, e, "allocate omega-derivative kernels");
+    }
+    if (rebuild || !c->kw_valid) {
+        QCHECK(c, launch_precompute(c, true), "precompute kernels and omega derivatives");
+        for (int b = 0; b < c->n_inst; ++b) c->k_omega[b] = p[b].omega;
+        c->k_valid_for = 1;
+        c->kw_valid = 1;
+    }
+    Ctl ctl = make_ctl(c);
+    QCHECK(c, cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream), "ctl");
+    QCHECK(c, launch_adjoint_init(c, c->work.lam, gA, gB), "adjoint init");
+    QCHECK(c, launch_adjoint_prep(c, A, B), "adjoint prep");
+    const auto t0 = std::chrono::steady_clock::now();
+    bool timed_out = false;
+    int chunk = 4;
+    while (true) {
+        for (int t = 0; t < chunk; ++t) {
+            QCHECK(c, launch_adjoint_sweep(c, gA, gB), "transposed sweep");
+            if (t == chunk - 1)
+                QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
+            QCHECK(c, launch_adjoint_update(c, c->work.lam, c->work.lamn, c->d_count), "adjoint update");
+        }
+        QCHECK(c, cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "poll");
+        QCHECK(c, cudaStreamSynchronize(c->stream), "poll sync");
+        c->polls++;
+        if (*c->h_count == 0) break;
+        if (c->opt.time_limit > 0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > c->opt.time_limit) {
+            timed_out = true;
+            break;
+        }
+        if (chunk < 64) chunk *= 2;
+    }
+    // dF/dD = (F(x*) - x0)/D and dF/domega at x*, both FP64 on the double-float kernels
+    double* Fh = c->work.xn64;
+    double* Fw = c->work.r64;
+    QCHECK(c, launch_residual_fp64(c, A, B, Fh, Fh + c->n_total, nullptr, 1, c->d_Khi, c->d_Klo), "dF/dD");
+    QCHECK(c, launch_residual_fp64(c, A, B, Fw, Fw + c->n_total, nullptr, 1, c->d_Kwhi, c->d_Kwlo), "dF/domega");
+    QCHECK(c, launch_adjoint_grads(c, A, B, c->work.lam, Fh, Fw, g_params, inst_status), "gradients");
+    if (lambda_out)
+        QCHECK(c, cudaMemcpyAsync(lambda_out, c->work.lam, sizeof(double) * 2 * c->n_total,
+                                  cudaMemcpyDeviceToDevice, c->stream), "copy lambda");
+    QCHECK(c, cudaStreamSynchronize(c->stream), "sync");
+    if (timed_out) return fail(c, QDSE_ERR_TIMEOUT, "time limit reached in the transposed solve");
+    return QDSE_OK;
+}
+
+qdse_status qdse_condensate(qdse_ctx* c, const double* A, const double* B, double* out) {
+    if (!c) return QDSE_ERR_ARG;
+    if (!A || !B || !out) return fail(c, QDSE_ERR_ARG, "condensate: null pointer");
+    QCHECK(c, launch_condensate(c, A, B, out), "condensate");
+    return QDSE_OK;
+}
+
+qdse_status qdse_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
+                                const double* cbar, double* gA, double* gB) {
+    if (!c) return QDSE_ERR_ARG;
+    if (!A || !B || !cbar || !gA || !gB) return fail(c, QDSE_ERR_ARG, "condensate_vjp: null pointer");
+    QCHECK(c, launch_condensate_vjp(c, A, B, cbar, gA, gB), "condensate vjp");
+    return QDSE_OK;
+}
+
+qdse_status qdse_last_stats(const qdse_ctx* c, long long* kernel_launches, long long* fp32_sweeps,
+                            long long* fp64_sweeps, long long* polls) {
+    if (!c) return QDSE_ERR_ARG;
+    if (kernel_launches) *kernel_launches = c->launches;
+    if (fp32_sweeps) *fp32_sweeps = c->sweeps32;
+    if (fp64_sweeps) *fp64_sweeps = c->sweeps64;
+    if (polls) *polls = c->polls;
+    return QDSE_OK;
+}
+
+}  // extern "C"

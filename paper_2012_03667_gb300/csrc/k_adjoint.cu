@@ -1,0 +1,416 @@
+// k_adjoint.cu -- transposed sweep, implicit-function adjoint and the chiral condensate.
+//
+// At a fixed point x* = F(x*) of the successive approximation (Eqs. jifen12, jifen122), a loss
+// L(x*(theta)) has dL/dtheta = lambda^T dF/dtheta with lambda = J^T lambda + g, J = dF/dx at x*
+// and g = dL/dx (implicit function theorem; no unrolled iterations are stored).  The transposed
+// fixed point is solved by the same successive approximation, sweep by sweep.
+//
+// J^T w for a collocated grid is computed row by row: with alpha_i = w^A_i kappa D/P_i and
+// beta_i = w^B_i kappa D, entry l collects
+//   (own)     sum_j alpha_l dT^A_lj/dx_l + beta_l dT^B_lj/dx_l          (row l of the kernels)
+//   (partner) sum_i alpha_i dT^A_il/dx_l + beta_i dT^B_il/dx_l          (column l = row l, since
+//             K_0 and K_3 are symmetric and K_T/(Q - P) is antisymmetric on a collocated grid)
+//   (diagonal) the removable-limit terms of rows l and of rows whose stencil contains l,
+// where T^A, T^B are the pair terms of the forward sweep (k_sweep.cu) and x_l = A_l or B_l
+// enters through a, b and e = W/(Q a^2 + b^2).  The pair j = l has no K_T part (it cancels).
+// Everything here runs in FP64 on the double-float kernels.
+#include <cfloat>
+
+#include "qdse_internal.h"
+
+namespace qdse {
+
+__device__ double block_sum_a(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if (threadIdx.x == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_max_a(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < nw) ? sh[threadIdx.x] : -DBL_MAX;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    }
+    if (threadIdx.x == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Per-point FP64 vectors at x*: a, b, u1, u2, u3 (e and its derivatives follow from them), the
+// stencil quotients, and the weights alpha_i, beta_i of the current cotangent w.
+// Stored in work.vec64 / dia64 (x* part, once) and work.dvec64 components 0, 1 (alpha, beta).
+__global__ void k_vjp_prep(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g,
+                           Work w, const double* A, const double* B, const double* wA,
+                           const double* wB, int ntot, int with_x) {
+    const DevInst I = inst[blockIdx.x];
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        if (with_x) {
+            const double a = A[gj], b = B[gj], Q = g.sq[gj];
+            const double e = g.W[gj] / (Q * a * a + b * b);
+            w.vec64[gj] = a;
+            w.vec64[ntot + gj] = b;
+            w.vec64[2 * ntot + gj] = e * b;
+            w.vec64[3 * ntot + gj] = e * a;
+            w.vec64[4 * ntot + gj] = e * a * Q;
+            const int s0 = I.x_off + g.sta[gj];
+            const double* c = g.stc + 3 * (size_t)gj;
+            w.dia64[gj] = c[0] * A[s0] + c[1] * A[s0 + 1] + c[2] * A[s0 + 2];
+            w.dia64[ntot + gj] = c[0] * B[s0] + c[1] * B[s0 + 1] + c[2] * B[s0 + 2];
+        }
+        const double scale = ctl->kappa * I.D;
+        w.dvec64[gj] = wA[gj] * scale / g.sp[gj];
+        w.dvec64[ntot + gj] = wB[gj] * scale;
+    }
+}
+
+// (J^T w)_l for a collocated grid.  One warp per point l.  If add_g, writes J^T w + g.
+__global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ inst,
+                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                 const float* __restrict__ Khi,
+                                                 const float* __restrict__ Klo,
+                                                 const DevState* __restrict__ state,
+                                                 double* JA, double* JB, const double* gA,
+                                                 const double* gB, int ntot, int add_g,
+                                                 int only_active) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= ntot) return;
+    const int bi = g.row_inst[r];
+    if (only_active && state[bi].phase == PH_DONE) return;
+    const DevInst I = inst[bi];
+    const int l = r - I.x_off;
+    const int o = I.x_off;
+    const long long plane = (long long)I.n * I.ld;
+    const long long row = I.k_off + (long long)l * I.ld;
+    const double* va = w.vec64 + o;
+    const double* vb = w.vec64 + ntot + o;
+    const double* v1 = w.vec64 + 2 * ntot + o;
+    const double* v2 = w.vec64 + 3 * ntot + o;
+    const double* v3 = w.vec64 + 4 * ntot + o;
+    const double* al = w.dvec64 + o;
+    const double* be = w.dvec64 + ntot + o;
+    const double* sp = g.sp + o;
+    const double Pl = sp[l], Al = va[l], Bl = vb[l];
+    const double Q = g.sq[r];
+    const double d = Q * Al * Al + Bl * Bl;
+    const double el = g.W[r] / d;
+    const double ca = -2.0 * el * Q * Al / d, cb = -2.0 * el * Bl / d;
+    const double alpha_l = al[l], beta_l = be[l];
+    double gAl = 0.0, gBl = 0.0;
+    if (ctl->vertex == QDSE_VERTEX_BC) {
+        for (int m = lane; m < I.n; m += 32) {
+            const double K0 = (double)Khi[row + m] + (double)Klo[row + m];
+            double KT = (double)Khi[row + plane + m] + (double)Klo[row + plane + m];
+            const double K3 = (double)Khi[row + 2 * plane + m] + (double)Klo[row + 2 * plane + m];
+            if (m == l) KT = 0.0;
+            // own part: l plays the row index, m the partner
+            const double u1 = v1[m], u2 = v2[m], u3 = v3[m];
+            gAl += alpha_l * (0.5 * (Pl * u2 + u3) * KT + 0.5 * u2 * K3) +
+                   beta_l * (-u1 * KT + 1.5 * u1 * K0);
+            gBl += alpha_l * (u1 * KT) + beta_l * (u2 * KT);
+            // partner part: m plays the row index i, l the partner; K_ml = K_lm, KT_ml = -KT_lm
+            const double KTi = -KT;
+            const double Ai = va[m], Bi = vb[m], Pi = sp[m], ai = al[m], bi = be[m];
+            const double PpQ = Pi + Q;
+            const double TAe = (-Bl * (Bl - Bi) - 0.5 * PpQ * Al * (Al - Ai)) * KTi +
+                               0.5 * Al * (Ai + Al) * K3;
+            const double TBe = (Al * Bi - Bl * Ai) * KTi + 1.5 * Bl * (Ai + Al) * K0;
+            const double dTA_da = el * (-0.5 * PpQ * (2.0 * Al - Ai) * KTi + 0.5 * (Ai + 2.0 * Al) * K3);
+            const double dTA_db = -el * (2.0 * Bl - Bi) * KTi;
+            const double dTB_da = el * (Bi * KTi + 1.5 * Bl * K0);
+            const double dTB_db = el * (-Ai * KTi + 1.5 * (Ai + Al) * K0);
+            gAl += ai * (dTA_da + TAe * ca) + bi * (dTB_da + TBe * ca);
+            gBl += ai * (dTA_db + TAe * cb) + bi * (dTB_db + TBe * cb);
+        }
+    } else {
+        for (int m = lane; m < I.n; m += 32) {
+            const double K0 = (double)Khi[row + m] + (double)Klo[row + m];
+            const double K3 = (double)Khi[row + 2 * plane + m] + (double)Klo[row + 2 * plane + m];
+            const double ai = al[m], bi = be[m];
+            gAl += ai * (el + Al * ca) * K3 + bi * 3.0 * Bl * ca * K0;
+            gBl += ai * Al * cb * K3 + bi * 3.0 * (el + Bl * cb) * K0;
+        }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        gAl += __shfl_xor_sync(0xffffffffu, gAl, s);
+        gBl += __shfl_xor_sync(0xffffffffu, gBl, s);
+    }
+    if (lane != 0) return;
+    if (ctl->vertex == QDSE_VERTEX_BC && I.mode == QDSE_COLLOCATED) {
+        // removable-limit terms of every row i whose value depends on x_l
+        const int i0 = l - 2 < 0 ? 0 : l - 2, i1 = l + 2 > I.n - 1 ? I.n - 1 : l + 2;
+        for (int i = i0; i <= i1; ++i) {
+            const long long rowi = I.k_off + (long long)i * I.ld;
+            const double KTd = (double)Khi[rowi + plane + i] + (double)Klo[rowi + plane + i];
+            const double ai = al[i], bi = be[i];
+            const double u1 = v1[i], u2 = v2[i], Pi = sp[i];
+            const double dA = w.dia64[o + i], dB = w.dia64[ntot + o + i];
+            const int sidx = l - g.sta[o + i];
+            if (sidx >= 0 && sidx <= 2) {
+                const double c = g.stc[3 * (size_t)(o + i) + sidx];
+                gAl += KTd * (ai * (-Pi * u2 * c) + bi * (u1 * c));
+                gBl += KTd * (ai * (-u1 * c) + bi * (-u2 * c));
+            }
+            if (i == l) {
+                const double eA = -2.0 * el * Pi * Al / d, eB = -2.0 * el * Bl / d;
+                gAl += KTd * (ai * (-Bl * eA * dB - Pi * (el + Al * eA) * dA) +
+                              bi * (Bl * eA * dA - (el + Al * eA) * dB));
+                gBl += KTd * (ai * (-(el + Bl * eB) * dB - Pi * Al * eB * dA) +
+                              bi * ((el + Bl * eB) * dA - Al * eB * dB));
+            }
+        }
+    }
+    if (add_g) {
+        gAl += gA[r];
+        gBl += gB[r];
+    }
+    JA[r] = gAl;
+    JB[r] = gBl;
+}
+
+// lambda <- (1 - alpha) lambda + alpha lambda_new with a max-norm relative stopping test.
+__global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* state,
+                                 const Ctl* __restrict__ ctl, Grid g, Work w, int ntot,
+                                 int* count) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    DevState s = state[b];
+    if (s.phase == PH_DONE) return;
+    const DevInst I = inst[b];
+    const double al = ctl->alpha;
+    double dmax = 0.0, cmax = 0.0, bad = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int k = c * ntot + gj;
+            const double ln = (1.0 - al) * w.lam[k] + al * w.lamn[k];
+            dmax = fmax(dmax, fabs(ln));
+            cmax = fmax(cmax, fabs(ln - w.lam[k]));
+            if (!isfinite(ln)) bad = 1.0;
+            w.lam[k] = ln;
+        }
+    }
+    dmax = block_max_a(dmax, sh);
+    cmax = block_max_a(cmax, sh);
+    bad = block_max_a(bad, sh);
+    // refresh alpha_i, beta_i for the next transposed sweep
+    const double scale = ctl->kappa * I.D;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        w.dvec64[gj] = w.lam[gj] * scale / g.sp[gj];
+        w.dvec64[ntot + gj] = w.lam[ntot + gj] * scale;
+    }
+    if (threadIdx.x == 0) {
+        s.iters += 1;
+        s.change = dmax > 0.0 ? cmax / dmax : 0.0;
+        if (bad != 0.0) {
+            s.phase = PH_DONE;
+            s.status = QDSE_ERR_NONFINITE;
+        } else if (s.change <= ctl->tol) {
+            s.phase = PH_DONE;
+            s.status = QDSE_OK;
+        } else if (s.iters >= ctl->max_iter) {
+            s.phase = PH_DONE;
+            s.status = QDSE_ERR_NOT_CONVERGED;
+        }
+        state[b] = s;
+        if (s.phase != PH_DONE && count) atomicAdd(count, 1);
+    }
+}
+
+__global__ void k_adjoint_init(const DevInst* __restrict__ inst, DevState* state, Work w,
+                               const double* gA, const double* gB, int ntot) {
+    const DevInst I = inst[blockIdx.x];
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        w.lam[gj] = gA[gj];
+        w.lam[ntot + gj] = gB[gj];
+    }
+    if (threadIdx.x == 0) {
+        DevState s{};
+        s.phase = PH_PICARD64;
+        s.status = QDSE_ERR_NOT_CONVERGED;
+        s.change = INFINITY;
+        state[blockIdx.x] = s;
+    }
+}
+
+// g_params[4b + (0..3)] = (lambda_B . 1, lambda . Fh / D, lambda . Fw, 0) with Fh = F(x*) - x0
+// and Fw = dF/domega at x*.
+__global__ void k_adjoint_grads(const DevInst* __restrict__ inst,
+                                const DevState* __restrict__ state, Work w, const double* Fh,
+                                const double* Fw, double* gp, int* inst_status, int ntot) {
+    __shared__ double sh[32];
+    const DevInst I = inst[blockIdx.x];
+    double sm = 0.0, sd = 0.0, sw = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        const double la = w.lam[gj], lb = w.lam[ntot + gj];
+        sm += lb;
+        sd += la * Fh[gj] + lb * Fh[ntot + gj];
+        sw += la * Fw[gj] + lb * Fw[ntot + gj];
+    }
+    sm = block_sum_a(sm, sh);
+    sd = block_sum_a(sd, sh);
+    sw = block_sum_a(sw, sh);
+    if (threadIdx.x == 0) {
+        gp[4 * blockIdx.x + 0] = sm;
+        gp[4 * blockIdx.x + 1] = I.D != 0.0 ? sd / I.D : 0.0;
+        gp[4 * blockIdx.x + 2] = sw;
+        gp[4 * blockIdx.x + 3] = 0.0;
+        if (inst_status) inst_status[blockIdx.x] = state[blockIdx.x].status;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// condensate  -<qbar q> = N_c/(4 pi^2) sum_j W_j b_j/(Q_j a_j^2 + b_j^2)
+// ------------------------------------------------------------------------------------------------
+__global__ void k_condensate(const DevInst* __restrict__ inst, Grid g, const double* A,
+                             const double* B, double* out) {
+    __shared__ double sh[32];
+    const DevInst I = inst[blockIdx.x];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        const double wt = g.wt[gj];
+        double a = A[gj], b = B[gj];
+        if (wt != 0.0) {
+            a += wt * (A[gj + 1] - a);
+            b += wt * (B[gj + 1] - b);
+        }
+        s += g.W[gj] * b / (g.sq[gj] * a * a + b * b);
+    }
+    s = block_sum_a(s, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = 3.0 / (4.0 * kPi * kPi) * s;
+}
+
+// gA_l += cbar dC/dA_l, gB_l += cbar dC/dB_l, pulled back through the interpolation.
+__global__ void k_condensate_vjp(const DevInst* __restrict__ inst, Grid g, const double* A,
+                                 const double* B, const double* cbar, double* gA, double* gB) {
+    const DevInst I = inst[blockIdx.x];
+    const double c = cbar[blockIdx.x] * 3.0 / (4.0 * kPi * kPi);
+    for (int l = threadIdx.x; l < I.n; l += blockDim.x) {
+        double ga = 0.0, gb = 0.0;
+        // internal nodes j = l (weight 1 - wt_l) and j = l - 1 (weight wt_{l-1}) use point l
+        for (int j = l - 1; j <= l; ++j) {
+            if (j < 0) continue;
+            const int gj = I.x_off + j;
+            const double wt = g.wt[gj];
+            const double f = (j == l) ? (1.0 - wt) : wt;
+            if (f == 0.0) continue;
+            double a = A[gj], b = B[gj];
+            if (wt != 0.0) {
+                a += wt * (A[gj + 1] - a);
+                b += wt * (B[gj + 1] - b);
+            }
+            const double Q = g.sq[gj], d = Q * a * a + b * b;
+            ga += f * g.W[gj] * b * (-2.0 * Q * a) / (d * d);
+            gb += f * g.W[gj] * (d - 2.0 * b * b) / (d * d);
+        }
+        gA[I.x_off + l] += c * ga;
+        gB[I.x_off + l] += c * gb;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const double* wA,
+                       const double* wB, double* JA, double* JB, int add_g, const double* gA,
+                       const double* gB) {
+    k_vjp_prep<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work, A, B, wA,
+                                                 wB, c->n_total, 1);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work,
+                                                            c->d_Khi, c->d_Klo, c->d_state, JA,
+                                                            JB, gA, gB, c->n_total, add_g, 0);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB) {
+    (void)lam;
+    k_adjoint_init<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, gA, gB,
+                                                     c->n_total);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B) {
+    k_vjp_prep<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work, A, B,
+                                                 c->work.lam, c->work.lam + c->n_total,
+                                                 c->n_total, 1);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* gA, const double* gB) {
+    k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, c->work.lamn,
+        c->work.lamn + c->n_total, gA, gB, c->n_total, 1, 1);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active) {
+    (void)lam;
+    (void)lam_new;
+    k_adjoint_update<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
+                                                       c->work, c->n_total, n_active);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_grads(qdse_ctx* c, const double* A, const double* B,
+                                 const double* lam, const double* F, const double* Fw,
+                                 double* g_params, int* inst_status) {
+    (void)A;
+    (void)B;
+    (void)lam;
+    k_adjoint_grads<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, F, Fw,
+                                                      g_params, inst_status, c->n_total);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_condensate(qdse_ctx* c, const double* A, const double* B, double* out) {
+    k_condensate<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->grid, A, B, out);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
+                                  const double* cbar, double* gA, double* gB) {
+    k_condensate_vjp<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->grid, A, B, cbar, gA, gB);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace qdse

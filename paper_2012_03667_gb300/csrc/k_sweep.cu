@@ -1,0 +1,792 @@
+// k_sweep.cu -- successive-approximation sweeps of the Ball-Chiu gap equation and the per-instance
+// solver state machine.
+//
+// One Jacobi sweep (Eq. jifen12 applied to Eqs. dsesys/dsesys2; every new A_i, B_i uses only the
+// previous iterate) reads, for external point p_i,
+//   A_i' = 1 + kappa D / P_i [ sum_j T^A_ij + diag^A_i ],   B_i' = m + kappa D [ sum_j T^B_ij + diag^B_i ]
+// with kappa = C_F/(8 pi^3) and, for internal node q_j with a = A(q_j), b = B(q_j),
+// e = W_j/(Q_j a^2 + b^2), u1 = e b, u2 = e a, u3 = e a Q_j (the BC vertex of Eq. 2 with
+// Sigma_A = (A_i + a)/2 and the difference quotients folded into the stored K_T/(Q_j - P_i)):
+//   T^A_ij = [-u1 (b - B_i) - (P_i u2 + u3)(a - A_i)/2] KT_ij + u2 (A_i + a)/2 K3_ij
+//   T^B_ij = [ u1 (a - A_i) - u2 (b - B_i)] KT_ij + 3/2 u1 (A_i + a) K0_ij
+// On a collocated grid the pair j = i contributes nothing to the KT terms (a = A_i, b = B_i) and
+// the removable limit q^2 -> p^2 is added separately with the stencil quotients dA, dB at p_i:
+//   diag^A_i = (-u1_i dB_i - P_i u2_i dA_i) K_T,ii,   diag^B_i = (u1_i dA_i - u2_i dB_i) K_T,ii.
+// The bare (rainbow) vertex keeps only u2 K3 and 3 u1 K0.
+//
+// A sweep is one warp per external point: lanes stride over j, read the three kernel rows
+// (coalesced) and the per-node vectors, accumulate in registers and reduce by warp shuffles.
+// The vectors (a, b, u1, u2, u3) are formed once per sweep per instance (O(N)) by the update
+// kernel, which also owns the convergence test (Eq. jifenab2, relative form) and the phase
+// transitions of the mixed-precision solve.
+#include <cfloat>
+
+#include "qdse_internal.h"
+
+namespace qdse {
+
+// ------------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reductions for blockDim.x a multiple of 32 (<= 1024).  All threads get the result.
+__device__ double block_max(double v, double* sh) {
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < nw) ? sh[threadIdx.x] : -DBL_MAX;
+    if (w == 0) r = warp_max(r);
+    if (threadIdx.x == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <typename T, bool LO>
+__device__ __forceinline__ T kload(const float* __restrict__ hi, const float* __restrict__ lo,
+                                   long long idx) {
+    if (LO) return (T)__ldg(hi + idx) + (T)__ldg(lo + idx);
+    return (T)__ldg(hi + idx);
+}
+
+// R7 relative change of one point: |d| / max(|x_new|, floor); 0 when d == 0.
+__device__ __forceinline__ double rel_change(double d, double xnew, double floor_) {
+    d = fabs(d);
+    if (d == 0.0) return 0.0;
+    const double den = fmax(fabs(xnew), floor_);
+    return den > 0.0 ? d / den : INFINITY;
+}
+
+// ------------------------------------------------------------------------------------------------
+// per-node vectors
+// ------------------------------------------------------------------------------------------------
+// a, b at internal node j: on-grid (collocated) or the modified interpolation (staggered).
+template <typename S>
+__device__ __forceinline__ double at_q(const S* F, int gj, double wt) {
+    double v = (double)F[gj];
+    if (wt != 0.0) v += wt * ((double)F[gj + 1] - v);
+    return v;
+}
+
+// Writes a, b, u1, u2, u3 (stride ntot) for every node of instance I, and the diagonal stencil
+// quotients dA/ds, dB/ds at p_i (collocated).  xa, xb: the iterate (FP32 or FP64 storage).
+template <typename S, typename T>
+__device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const S* xa,
+                                const S* xb, T* vec, T* dia) {
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        const double wt = g.wt[gj];
+        const double a = at_q(xa, gj, wt), b = at_q(xb, gj, wt);
+        const double Q = g.sq[gj];
+        const double e = g.W[gj] / (Q * a * a + b * b);
+        vec[gj] = (T)a;
+        vec[ntot + gj] = (T)b;
+        vec[2 * ntot + gj] = (T)(e * b);
+        vec[3 * ntot + gj] = (T)(e * a);
+        vec[4 * ntot + gj] = (T)(e * a * Q);
+        if (I.mode == QDSE_COLLOCATED) {
+            const int s0 = I.x_off + g.sta[gj];
+            const double* c = g.stc + 3 * (size_t)gj;
+            dia[gj] = (T)(c[0] * (double)xa[s0] + c[1] * (double)xa[s0 + 1] +
+                          c[2] * (double)xa[s0 + 2]);
+            dia[ntot + gj] = (T)(c[0] * (double)xb[s0] + c[1] * (double)xb[s0 + 1] +
+                                 c[2] * (double)xb[s0 + 2]);
+        }
+    }
+}
+
+// Tangent vectors at the iterate (xa, xb) in direction (va, vb):
+// delta a, delta b, delta u1, delta u2, delta u3 and the stencil of the direction.
+template <typename S, typename V, typename T>
+__device__ void prepare_tangent(const DevInst& I, const Grid& g, int ntot, const S* xa,
+                                const S* xb, const V* va, const V* vb, T* dvec, T* ddia) {
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        const double wt = g.wt[gj];
+        const double a = at_q(xa, gj, wt), b = at_q(xb, gj, wt);
+        const double da = at_q(va, gj, wt), db = at_q(vb, gj, wt);
+        const double Q = g.sq[gj];
+        const double d = Q * a * a + b * b;
+        const double e = g.W[gj] / d;
+        const double de = -e * (2.0 * Q * a * da + 2.0 * b * db) / d;
+        const double du2 = de * a + e * da;
+        dvec[gj] = (T)da;
+        dvec[ntot + gj] = (T)db;
+        dvec[2 * ntot + gj] = (T)(de * b + e * db);
+        dvec[3 * ntot + gj] = (T)du2;
+        dvec[4 * ntot + gj] = (T)(du2 * Q);
+        if (I.mode == QDSE_COLLOCATED) {
+            const int s0 = I.x_off + g.sta[gj];
+            const double* c = g.stc + 3 * (size_t)gj;
+            ddia[gj] = (T)(c[0] * (double)va[s0] + c[1] * (double)va[s0 + 1] +
+                           c[2] * (double)va[s0 + 2]);
+            ddia[ntot + gj] = (T)(c[0] * (double)vb[s0] + c[1] * (double)vb[s0 + 1] +
+                                  c[2] * (double)vb[s0 + 2]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// row kernels (one warp per external point)
+// ------------------------------------------------------------------------------------------------
+// Sums of one sweep row: sA, sB with F^A = 1 + kappa D sA / P_i, F^B = m + kappa D sB.
+template <typename T, bool LO>
+__device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi, T Ai, T Bi,
+                                        const T* __restrict__ vec, const T* __restrict__ dia,
+                                        int ntot, const float* __restrict__ Khi,
+                                        const float* __restrict__ Klo, int vertex, T& outA,
+                                        T& outB) {
+    const long long plane = (long long)I.n * I.ld;
+    const long long row = I.k_off + (long long)i * I.ld;
+    const T* va = vec + I.x_off;
+    const T* vb = vec + ntot + I.x_off;
+    const T* v1 = vec + 2 * ntot + I.x_off;
+    const T* v2 = vec + 3 * ntot + I.x_off;
+    const T* v3 = vec + 4 * ntot + I.x_off;
+    T sA = 0, sB = 0;
+    if (vertex == QDSE_VERTEX_BC) {
+#pragma unroll 4
+        for (int j = lane; j < I.n; j += 32) {
+            const T a = va[j], b = vb[j], u1 = v1[j], u2 = v2[j], u3 = v3[j];
+            const T K0 = kload<T, LO>(Khi, Klo, row + j);
+            const T KT = kload<T, LO>(Khi, Klo, row + plane + j);
+            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            const T da = a - Ai, db = b - Bi, sa = Ai + a;
+            const T cT = -u1 * db - (T)0.5 * (Pi * u2 + u3) * da;
+            sA += cT * KT + (T)0.5 * u2 * sa * K3;
+            sB += (u1 * da - u2 * db) * KT + (T)1.5 * u1 * sa * K0;
+        }
+    } else {
+#pragma unroll 4
+        for (int j = lane; j < I.n; j += 32) {
+            const T K0 = kload<T, LO>(Khi, Klo, row + j);
+            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            sA += v2[j] * K3;
+            sB += (T)3 * v1[j] * K0;
+        }
+    }
+    sA = warp_sum(sA);
+    sB = warp_sum(sB);
+    if (vertex == QDSE_VERTEX_BC && I.mode == QDSE_COLLOCATED) {
+        const T KTd = kload<T, LO>(Khi, Klo, row + plane + i);
+        const T dAi = dia[I.x_off + i], dBi = dia[ntot + I.x_off + i];
+        sA += (-v1[i] * dBi - Pi * v2[i] * dAi) * KTd;
+        sB += (v1[i] * dAi - v2[i] * dBi) * KTd;
+    }
+    outA = sA;
+    outB = sB;
+}
+
+// Tangent of row_map in direction (dAi, dBi at p_i; dvec, ddia per node).
+template <typename T, bool LO>
+__device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T Pi, T Ai, T Bi,
+                                            T dAi, T dBi, const T* __restrict__ vec,
+                                            const T* __restrict__ dia,
+                                            const T* __restrict__ dvec,
+                                            const T* __restrict__ ddia, int ntot,
+                                            const float* __restrict__ Khi,
+                                            const float* __restrict__ Klo, int vertex, T& outA,
+                                            T& outB) {
+    const long long plane = (long long)I.n * I.ld;
+    const long long row = I.k_off + (long long)i * I.ld;
+    const int o = I.x_off;
+    T sA = 0, sB = 0;
+    if (vertex == QDSE_VERTEX_BC) {
+#pragma unroll 2
+        for (int j = lane; j < I.n; j += 32) {
+            const T a = vec[o + j], b = vec[ntot + o + j];
+            const T u1 = vec[2 * ntot + o + j], u2 = vec[3 * ntot + o + j],
+                    u3 = vec[4 * ntot + o + j];
+            const T ea = dvec[o + j], eb = dvec[ntot + o + j];
+            const T e1 = dvec[2 * ntot + o + j], e2 = dvec[3 * ntot + o + j],
+                    e3 = dvec[4 * ntot + o + j];
+            const T K0 = kload<T, LO>(Khi, Klo, row + j);
+            const T KT = kload<T, LO>(Khi, Klo, row + plane + j);
+            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            const T da = a - Ai, db = b - Bi, sa = Ai + a;
+            const T dda = ea - dAi, ddb = eb - dBi, dsa = dAi + ea;
+            const T t = Pi * u2 + u3, dt = Pi * e2 + e3;
+            const T dcT = -e1 * db - u1 * ddb - (T)0.5 * (dt * da + t * dda);
+            sA += dcT * KT + (T)0.5 * (e2 * sa + u2 * dsa) * K3;
+            sB += (e1 * da + u1 * dda - e2 * db - u2 * ddb) * KT +
+                  (T)1.5 * (e1 * sa + u1 * dsa) * K0;
+        }
+    } else {
+#pragma unroll 4
+        for (int j = lane; j < I.n; j += 32) {
+            const T K0 = kload<T, LO>(Khi, Klo, row + j);
+            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            sA += dvec[3 * ntot + o + j] * K3;
+            sB += (T)3 * dvec[2 * ntot + o + j] * K0;
+        }
+    }
+    sA = warp_sum(sA);
+    sB = warp_sum(sB);
+    if (vertex == QDSE_VERTEX_BC && I.mode == QDSE_COLLOCATED) {
+        const T KTd = kload<T, LO>(Khi, Klo, row + plane + i);
+        const int gi = o + i;
+        const T u1 = vec[2 * ntot + gi], u2 = vec[3 * ntot + gi];
+        const T e1 = dvec[2 * ntot + gi], e2 = dvec[3 * ntot + gi];
+        const T dA = dia[gi], dB = dia[ntot + gi], edA = ddia[gi], edB = ddia[ntot + gi];
+        sA += (-e1 * dB - u1 * edB - Pi * (e2 * dA + u2 * edA)) * KTd;
+        sB += (e1 * dA + u1 * edA - e2 * dB - u2 * edB) * KTd;
+    }
+    outA = sA;
+    outB = sB;
+}
+
+// One tick of the batched solve: every external point of every unfinished instance advances by
+// the operation its instance's phase asks for.
+__global__ void __launch_bounds__(256) k_tick(const DevInst* __restrict__ inst,
+                                              const DevState* __restrict__ state,
+                                              const Ctl* __restrict__ ctl, Grid g, Work w,
+                                              const float* __restrict__ Khi,
+                                              const float* __restrict__ Klo, const double* A,
+                                              const double* B, int ntot) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= ntot) return;
+    const int b = g.row_inst[r];
+    const int phase = state[b].phase;
+    if (phase == PH_DONE) return;
+    const DevInst I = inst[b];
+    const int i = r - I.x_off;
+    const int vertex = ctl->vertex;
+    const double scale = ctl->kappa * I.D;
+    if (phase == PH_PICARD32) {
+        float sA, sB;
+        row_map<float, false>(lane, I, i, g.sp32[r], w.x32[r], w.x32[ntot + r], w.vec32, w.dia32,
+                              ntot, Khi, Klo, vertex, sA, sB);
+        if (lane == 0) {
+            w.xn32[r] = (float)(1.0 + scale * (double)sA / g.sp[r]);
+            w.xn32[ntot + r] = (float)(I.m + scale * (double)sB);
+        }
+    } else if (phase == PH_TANGENT32) {
+        float sA, sB;
+        row_tangent<float, false>(lane, I, i, g.sp32[r], w.x32[r], w.x32[ntot + r], w.d32[r],
+                                  w.d32[ntot + r], w.vec32, w.dia32, w.dvec32, w.ddia32, ntot,
+                                  Khi, Klo, vertex, sA, sB);
+        if (lane == 0) {
+            w.xn32[r] = (float)(scale * (double)sA / g.sp[r]);
+            w.xn32[ntot + r] = (float)(scale * (double)sB);
+        }
+    } else {  // PH_RESID64 or PH_PICARD64 on the precomputed double-float kernels
+        double sA, sB;
+        row_map<double, true>(lane, I, i, g.sp[r], A[r], B[r], w.vec64, w.dia64, ntot, Khi, Klo,
+                              vertex, sA, sB);
+        if (lane == 0) {
+            w.xn64[r] = 1.0 + scale * sA / g.sp[r];
+            w.xn64[ntot + r] = I.m + scale * sB;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 on-the-fly sweep: the full (j, theta) double sum of Eqs. dsesys/dsesys2 for every point,
+// with exp() per term and no precomputed kernel matrices.  One block per external point.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ inst,
+                                                   const DevState* __restrict__ state,
+                                                   const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                   const double* __restrict__ A,
+                                                   const double* __restrict__ B,
+                                                   double* __restrict__ FA,
+                                                   double* __restrict__ FB, int ntot,
+                                                   int only_active) {
+    extern __shared__ double sm[];
+    const int r = blockIdx.x;
+    const int b = g.row_inst[r];
+    if (only_active && state[b].phase == PH_DONE) return;
+    const DevInst I = inst[b];
+    const int i = r - I.x_off;
+    double* sy = sm;
+    double* sz = sm + I.nt;
+    double* ss = sm + 2 * I.nt;
+    double* sw = sm + 3 * I.nt;
+    double* red = sm + 4 * I.nt;
+    for (int k = threadIdx.x; k < I.nt; k += blockDim.x) {
+        sy[k] = g.y[I.t_off + k];
+        sz[k] = g.z[I.t_off + k];
+        ss[k] = g.s2[I.t_off + k];
+        sw[k] = g.wz[I.t_off + k];
+    }
+    __syncthreads();
+    const int vertex = ctl->vertex;
+    const double P = g.sp[r], rP = g.rsp[r];
+    const double Ai = A[r], Bi = B[r];
+    const double iw2 = 1.0 / (I.omega * I.omega);
+    const double pref = 8.0 * kPi * kPi * I.D / (I.omega * I.omega * I.omega * I.omega);
+    double sA = 0.0, sB = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        const double a = w.vec64[gj], bq = w.vec64[ntot + gj];
+        const double Q = g.sq[gj], rQ = g.rsq[gj];
+        const double e = g.W[gj] / (Q * a * a + bq * bq);
+        double qA, qB;  // difference quotients of Eq. 2
+        if (I.mode == QDSE_COLLOCATED && j == i) {
+            qA = w.dia64[gj];
+            qB = w.dia64[ntot + gj];
+        } else {
+            qA = (a - Ai) / (Q - P);
+            qB = (bq - Bi) / (Q - P);
+        }
+        const double SA = 0.5 * (Ai + a);
+        const double dd = (rP - rQ) * (rP - rQ), c2 = 2.0 * rP * rQ, x0 = rP * rQ;
+        const double PQ = P * Q, PpQ = P + Q;
+        double S0 = 0.0, ST = 0.0, S3 = 0.0;
+        for (int k = 0; k < I.nt; ++k) {
+            const double k2 = dd + c2 * sy[k];
+            const double E = sw[k] * exp(-k2 * iw2);
+            const double rk = 1.0 / k2;
+            const double x = x0 * sz[k];
+            S0 += E;
+            ST += E * 2.0 * PQ * ss[k] * rk;
+            S3 += E * (3.0 * x * PpQ - 4.0 * x * x - 2.0 * PQ) * rk;
+        }
+        if (vertex == QDSE_VERTEX_BC) {
+            sA += e * ((-bq * qB - 0.5 * PpQ * a * qA) * ST + a * SA * S3);
+            sB += e * ((-a * qB + bq * qA) * ST + 3.0 * bq * SA * S0);
+        } else {
+            sA += e * a * S3;
+            sB += 3.0 * e * bq * S0;
+        }
+    }
+    sA = block_sum(sA, red);
+    sB = block_sum(sB, red);
+    if (threadIdx.x == 0) {
+        FA[r] = 1.0 + ctl->kappa * pref * sA / P;
+        FB[r] = I.m + ctl->kappa * pref * sB;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// per-instance state machine
+// ------------------------------------------------------------------------------------------------
+__device__ void prepare_phase(int phase, const DevInst& I, const Grid& g, const Work& w, int ntot,
+                              const double* A, const double* B) {
+    if (phase == PH_PICARD32) {
+        prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.dia32);
+    } else if (phase == PH_RESID64 || phase == PH_PICARD64) {
+        prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, w.dia64);
+    } else if (phase == PH_TANGENT32) {
+        prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
+                                             w.d32 + ntot, w.dvec32, w.ddia32);
+    }
+}
+
+// Set every instance to its first phase, convert the start to FP32 where needed and form the
+// vectors of the first sweep.  One block per instance.
+__global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
+                             const Ctl* __restrict__ ctl, Grid g, Work w, const double* A,
+                             const double* B, int ntot, int phase0) {
+    const int b = blockIdx.x;
+    const DevInst I = inst[b];
+    if (phase0 == PH_PICARD32) {
+        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            const int gj = I.x_off + j;
+            w.x32[gj] = (float)A[gj];
+            w.x32[ntot + gj] = (float)B[gj];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        DevState s;
+        s.phase = phase0;
+        s.iters = 0;
+        s.inner = 0;
+        s.status = QDSE_ERR_NOT_CONVERGED;
+        s.change = INFINITY;
+        s.dnorm = INFINITY;
+        s.loc = (phase0 == PH_PICARD32) ? 1 : 0;
+        s.pad = 0;
+        state[b] = s;
+    }
+    prepare_phase(phase0, I, g, w, ntot, A, B);
+}
+
+// Advance one instance after a tick.  One block (256 threads) per instance.
+__global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst, DevState* state,
+                                                const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                double* A, double* B, int ntot, int* count) {
+    __shared__ double sh[32];
+    __shared__ int s_next;
+    const int b = blockIdx.x;
+    DevState s = state[b];
+    if (s.phase == PH_DONE) return;
+    const DevInst I = inst[b];
+    const Ctl C = *ctl;
+    const int o = I.x_off;
+    int next = s.phase;
+    bool done = false;
+    int status = s.status;
+
+    if (s.phase == PH_PICARD32 || s.phase == PH_PICARD64 || s.phase == PH_RESID64) {
+        // relaxed Picard step (or the residual of one) and its R7 relative change
+        const bool f32 = (s.phase == PH_PICARD32);
+        double bmax = 0.0, bad = 0.0;
+        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            const int gj = o + j;
+            double fb = f32 ? (double)w.xn32[ntot + gj] : w.xn64[ntot + gj];
+            double fa = f32 ? (double)w.xn32[gj] : w.xn64[gj];
+            double xb = f32 ? (double)w.x32[ntot + gj] : B[gj];
+            double xa = f32 ? (double)w.x32[gj] : A[gj];
+            if (s.phase != PH_RESID64) {
+                fa = (1.0 - C.alpha) * xa + C.alpha * fa;
+                fb = (1.0 - C.alpha) * xb + C.alpha * fb;
+            }
+            bmax = fmax(bmax, fabs(fb));
+            if (!isfinite(fa) || !isfinite(fb)) bad = 1.0;
+        }
+        bmax = block_max(bmax, sh);
+        bad = block_max(bad, sh);
+        const double fl = 1e-12 * bmax;
+        double ch = 0.0;
+        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            const int gj = o + j;
+            double fa = f32 ? (double)w.xn32[gj] : w.xn64[gj];
+            double fb = f32 ? (double)w.xn32[ntot + gj] : w.xn64[ntot + gj];
+            const double xa = f32 ? (double)w.x32[gj] : A[gj];
+            const double xb = f32 ? (double)w.x32[ntot + gj] : B[gj];
+            if (s.phase != PH_RESID64) {
+                fa = (1.0 - C.alpha) * xa + C.alpha * fa;
+                fb = (1.0 - C.alpha) * xb + C.alpha * fb;
+            }
+            ch = fmax(ch, fmax(rel_change(fa - xa, fa, 0.0), rel_change(fb - xb, fb, fl)));
+            if (s.phase == PH_PICARD32) {
+                w.x32[gj] = (float)fa;
+                w.x32[ntot + gj] = (float)fb;
+            } else if (s.phase == PH_PICARD64) {
+                A[gj] = fa;
+                B[gj] = fb;
+            } else {  // residual: keep r = F(x) - x for the correction solve
+                w.r64[gj] = fa - xa;
+                w.r64[ntot + gj] = fb - xb;
+            }
+        }
+        ch = block_max(ch, sh);
+        s.change = ch;
+        s.iters += 1;
+        if (bad != 0.0) {
+            done = true;
+            status = QDSE_ERR_NONFINITE;
+        } else if (!C.never_converge && ch <= C.tol) {
+            done = true;
+            status = QDSE_OK;
+        }
+        if (s.phase == PH_RESID64) {
+            if (done && status == QDSE_OK) {
+                // accept the FP64 Picard step from the refined iterate
+                for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                    A[o + j] = w.xn64[o + j];
+                    B[o + j] = w.xn64[ntot + o + j];
+                }
+            } else if (!done) {
+                // start a correction solve delta = J delta + r at the current x
+                for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                    const int gj = o + j;
+                    w.d64[gj] = w.r64[gj];
+                    w.d64[ntot + gj] = w.r64[ntot + gj];
+                    w.d32[gj] = (float)w.r64[gj];
+                    w.d32[ntot + gj] = (float)w.r64[ntot + gj];
+                    w.x32[gj] = (float)A[gj];
+                    w.x32[ntot + gj] = (float)B[gj];
+                }
+                __syncthreads();
+                prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.dia32);
+                next = PH_TANGENT32;
+                s.inner = 0;
+            }
+        } else if (s.phase == PH_PICARD32 && !done && C.final_phase != PH_PICARD32 &&
+                   (ch <= C.sw_tol || s.iters >= C.max_fp32)) {
+            next = PH_RESID64;  // hand the FP32 iterate to the FP64 refinement
+        }
+    } else if (s.phase == PH_TANGENT32) {
+        // delta <- delta + alpha (J delta + r - delta); relative change of delta (max norm)
+        double dmax = 0.0, cmax = 0.0, bad = 0.0;
+        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            const int gj = o + j;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int k = c * ntot + gj;
+                const double d = w.d64[k];
+                const double dn = d + C.alpha * ((double)w.xn32[k] + w.r64[k] - d);
+                dmax = fmax(dmax, fabs(dn));
+                cmax = fmax(cmax, fabs(dn - d));
+                if (!isfinite(dn)) bad = 1.0;
+                w.d64[k] = dn;
+                w.d32[k] = (float)dn;
+            }
+        }
+        dmax = block_max(dmax, sh);
+        cmax = block_max(cmax, sh);
+        bad = block_max(bad, sh);
+        s.iters += 1;
+        s.inner += 1;
+        s.dnorm = dmax > 0.0 ? cmax / dmax : 0.0;
+        if (bad != 0.0) {
+            done = true;
+            status = QDSE_ERR_NONFINITE;
+        } else if (s.dnorm <= C.inner_tol || s.inner >= C.max_inner) {
+            for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                A[o + j] += w.d64[o + j];
+                B[o + j] += w.d64[ntot + o + j];
+            }
+            next = PH_RESID64;
+        }
+    }
+    if (!done && s.iters >= C.max_iter) {
+        done = true;
+        status = QDSE_ERR_NOT_CONVERGED;
+    }
+    __syncthreads();
+    if (done) {
+        next = PH_DONE;
+    } else {
+        if (next == PH_RESID64 && s.phase == PH_PICARD32) {
+            for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                A[o + j] = (double)w.x32[o + j];
+                B[o + j] = (double)w.x32[ntot + o + j];
+            }
+            __syncthreads();
+        }
+        if (next != PH_TANGENT32 || s.phase == PH_TANGENT32) {
+            prepare_phase(next, I, g, w, ntot, A, B);
+        } else {
+            prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
+                                                 w.d32 + ntot, w.dvec32, w.ddia32);
+        }
+    }
+    if (threadIdx.x == 0) {
+        s_next = next;
+        s.phase = next;
+        s.status = status;
+        if (next == PH_PICARD32) s.loc = 1;
+        else if (next != PH_DONE) s.loc = 0;
+        state[b] = s;
+        if (!done && count) atomicAdd(count, 1);
+    }
+}
+
+// Copy the final iterate out of the FP32 store where needed and report per-instance results.
+__global__ void k_finish(const DevInst* __restrict__ inst, const DevState* __restrict__ state,
+                         Work w, double* A, double* B, int ntot, double* change_out, int* iters,
+                         int* status, int timed_out) {
+    const int b = blockIdx.x;
+    const DevInst I = inst[b];
+    const DevState s = state[b];
+    if (s.loc == 1) {
+        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            A[I.x_off + j] = (double)w.x32[I.x_off + j];
+            B[I.x_off + j] = (double)w.x32[ntot + I.x_off + j];
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (change_out) change_out[b] = s.change;
+        if (iters) iters[b] = s.iters;
+        if (status) {
+            int st = s.status;
+            if (timed_out && s.phase != PH_DONE) st = QDSE_ERR_TIMEOUT;
+            status[b] = st;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// stand-alone FP64 evaluations (residual, Jacobian-vector product)
+// ------------------------------------------------------------------------------------------------
+__global__ void k_prep64(const DevInst* __restrict__ inst, Grid g, Work w, const double* A,
+                         const double* B, const double* vA, const double* vB, int ntot) {
+    const DevInst I = inst[blockIdx.x];
+    prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, w.dia64);
+    if (vA) prepare_tangent<double, double, double>(I, g, ntot, A, B, vA, vB, w.dvec64, w.ddia64);
+}
+
+// F(x) (homogeneous = 0) or F(x) - x0 (homogeneous = 1) on the double-float kernels.
+__global__ void __launch_bounds__(256) k_row_map64(const DevInst* __restrict__ inst,
+                                                   const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                   const float* __restrict__ Khi,
+                                                   const float* __restrict__ Klo,
+                                                   const double* A, const double* B, double* FA,
+                                                   double* FB, int ntot, int homogeneous) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= ntot) return;
+    const DevInst I = inst[g.row_inst[r]];
+    const int i = r - I.x_off;
+    double sA, sB;
+    row_map<double, true>(lane, I, i, g.sp[r], A[r], B[r], w.vec64, w.dia64, ntot, Khi, Klo,
+                          ctl->vertex, sA, sB);
+    if (lane == 0) {
+        const double scale = ctl->kappa * I.D;
+        FA[r] = (homogeneous ? 0.0 : 1.0) + scale * sA / g.sp[r];
+        FB[r] = (homogeneous ? 0.0 : I.m) + scale * sB;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_row_jvp64(const DevInst* __restrict__ inst,
+                                                   const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                   const float* __restrict__ Khi,
+                                                   const float* __restrict__ Klo,
+                                                   const double* A, const double* B,
+                                                   const double* vA, const double* vB,
+                                                   double* JA, double* JB, int ntot) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= ntot) return;
+    const DevInst I = inst[g.row_inst[r]];
+    const int i = r - I.x_off;
+    double sA, sB;
+    row_tangent<double, true>(lane, I, i, g.sp[r], A[r], B[r], vA[r], vB[r], w.vec64, w.dia64,
+                              w.dvec64, w.ddia64, ntot, Khi, Klo, ctl->vertex, sA, sB);
+    if (lane == 0) {
+        const double scale = ctl->kappa * I.D;
+        JA[r] = scale * sA / g.sp[r];
+        JB[r] = scale * sB;
+    }
+}
+
+// R7 relative change between F and x per instance.
+__global__ void k_rel64(const DevInst* __restrict__ inst, const double* A, const double* B,
+                        const double* FA, const double* FB, double* rel) {
+    __shared__ double sh[32];
+    const DevInst I = inst[blockIdx.x];
+    double bmax = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) bmax = fmax(bmax, fabs(FB[I.x_off + j]));
+    bmax = block_max(bmax, sh);
+    double ch = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+        ch = fmax(ch, fmax(rel_change(FA[gj] - A[gj], FA[gj], 0.0),
+                           rel_change(FB[gj] - B[gj], FB[gj], 1e-12 * bmax)));
+    }
+    ch = block_max(ch, sh);
+    if (threadIdx.x == 0) rel[blockIdx.x] = ch;
+}
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+static inline int row_blocks(int ntot) { return (ntot + 7) / 8; }
+
+cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0) {
+    cudaError_t e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    k_init_state<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
+                                                   c->work, A, B, c->n_total, phase0);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick(qdse_ctx* c, double* A, double* B) {
+    k_tick<<<row_blocks(c->n_total), 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl,
+                                                          c->grid, c->work, c->d_Khi, c->d_Klo, A,
+                                                          B, c->n_total);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
+    k_update<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
+                                               A, B, c->n_total, c->d_count);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_otf(qdse_ctx* c, const double* A, const double* B, double* FA,
+                             double* FB, int only_active) {
+    const size_t smem = (4 * (size_t)c->max_nt + 32) * sizeof(double);
+    k_sweep_otf<<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
+                                                      c->work, A, B, FA, FB, c->n_total,
+                                                      only_active);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(qdse_ctx* c, double* A, double* B, double* change_out, int* iters,
+                          int* status) {
+    k_finish<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, A, B, c->n_total,
+                                               change_out, iters, status, 0);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_timeout(qdse_ctx* c, double* A, double* B, double* change_out,
+                                  int* iters, int* status) {
+    k_finish<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, A, B, c->n_total,
+                                               change_out, iters, status, 1);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep64(qdse_ctx* c, const double* A, const double* B, const double* vA,
+                          const double* vB) {
+    k_prep64<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->grid, c->work, A, B, vA, vB,
+                                               c->n_total);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_fp64(qdse_ctx* c, const double* A, const double* B, double* FA,
+                                 double* FB, double* rel, int homogeneous, const float* Khi,
+                                 const float* Klo) {
+    cudaError_t e = launch_prep64(c, A, B, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    k_row_map64<<<row_blocks(c->n_total), 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, Khi, Klo, A, B, FA, FB, c->n_total, homogeneous);
+    c->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !rel) return e;
+    k_rel64<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, A, B, FA, FB, rel);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jvp(qdse_ctx* c, const double* A, const double* B, const double* vA,
+                       const double* vB, double* JA, double* JB) {
+    cudaError_t e = launch_prep64(c, A, B, vA, vB);
+    if (e != cudaSuccess) return e;
+    k_row_jvp64<<<row_blocks(c->n_total), 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, vA, vB, JA, JB,
+        c->n_total);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rel64(qdse_ctx* c, const double* A, const double* B, const double* FA,
+                         const double* FB, double* rel) {
+    k_rel64<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, A, B, FA, FB, rel);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace qdse

@@ -1,0 +1,198 @@
+// qdse_internal.h -- internal data structures of libqdse (not part of the C interface).
+//
+// Device memory layout (all arrays structure-of-arrays over the batch):
+//   points      : every instance b owns global point indices [x_off[b], x_off[b] + n_b).
+//                 FP64 grid arrays (s_p, s_q, W, ...) and every per-point work vector use this
+//                 index; vectors with several components are stored component-major with stride
+//                 n_total (component c of point g at [c * n_total + g]).
+//   kernel pool : instance b owns 3 planes of n_b x ld_b floats starting at k_off[b]
+//                 (plane 0 = K_0, 1 = K_T / (Q_j - P_i) (diagonal: K_T), 2 = K_3), rows i
+//                 (external p_i), columns j (internal q_j), ld_b = n_b rounded up to 4.  The
+//                 same layout holds the low parts (double-float residues) in a second buffer and,
+//                 for the adjoint, the omega-derivatives of the three kernels.
+//   angular     : instance b owns nodes [t_off[b], t_off[b] + n_theta_b).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qdse.h"
+
+namespace qdse {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int kMaxN = 1024;
+constexpr int kMaxTheta = 512;
+
+// Solver phases of one instance (a small state machine advanced on the device).
+enum Phase : int {
+    PH_PICARD32 = 0,  // FP32 successive approximation on the precomputed kernels
+    PH_RESID64 = 1,   // FP64 evaluation of F(x) for the refinement residual
+    PH_TANGENT32 = 2, // FP32 tangent sweep J(x) delta for the correction solve
+    PH_PICARD64 = 3,  // FP64 successive approximation (precomputed or on-the-fly kernels)
+    PH_DONE = 4
+};
+
+struct DevInst {          // per-instance descriptor, read-only during a solve
+    int n;                // radial points
+    int nt;               // angular nodes
+    int x_off;            // first global point
+    int t_off;            // first angular node
+    long long k_off;      // first element of plane 0 in the kernel pool
+    int ld;               // row stride of the kernel planes (n rounded up to 4)
+    int mode;             // QDSE_COLLOCATED / QDSE_STAGGERED
+    double D, omega, m;   // current parameters
+};
+
+struct DevState {         // per-instance solver state, updated by the update kernel
+    int phase;
+    int iters;            // sweeps of any kind
+    int inner;            // tangent sweeps in the current correction solve
+    int status;           // qdse_status of the instance
+    double change;        // last R7 relative change (Picard) or residual
+    double dnorm;         // last relative change of the correction (inner solve)
+    int loc;              // 1 if the current iterate lives in the FP32 copy, 0 if in A, B
+    int pad;
+};
+
+struct Ctl {              // solver controls shared by every instance of a call
+    double kappa;         // C_F / (8 pi^3)
+    double tol;           // final tolerance
+    double sw_tol;        // FP32 -> refinement switch threshold
+    double inner_tol;     // relative change that ends a correction solve
+    double alpha;         // relaxation
+    int max_iter;
+    int max_inner;        // tangent sweeps per correction solve
+    int max_fp32;         // cap of the FP32 Picard phase
+    int vertex;           // QDSE_VERTEX_BC / _RL
+    int precision;
+    int final_phase;      // PH_PICARD64 for FP64 modes, PH_PICARD32 for FP32-only
+    int never_converge;   // 1 for qdse_iterate (run exactly max_iter sweeps)
+};
+
+// Work arrays (device).  Component counts in brackets, each of length n_total.
+struct Work {
+    double* xn64;   // [2] F(x) in FP64 (residual / FP64 sweeps)
+    double* r64;    // [2] refinement right-hand side r = F(x) - x
+    double* d64;    // [2] correction delta (FP64 master)
+    double* vec64;  // [5] per internal node: a, b, u1 = e b, u2 = e a, u3 = e a Q (FP64)
+    double* dia64;  // [2] diagonal difference quotients dA/ds, dB/ds at p_i (collocated)
+    float* x32;     // [2] FP32 iterate
+    float* xn32;    // [2] FP32 sweep output (F(x) or J delta)
+    float* vec32;   // [5] FP32 copies of vec64 entries at the current iterate
+    float* dia32;   // [2]
+    float* dvec32;  // [5] tangent: delta a, delta b, delta u1, delta u2, delta u3
+    float* ddia32;  // [2] tangent: stencil of delta
+    float* d32;     // [2] FP32 copy of the correction (delta A_i, delta B_i at p_i)
+    double* dvec64; // [5] FP64 tangent vectors (Jacobian-vector products)
+    double* ddia64; // [2]
+    double* lam;    // [2] adjoint iterate
+    double* lamn;   // [2] adjoint sweep output
+};
+
+struct Grid {              // FP64 grid arrays on the device (global point index)
+    double* sp;            // external nodes s_p = p^2
+    double* sq;            // internal nodes s_q = q^2
+    double* W;             // internal weights, int ds s f ~ sum W f
+    double* rsp;           // sqrt(s_p)
+    double* rsq;           // sqrt(s_q)
+    double* wt;            // staggered: weight of the upper bracket point (0 at the last node)
+    double* stc;           // [3] collocated: Lagrange derivative coefficients (per s) of the stencil
+    int* sta;              // collocated: first point of the stencil (local index)
+    float* sp32;           // float copies
+    float* sq32;
+    double* z;             // angular nodes (per instance slice)
+    double* y;             // 1 - z
+    double* s2;            // 1 - z^2
+    double* wz;            // angular weights
+    int* row_inst;         // instance of every global point
+};
+
+struct HostInst {
+    qdse_grid g;
+    int x_off, t_off, ld;
+    long long k_off;
+};
+
+}  // namespace qdse
+
+struct qdse_ctx {
+    int n_inst = 0;
+    int n_total = 0;
+    int t_total = 0;
+    long long k_total = 0;   // floats per kernel plane set (sum of 3 n ld)
+    int max_n = 0, max_nt = 0;
+    qdse_options opt{};
+    cudaStream_t stream = nullptr;
+    std::vector<qdse::HostInst> hinst;
+    std::vector<double> h_sp, h_sq, h_W;  // host copies of the grid
+    bool any_staggered = false;
+
+    qdse::DevInst* d_inst = nullptr;
+    qdse::DevState* d_state = nullptr;
+    qdse::Ctl* d_ctl = nullptr;
+    qdse::Grid grid{};
+    qdse::Work work{};
+    float* d_Khi = nullptr;
+    float* d_Klo = nullptr;
+    float* d_Kwhi = nullptr;  // omega-derivative kernels (allocated on first adjoint)
+    float* d_Kwlo = nullptr;
+    int* d_count = nullptr;   // [1] number of unfinished instances after the last update
+    unsigned long long* d_sweeps = nullptr;  // [2] instance-sweeps in FP32 / FP64 of the call
+    double* d_hostA = nullptr;  // staging for qdse_solve_host: [2 n_total] doubles
+    int* d_hostI = nullptr;     // [2 n_inst] ints (iterations, status)
+    int* h_count = nullptr;   // pinned mirror
+    qdse::DevInst* h_inst_pinned = nullptr;
+
+    std::string err;
+    long long launches = 0, sweeps32 = 0, sweeps64 = 0, polls = 0;
+    int k_valid_for = 0;     // 1 if the kernel pool matches the parameters in d_inst (w, grid)
+    int kw_valid = 0;
+    std::vector<double> k_omega;  // omega each instance's kernels were built for
+};
+
+namespace qdse {
+
+// ---- host grid construction (grid.cpp) -------------------------------------------------------
+int gauss_legendre_nodes(int n, double* t, double* v);
+void build_instance_grid(const qdse_grid& g, double* sp, double* sq, double* W, double* wt,
+                         double* stc, int* sta);
+void build_angular(int nt, double* z, double* y, double* s2, double* w);
+
+// ---- kernel launchers (return cudaError_t of the launch) -------------------------------------
+cudaError_t launch_precompute(qdse_ctx* c, bool with_omega_derivative);
+cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
+cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
+cudaError_t launch_update(qdse_ctx* c, double* A, double* B);
+cudaError_t launch_sweep_otf(qdse_ctx* c, const double* A, const double* B, double* FA,
+                             double* FB, int only_active);
+cudaError_t launch_finish(qdse_ctx* c, double* A, double* B, double* change_out, int* iters,
+                          int* status);
+cudaError_t launch_residual_fp64(qdse_ctx* c, const double* A, const double* B, double* FA,
+                                 double* FB, double* rel, int homogeneous, const float* Khi,
+                                 const float* Klo);
+cudaError_t launch_jvp(qdse_ctx* c, const double* A, const double* B, const double* vA,
+                       const double* vB, double* JA, double* JB);
+cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const double* wA,
+                       const double* wB, double* JA, double* JB, int add_g, const double* gA,
+                       const double* gB);
+cudaError_t launch_condensate(qdse_ctx* c, const double* A, const double* B, double* out);
+cudaError_t launch_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
+                                  const double* cbar, double* gA, double* gB);
+cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active);
+cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B);
+cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* gA, const double* gB);
+cudaError_t launch_finish_timeout(qdse_ctx* c, double* A, double* B, double* change_out,
+                                  int* iters, int* status);
+cudaError_t launch_prep64(qdse_ctx* c, const double* A, const double* B, const double* vA,
+                          const double* vB);
+cudaError_t launch_rel64(qdse_ctx* c, const double* A, const double* B, const double* FA,
+                         const double* FB, double* rel);
+cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB);
+cudaError_t launch_adjoint_grads(qdse_ctx* c, const double* A, const double* B,
+                                 const double* lam, const double* F, const double* Fw,
+                                 double* g_params, int* inst_status);
+
+}  // namespace qdse

@@ -1,0 +1,365 @@
+"""GPU parity: the CUDA path (through the C interface) against the FP64 oracle, element by element.
+
+Tolerances: FP64 sweeps and FP64 maps/derivatives agree with the oracle to 1e-12 relative (only
+summation order differs); converged FP64 solutions to 1e-10 (both sides iterate to 1e-13 or run the
+same sweep count); the mixed-precision solve to 1e-8 (the target of the FP32 sweeps + FP64
+refinement scheme).  Relative errors are max-norm over each function (max|dx| / max|x|).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2012_03667_gb300 import build as Bld
+from paper_2012_03667_gb300 import inputs
+from paper_2012_03667_gb300 import qdse as Q
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    Bld.build()
+    Q.load_library()
+    torch.cuda.set_device(0)
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def problem(inst, mode=O.COLLOCATED, vertex=O.BC):
+    return O.Problem(n=inst.n_p, n_theta=inst.n_theta, s_min=inst.s_min, s_max=inst.s_max,
+                     grid_mode=mode, vertex=vertex, D=inst.D, omega=inst.omega, m=inst.m)
+
+
+def grid(inst, mode=Q.QDSE_COLLOCATED):
+    return Q.Grid(inst.n_p, inst.n_theta, inst.s_min, inst.s_max, mode)
+
+
+def prm(inst):
+    return [[inst.D, inst.omega, inst.m, 0.0]]
+
+
+SMALL = inputs.SMALL
+PAPER = inputs.PAPER
+TINY = inputs.Instance(40, 24, 0.93, 0.5, 0.005)  # several 32-wide tiles + a ragged tail
+
+
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [Q.QDSE_FP64, Q.QDSE_FP64_PRE])
+@pytest.mark.parametrize("inst", [SMALL, PAPER, TINY], ids=["small", "paper", "tiny"])
+def test_fp64_sweeps_match_oracle_iterate_by_iterate(precision, inst):
+    ctx = Q.Context(grid(inst), 1, precision=precision)
+    pr = problem(inst)
+    A = dev(np.full(inst.n_p, 1.0)); B = dev(np.full(inst.n_p, 0.3))
+    Ao, Bo = np.full(inst.n_p, 1.0), np.full(inst.n_p, 0.3)
+    done = 0
+    for n in (1, 2, 5):
+        ctx.qdse_iterate(prm(inst), A, B, n - done)
+        for _ in range(n - done):
+            Ao, Bo = O.sweep(pr, Ao, Bo)
+        done = n
+        assert rel(host(A), Ao) < 1e-12, n
+        assert rel(host(B), Bo) < 1e-12, n
+
+
+@pytest.mark.parametrize("mode", [O.COLLOCATED, O.STAGGERED])
+@pytest.mark.parametrize("vertex", [O.BC, O.RL])
+def test_map_residual_matches_oracle_random_inputs(mode, vertex):
+    inst = TINY
+    rng = np.random.default_rng(3)
+    A = 1 + rng.uniform(0, 1.5, inst.n_p); B = rng.uniform(0.01, 0.8, inst.n_p)
+    Fo_A, Fo_B = O.sweep(problem(inst, mode, vertex), A, B)
+    for precision in (Q.QDSE_FP64, Q.QDSE_FP64_PRE):
+        ctx = Q.Context(grid(inst, mode), 1, precision=precision, vertex=vertex)
+        FA = dev(np.zeros(inst.n_p)); FB = dev(np.zeros(inst.n_p)); r = dev(np.zeros(1))
+        ctx.qdse_residual(prm(inst), dev(A), dev(B), FA, FB, r)
+        assert rel(host(FA), Fo_A) < 1e-12
+        assert rel(host(FB), Fo_B) < 1e-12
+
+
+def test_fp32_sweeps_track_oracle():
+    inst = SMALL
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_FP32)
+    A = dev(np.full(inst.n_p, 1.0)); B = dev(np.full(inst.n_p, 0.3))
+    ctx.qdse_iterate(prm(inst), A, B, 3)
+    Ao, Bo = np.full(inst.n_p, 1.0), np.full(inst.n_p, 0.3)
+    for _ in range(3):
+        Ao, Bo = O.sweep(problem(inst), Ao, Bo)
+    assert rel(host(A), Ao) < 2e-5 and rel(host(B), Bo) < 2e-5
+
+
+def test_jvp_matches_complex_step_jacobian():
+    inst = TINY
+    rng = np.random.default_rng(9)
+    A = 1 + rng.uniform(0, 1.5, inst.n_p); B = rng.uniform(0.05, 0.8, inst.n_p)
+    J = O.jacobian(problem(inst), A, B)
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_FP64_PRE)
+    for trial in range(3):
+        v = rng.normal(size=2 * inst.n_p)
+        JA = dev(np.zeros(inst.n_p)); JB = dev(np.zeros(inst.n_p))
+        ctx.qdse_jvp(prm(inst), dev(A), dev(B), dev(v[:inst.n_p]), dev(v[inst.n_p:]), JA, JB)
+        ref = J @ v
+        got = np.concatenate([host(JA), host(JB)])
+        assert rel(got, ref) < 1e-11
+
+
+@pytest.mark.parametrize("vertex", [O.BC, O.RL])
+def test_vjp_matches_transposed_jacobian(vertex):
+    inst = TINY
+    rng = np.random.default_rng(4)
+    A = 1 + rng.uniform(0, 1.5, inst.n_p); B = rng.uniform(0.05, 0.8, inst.n_p)
+    J = O.jacobian(problem(inst, vertex=vertex), A, B)
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_FP64_PRE, vertex=vertex)
+    w = rng.normal(size=2 * inst.n_p)
+    JA = dev(np.zeros(inst.n_p)); JB = dev(np.zeros(inst.n_p))
+    ctx.qdse_vjp(prm(inst), dev(A), dev(B), dev(w[:inst.n_p]), dev(w[inst.n_p:]), JA, JB)
+    got = np.concatenate([host(JA), host(JB)])
+    assert rel(got, J.T @ w) < 1e-11
+
+
+# ------------------------------------------------------------------------------------------------
+def oracle_fixed_point(inst, mode=O.COLLOCATED, vertex=O.BC):
+    A, B, it, ch, st = O.solve(problem(inst, mode, vertex), tol=1e-13, max_iter=20000,
+                               nthreads=O.max_threads())
+    assert st == 0
+    return A, B, it
+
+
+@pytest.mark.parametrize("precision,tol", [(Q.QDSE_FP64, 1e-10), (Q.QDSE_FP64_PRE, 1e-10),
+                                           (Q.QDSE_MIXED, 1e-8)])
+@pytest.mark.parametrize("inst", [SMALL, PAPER], ids=["small", "paper"])
+def test_solve_matches_oracle_fixed_point(precision, tol, inst):
+    Ar, Br, it = oracle_fixed_point(inst)
+    ctx = Q.Context(grid(inst), 1, precision=precision, tol=1e-13, max_iter=40000)
+    A = dev(np.full(inst.n_p, 1.0)); B = dev(np.full(inst.n_p, 0.3))
+    iters = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_solve(prm(inst), A, B, iters, st)
+    assert int(st.item()) == Q.QDSE_OK
+    eA, eB = rel(host(A), Ar), rel(host(B), Br)
+    eM = rel(host(B) / host(A), Br / Ar)
+    assert max(eA, eB, eM) < tol, (eA, eB, eM)
+
+
+def test_staggered_solve_matches_oracle():
+    inst = PAPER
+    Ar, Br, it = oracle_fixed_point(inst, O.STAGGERED)
+    ctx = Q.Context(grid(inst, Q.QDSE_STAGGERED), 1, precision=Q.QDSE_MIXED, tol=1e-13)
+    A = dev(np.full(inst.n_p, 1.0)); B = dev(np.full(inst.n_p, 0.3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_solve(prm(inst), A, B, None, st)
+    assert int(st.item()) == 0
+    assert rel(host(A), Ar) < 1e-8 and rel(host(B), Br) < 1e-8
+
+
+def test_ragged_batch_matches_per_instance_oracle():
+    insts = [inputs.Instance(48, 16, 0.55, 0.678, 0.005), inputs.Instance(64, 24, 0.7, 0.6, 0.05),
+             inputs.Instance(37, 8, 0.6, 0.55, 0.0), inputs.Instance(72, 32, 0.5, 0.7, 0.1)]
+    grids = [grid(i) for i in insts]
+    ctx = Q.Context(grids, precision=Q.QDSE_MIXED, tol=1e-13, max_iter=40000)
+    x_off = ctx.layout()
+    A = dev(np.ones(ctx.n_total)); B = dev(np.full(ctx.n_total, 0.3))
+    st = torch.zeros(len(insts), dtype=torch.int32, device="cuda")
+    ctx.qdse_solve([[i.D, i.omega, i.m, 0] for i in insts], A, B, None, st)
+    Ah, Bh = host(A), host(B)
+    assert np.all(host(st) == 0)
+    for b, inst in enumerate(insts):
+        Ar, Br, _ = oracle_fixed_point(inst)
+        sl = slice(x_off[b], x_off[b + 1])
+        assert rel(Ah[sl], Ar) < 1e-8 and rel(Bh[sl], Br) < 1e-8, b
+
+
+LARGE_PAPER = inputs.Instance(512, 128, 0.55, 0.678, 0.005)
+
+
+@pytest.mark.parametrize("precision", [Q.QDSE_FP64, Q.QDSE_FP64_PRE])
+def test_large_grid_first_sweeps_match_oracle(precision):
+    """N = 512, N_theta = 128, D = 0.93, w = 0.5: sweep-by-sweep parity.  At these parameters the
+    Picard iteration is chaotic (rounding differences grow ~10x per 10 sweeps after the first
+    ~20), so iterates are compared while the two trajectories are still the same trajectory."""
+    inst = inputs.LARGE
+    pr = problem(inst)
+    ctx = Q.Context(grid(inst), 1, precision=precision)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    Ao, Bo = np.ones(inst.n_p), np.full(inst.n_p, 0.3)
+    done = 0
+    for n, tol in ((1, 1e-13), (5, 1e-12), (15, 1e-11)):
+        ctx.qdse_iterate(prm(inst), A, B, n - done)
+        for _ in range(n - done):
+            Ao, Bo = O.sweep(pr, Ao, Bo, nthreads=O.max_threads())
+        done = n
+        assert rel(host(A), Ao) < tol and rel(host(B), Bo) < tol, n
+
+
+def test_large_grid_solution_is_a_fixed_point_of_the_oracle_map():
+    """The FP64 GPU solve at N = 512, N_theta = 128, D = 0.93 (deterministic on the GPU) ends on a
+    fixed point of the oracle's map, checked on every row."""
+    inst = inputs.LARGE
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_FP64, tol=1e-11, max_iter=6000)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_solve(prm(inst), A, B, None, st)
+    assert int(st.item()) == 0
+    Ah, Bh = host(A), host(B)
+    Fa, Fb = O.sweep(problem(inst), Ah, Bh, nthreads=O.max_threads())
+    assert rel(Fa, Ah) < 1e-9 and rel(Fb, Bh) < 1e-9
+
+
+@pytest.mark.parametrize("precision,tol", [(Q.QDSE_FP64_PRE, 1e-10), (Q.QDSE_MIXED, 1e-8)])
+def test_large_grid_solve_matches_oracle_paper_parameters(precision, tol):
+    """N = 512, N_theta = 128 with the paper's D = 0.55, w = 0.678 (a unique attracting fixed
+    point): GPU solution against the oracle's, element by element."""
+    inst = LARGE_PAPER
+    Ar, Br, _ = oracle_fixed_point(inst)
+    ctx = Q.Context(grid(inst), 1, precision=precision, tol=1e-13, max_iter=5000)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_solve(prm(inst), A, B, None, st)
+    assert int(st.item()) == 0
+    assert rel(host(A), Ar) < tol and rel(host(B), Br) < tol
+    assert rel(host(B) / host(A), Br / Ar) < tol
+
+
+def test_mixed_solution_is_an_fp64_fixed_point_in_the_chaotic_regime():
+    """D = 0.93 on the large grid: whichever fixed point the mixed-precision solve reaches, it is
+    an FP64 fixed point to 1e-8: plain FP64 successive approximation restarted from it stays put,
+    and the oracle's map leaves it unchanged."""
+    inst = inputs.LARGE
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED, tol=1e-11, max_iter=6000)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_solve(prm(inst), A, B, None, st)
+    s = int(st.item())
+    assert s in (Q.QDSE_OK, Q.QDSE_ERR_NOT_CONVERGED)
+    if s != Q.QDSE_OK:
+        pytest.skip("the mixed trajectory ended in a cycle (allowed: Picard is chaotic here)")
+    Ah, Bh = host(A), host(B)
+    Fa, Fb = O.sweep(problem(inst), Ah, Bh, nthreads=O.max_threads())
+    assert rel(Fa, Ah) < 1e-9 and rel(Fb, Bh) < 1e-9
+    c64 = Q.Context(grid(inst), 1, precision=Q.QDSE_FP64, tol=1e-10, max_iter=2000)
+    A2, B2 = A.clone(), B.clone()
+    c64.qdse_solve(prm(inst), A2, B2, None, st)
+    assert int(st.item()) == 0
+    assert rel(host(A2), Ah) < 1e-8 and rel(host(B2), Bh) < 1e-8
+
+
+# ------------------------------------------------------------------------------------------------
+def test_adjoint_matches_oracle_adjoint():
+    inst = inputs.Instance(32, 16, 0.55, 0.678, 0.02)
+    pr = problem(inst)
+    Ar, Br, it, ch, st = O.solve(pr, tol=1e-14, max_iter=20000)
+    rng = np.random.default_rng(1)
+    gA = rng.normal(size=inst.n_p); gB = rng.normal(size=inst.n_p)
+    gp_ref, lam_ref = O.adjoint(pr, Ar, Br, gA, gB)
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED, tol=1e-14, max_iter=40000)
+    gp = dev(np.zeros(4)); lam = dev(np.zeros(2 * inst.n_p))
+    ist = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_adjoint(prm(inst), dev(Ar), dev(Br), dev(gA), dev(gB), gp, lam, ist)
+    assert int(ist.item()) == 0
+    assert rel(host(lam), lam_ref) < 1e-10
+    got = host(gp)
+    np.testing.assert_allclose(got[:3], gp_ref[:3], rtol=1e-9)
+    assert got[3] == 0.0
+
+
+def test_condensate_and_its_cotangent():
+    inst = PAPER
+    Ar, Br, _ = oracle_fixed_point(inst)
+    ctx = Q.Context(grid(inst), 1)
+    out = dev(np.zeros(1))
+    ctx.qdse_condensate(dev(Ar), dev(Br), out)
+    ref = O.condensate(problem(inst), Ar, Br)
+    assert host(out)[0] == pytest.approx(ref, rel=1e-13)
+    gA = dev(np.zeros(inst.n_p)); gB = dev(np.zeros(inst.n_p))
+    ctx.qdse_condensate_vjp(dev(Ar), dev(Br), dev([1.0]), gA, gB)
+    h = 1e-6
+    for k in (0, 20, 40):
+        for arr, g in ((Ar, gA), (Br, gB)):
+            xp = arr.copy(); xp[k] += h; xm = arr.copy(); xm[k] -= h
+            a1 = (xp, Br) if arr is Ar else (Ar, xp)
+            a2 = (xm, Br) if arr is Ar else (Ar, xm)
+            fd = (O.condensate(problem(inst), *a1) - O.condensate(problem(inst), *a2)) / (2 * h)
+            assert host(g)[k] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------
+def test_status_not_converged_nonfinite_and_timeout():
+    inst = SMALL
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED, max_iter=1)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    it = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_solve(prm(inst), A, B, it, st)
+    assert int(st.item()) == Q.QDSE_ERR_NOT_CONVERGED and int(it.item()) == 1
+    # a NaN in the start is reported per instance
+    ctx.set_options(max_iter=100)
+    a = np.ones(inst.n_p); a[10] = np.nan
+    A = dev(a); B = dev(np.full(inst.n_p, 0.3))
+    ctx.qdse_solve(prm(inst), A, B, None, st)
+    assert int(st.item()) == Q.QDSE_ERR_NONFINITE
+    # a wall-clock limit that runs out ends the call with QDSE_ERR_TIMEOUT (host-side check)
+    ctx3 = Q.Context(grid(inst), 1, precision=Q.QDSE_FP64, max_iter=10 ** 6, time_limit=1e-9,
+                     tol=0.0)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    with pytest.raises(Q.QdseError) as e:
+        ctx3.qdse_solve(prm(inst), A, B, None, st)
+    assert e.value.status == Q.QDSE_ERR_TIMEOUT
+    assert int(st.item()) == Q.QDSE_ERR_TIMEOUT
+
+
+def test_bad_parameters_rejected():
+    ctx = Q.Context(grid(SMALL), 1)
+    A = dev(np.ones(SMALL.n_p)); B = dev(np.full(SMALL.n_p, 0.3))
+    for p in ([[0.93, -0.5, 0.005, 0]], [[np.nan, 0.5, 0.005, 0]], [[0.93, 0.5, np.inf, 0]]):
+        with pytest.raises(Q.QdseError) as e:
+            ctx.qdse_solve(p, A, B)
+        assert e.value.status == Q.QDSE_ERR_ARG
+    with pytest.raises(Q.QdseError) as e:
+        ctx.qdse_solve([[0.93, 0.5, 0.005, 0.1]], A, B)
+    assert e.value.status == Q.QDSE_ERR_UNSUPPORTED
+
+
+def test_chiral_limit_keeps_b_zero():
+    inst = inputs.Instance(48, 16, 0.55, 0.678, 0.0)
+    for precision in (Q.QDSE_FP64, Q.QDSE_MIXED):
+        ctx = Q.Context(grid(inst), 1, precision=precision, tol=1e-12)
+        A = dev(np.ones(inst.n_p)); B = dev(np.zeros(inst.n_p))
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ctx.qdse_solve(prm(inst), A, B, None, st)
+        assert int(st.item()) == 0
+        assert np.all(host(B) == 0.0)
+
+
+def test_minimum_sizes():
+    inst = inputs.Instance(3, 1, 0.55, 0.678, 0.005, 1e-2, 1e2)
+    pr = problem(inst)
+    Ao, Bo = O.sweep(pr, np.ones(3), np.full(3, 0.3))
+    for precision in (Q.QDSE_FP64, Q.QDSE_FP64_PRE):
+        ctx = Q.Context(grid(inst), 1, precision=precision)
+        A = dev(np.ones(3)); B = dev(np.full(3, 0.3))
+        ctx.qdse_iterate(prm(inst), A, B, 1)
+        assert rel(host(A), Ao) < 1e-12 and rel(host(B), Bo) < 1e-12
+
+
+def test_host_buffer_entry_point_equals_device_path():
+    inst = PAPER
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED, tol=1e-12)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    ctx.qdse_solve(prm(inst), A, B)
+    Ah = np.ones(inst.n_p); Bh = np.full(inst.n_p, 0.3)
+    it = np.zeros(1, dtype=np.int32); st = np.zeros(1, dtype=np.int32)
+    ctx.qdse_solve_host(prm(inst), Ah, Bh, it, st)
+    assert st[0] == 0 and it[0] > 0
+    np.testing.assert_array_equal(Ah, host(A))
+    np.testing.assert_array_equal(Bh, host(B))
