@@ -205,6 +205,20 @@ qdse_status qdse_condensate_vjp(qdse_ctx* ctx, const double* A, const double* B,
 qdse_status qdse_last_stats(const qdse_ctx* ctx, long long* kernel_launches,
                             long long* fp32_sweeps, long long* fp64_sweeps, long long* polls);
 
+/* Work of the last call: algorithmic bytes of its sweep kernels (kernel-matrix rows, per-node
+ * vectors, own values and outputs, summed over every instance-sweep) and BC-kernel evaluations
+ * (n_p n_q n_theta per instance-sweep).  Synchronises the stream.  Either pointer may be NULL. */
+qdse_status qdse_last_work(const qdse_ctx* ctx, double* sweep_bytes, double* kernel_evals);
+
+/* Turn CUDA-event timing of every kernel launch on (1) or off (0).  Off by default: when on,
+ * each launch is bracketed by two events on the context's stream. */
+qdse_status qdse_set_profiling(qdse_ctx* ctx, int on);
+
+/* Device time of the last call's launches by kind, from the events recorded while profiling was
+ * on: ms[4] and launches[4] (host arrays) for 0 = kernel precompute, 1 = sweeps (all sweep,
+ * residual and transposed-sweep kernels), 2 = per-instance updates, 3 = other.  Synchronises. */
+qdse_status qdse_profile(const qdse_ctx* ctx, double* ms, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,35 @@
 
 using namespace qdse;
 
+namespace qdse {
+
+static cudaEvent_t next_event(qdse_ctx* c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+void prof_begin(qdse_ctx* c, int kind) {
+    if (!c->profiling) return;
+    cudaEvent_t a = next_event(c);
+    if (!a) return;
+    cudaEventRecord(a, c->stream);
+    c->prof.push_back({kind, a, nullptr});
+}
+
+void prof_end(qdse_ctx* c) {
+    if (!c->profiling || c->prof.empty() || c->prof.back().b) return;
+    cudaEvent_t b = next_event(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->prof.back().b = b;
+}
+
+}  // namespace qdse
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -74,9 +103,11 @@ void free_ctx(qdse_ctx* c) {
                     c->work.dia64, c->work.x32, c->work.xn32, c->work.vec32, c->work.dia32,
                     c->work.dvec32, c->work.ddia32, c->work.d32, c->work.dvec64, c->work.ddia64,
                     c->work.lam, c->work.lamn, c->d_Khi, c->d_Klo, c->d_Kwhi, c->d_Kwlo,
-                    c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI};
+                    c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
+                    c->grid.groups};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->h_count) cudaFreeHost(c->h_count);
     if (c->h_inst_pinned) cudaFreeHost(c->h_inst_pinned);
     delete c;
@@ -108,6 +139,8 @@ qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
         d.k_off = h.k_off;
         d.ld = h.ld;
         d.mode = h.g.grid_mode;
+        d.v_off = h.v_off;
+        d.pad_ = 0;
         d.D = p[b].D;
         d.omega = p[b].omega;
         d.m = p[b].m;
@@ -149,6 +182,9 @@ void reset_stats(qdse_ctx* c) {
     c->sweeps32 = 0;
     c->sweeps64 = 0;
     c->polls = 0;
+    c->ev_used = 0;
+    c->prof.clear();
+    if (c->d_sweeps) cudaMemsetAsync(c->d_sweeps, 0, 4 * sizeof(unsigned long long), c->stream);
 }
 
 // The batched successive approximation: ticks of (sweep rows, update instances) with the number
@@ -221,14 +257,17 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     c->k_omega.assign(n_inst, NAN);
     std::map<int, int> t_of;  // angular node count -> offset of its shared table
     long long k = 0;
-    int x = 0, t = 0;
+    int x = 0, t = 0, v = 0, ng = 0;
     for (int b = 0; b < n_inst; ++b) {
         HostInst& h = c->hinst[b];
         h.g = ragged ? g[b] : g[0];
         h.x_off = x;
         h.ld = (h.g.n_p + 3) & ~3;
+        h.v_off = v;
         h.k_off = k;
         x += h.g.n_p;
+        v += h.ld;
+        ng += (h.g.n_p + kRows - 1) / kRows;
         k += 3LL * h.g.n_p * h.ld;
         if (!t_of.count(h.g.n_theta)) {
             t_of[h.g.n_theta] = t;
@@ -240,6 +279,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         if (h.g.grid_mode == QDSE_STAGGERED) c->any_staggered = true;
     }
     c->n_total = x;
+    c->nv_total = v;
+    c->n_groups = ng;
     c->t_total = t;
     c->k_total = k;
 
@@ -247,6 +288,10 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     const int N = c->n_total;
     std::vector<double> sp(N), sq(N), W(N), wt(N), stc(3 * (size_t)N), rsp(N), rsq(N);
     std::vector<int> sta(N), row_inst(N);
+    std::vector<int2> groups;
+    groups.reserve(ng);
+    for (int b = 0; b < n_inst; ++b)
+        for (int i0 = 0; i0 < c->hinst[b].g.n_p; i0 += kRows) groups.push_back(make_int2(b, i0));
     std::vector<float> sp32(N), sq32(N);
     for (int b = 0; b < n_inst; ++b) {
         const HostInst& h = c->hinst[b];
@@ -294,6 +339,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->grid.s2, t);
     CALLOC(c->grid.wz, t);
     CALLOC(c->grid.row_inst, N);
+    CALLOC(c->grid.band, N);
+    CALLOC(c->grid.groups, ng);
     CALLOC(c->work.xn64, 2 * (size_t)N);
     CALLOC(c->work.r64, 2 * (size_t)N);
     CALLOC(c->work.d64, 2 * (size_t)N);
@@ -301,9 +348,9 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->work.dia64, 2 * (size_t)N);
     CALLOC(c->work.x32, 2 * (size_t)N);
     CALLOC(c->work.xn32, 2 * (size_t)N);
-    CALLOC(c->work.vec32, 5 * (size_t)N);
+    CALLOC(c->work.vec32, 5 * (size_t)v);
     CALLOC(c->work.dia32, 2 * (size_t)N);
-    CALLOC(c->work.dvec32, 5 * (size_t)N);
+    CALLOC(c->work.dvec32, 5 * (size_t)v);
     CALLOC(c->work.ddia32, 2 * (size_t)N);
     CALLOC(c->work.d32, 2 * (size_t)N);
     CALLOC(c->work.dvec64, 5 * (size_t)N);
@@ -313,7 +360,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->d_Khi, (size_t)k);
     CALLOC(c->d_Klo, (size_t)k);
     CALLOC(c->d_count, 1);
-    CALLOC(c->d_sweeps, 2);
+    CALLOC(c->d_sweeps, 4);
     CALLOC(c->d_hostA, 2 * (size_t)N);
     CALLOC(c->d_hostI, 2 * (size_t)n_inst);
 #undef CALLOC
@@ -333,7 +380,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         {c->grid.sq32, sq32.data(), sizeof(float) * N}, {c->grid.z, z.data(), sizeof(double) * t},
         {c->grid.y, y.data(), sizeof(double) * t}, {c->grid.s2, s2.data(), sizeof(double) * t},
         {c->grid.wz, wz.data(), sizeof(double) * t},
-        {c->grid.row_inst, row_inst.data(), sizeof(int) * N}};
+        {c->grid.row_inst, row_inst.data(), sizeof(int) * N},
+        {c->grid.groups, groups.data(), sizeof(int2) * ng}};
     for (auto& u : ups) {
         e = cudaMemcpy(u.d, u.h, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -341,6 +389,25 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
             free_ctx(c);
             return s;
         }
+    }
+    c->work.nv = v;
+    // zero the padding of the node vectors once; descriptors get their layout now and their
+    // parameters on every call
+    e = cudaMemset(c->work.vec32, 0, sizeof(float) * 5 * (size_t)v);
+    if (e == cudaSuccess) e = cudaMemset(c->work.dvec32, 0, sizeof(float) * 5 * (size_t)v);
+    if (e == cudaSuccess) {
+        std::vector<qdse_params> zero(n_inst, qdse_params{0.0, 1.0, 0.0, 0.0});
+        bool rb = false;
+        c->stream = nullptr;
+        if (set_params(c, zero.data(), rb) != QDSE_OK) e = cudaErrorUnknown;
+        else e = cudaStreamSynchronize(nullptr);
+        c->stream = (cudaStream_t)o->stream;
+        for (int b = 0; b < n_inst; ++b) c->k_omega[b] = NAN;
+    }
+    if (e != cudaSuccess) {
+        qdse_status s = cuda_fail(nullptr, e, "initialise workspaces");
+        free_ctx(c);
+        return s;
     }
     *out = c;
     return QDSE_OK;
@@ -650,10 +717,50 @@ qdse_status qdse_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
 qdse_status qdse_last_stats(const qdse_ctx* c, long long* kernel_launches, long long* fp32_sweeps,
                             long long* fp64_sweeps, long long* polls) {
     if (!c) return QDSE_ERR_ARG;
+    unsigned long long ctr[4] = {0, 0, 0, 0};
+    if (fp32_sweeps || fp64_sweeps) {
+        cudaError_t e = cudaMemcpyAsync(ctr, c->d_sweeps, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return QDSE_ERR_CUDA;
+    }
     if (kernel_launches) *kernel_launches = c->launches;
-    if (fp32_sweeps) *fp32_sweeps = c->sweeps32;
-    if (fp64_sweeps) *fp64_sweeps = c->sweeps64;
+    if (fp32_sweeps) *fp32_sweeps = (long long)ctr[0];
+    if (fp64_sweeps) *fp64_sweeps = (long long)ctr[1];
     if (polls) *polls = c->polls;
+    return QDSE_OK;
+}
+
+qdse_status qdse_last_work(const qdse_ctx* c, double* sweep_bytes, double* kernel_evals) {
+    if (!c) return QDSE_ERR_ARG;
+    unsigned long long ctr[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(ctr, c->d_sweeps, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return QDSE_ERR_CUDA;
+    if (sweep_bytes) *sweep_bytes = (double)ctr[2];
+    if (kernel_evals) *kernel_evals = (double)ctr[3];
+    return QDSE_OK;
+}
+
+qdse_status qdse_set_profiling(qdse_ctx* c, int on) {
+    if (!c) return QDSE_ERR_ARG;
+    c->profiling = on ? 1 : 0;
+    return QDSE_OK;
+}
+
+qdse_status qdse_profile(const qdse_ctx* c, double* ms, long long* launches) {
+    if (!c || !ms || !launches) return QDSE_ERR_ARG;
+    for (int k = 0; k < PK_COUNT; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return QDSE_ERR_CUDA;
+    for (const auto& r : c->prof) {
+        if (!r.a || !r.b || r.kind < 0 || r.kind >= PK_COUNT) continue;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return QDSE_ERR_CUDA;
+        ms[r.kind] += t;
+        launches[r.kind] += 1;
+    }
     return QDSE_OK;
 }
 

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
 // lambda <- (1 - alpha) lambda + alpha lambda_new with a max-norm relative stopping test.
 __global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* state,
                                  const Ctl* __restrict__ ctl, Grid g, Work w, int ntot,
-                                 int* count) {
+                                 int* count, unsigned long long* ctr) {
     __shared__ double sh[32];
     const int b = blockIdx.x;
     DevState s = state[b];
@@ -226,6 +226,12 @@ __global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* sta
         w.dvec64[ntot + gj] = w.lam[ntot + gj] * scale;
     }
     if (threadIdx.x == 0) {
+        if (ctr) {
+            const unsigned long long n = (unsigned long long)I.n;
+            atomicAdd(ctr + 1, 1ull);
+            atomicAdd(ctr + 2, 24ull * n * n + 96ull * n);
+            atomicAdd(ctr + 3, n * n * (unsigned long long)I.nt);
+        }
         s.iters += 1;
         s.change = dmax > 0.0 ? cmax / dmax : 0.0;
         if (bad != 0.0) {
@@ -343,48 +349,61 @@ __global__ void k_condensate_vjp(const DevInst* __restrict__ inst, Grid g, const
 cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const double* wA,
                        const double* wB, double* JA, double* JB, int add_g, const double* gA,
                        const double* gB) {
+    prof_begin(c, PK_OTHER);
     k_vjp_prep<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work, A, B, wA,
                                                  wB, c->n_total, 1);
     c->launches++;
+    prof_end(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    prof_begin(c, PK_SWEEP);
     k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work,
                                                             c->d_Khi, c->d_Klo, c->d_state, JA,
                                                             JB, gA, gB, c->n_total, add_g, 0);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB) {
     (void)lam;
+    prof_begin(c, PK_OTHER);
     k_adjoint_init<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, gA, gB,
                                                      c->n_total);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B) {
+    prof_begin(c, PK_OTHER);
     k_vjp_prep<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work, A, B,
                                                  c->work.lam, c->work.lam + c->n_total,
                                                  c->n_total, 1);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* gA, const double* gB) {
+    prof_begin(c, PK_SWEEP);
     k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
         c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, c->work.lamn,
         c->work.lamn + c->n_total, gA, gB, c->n_total, 1, 1);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active) {
     (void)lam;
     (void)lam_new;
+    prof_begin(c, PK_UPDATE);
     k_adjoint_update<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
-                                                       c->work, c->n_total, n_active);
+                                                       c->work, c->n_total, n_active,
+                                                       c->d_sweeps);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
@@ -394,22 +413,28 @@ cudaError_t launch_adjoint_grads(qdse_ctx* c, const double* A, const double* B,
     (void)A;
     (void)B;
     (void)lam;
+    prof_begin(c, PK_OTHER);
     k_adjoint_grads<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, F, Fw,
                                                       g_params, inst_status, c->n_total);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_condensate(qdse_ctx* c, const double* A, const double* B, double* out) {
+    prof_begin(c, PK_OTHER);
     k_condensate<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->grid, A, B, out);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
                                   const double* cbar, double* gA, double* gB) {
+    prof_begin(c, PK_OTHER);
     k_condensate_vjp<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->grid, A, B, cbar, gA, gB);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 

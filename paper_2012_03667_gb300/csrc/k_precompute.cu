@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
                                                     float* __restrict__ Kwhi,
                                                     float* __restrict__ Kwlo) {
     extern __shared__ double sm[];
+    __shared__ int s_lo, s_hi;
     const int r = blockIdx.x;  // global external point
     const int b = g.row_inst[r];
     const DevInst I = inst[b];
@@ -41,6 +42,10 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
         sz[k] = g.z[I.t_off + k];
         ss[k] = g.s2[I.t_off + k];
         sw[k] = g.wz[I.t_off + k];
+    }
+    if (threadIdx.x == 0) {
+        s_lo = I.ld;
+        s_hi = -1;
     }
     __syncthreads();
 
@@ -59,6 +64,8 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
             const double Q = g.sq[gj], rQ = g.rsq[gj];
             const double dd = (rP - rQ) * (rP - rQ);
             if (dd * iw2 < kSkipExponent) {
+                atomicMin(&s_lo, j);
+                atomicMax(&s_hi, j);
                 const double c2 = 2.0 * rP * rQ, x0 = rP * rQ, PQ = P * Q, PpQ = P + Q;
                 for (int k = 0; k < I.nt; ++k) {
                     const double k2 = dd + c2 * sy[k];
@@ -105,10 +112,26 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
             }
         }
     }
+    // the nonzero entries of a row are a contiguous range of j (|sqrt P - sqrt Q| grows
+    // monotonically away from it); store it widened to multiples of 4
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int lo = s_lo, hi = s_hi + 1;
+        if (hi <= lo) {
+            lo = 0;
+            hi = 0;
+        } else {
+            lo &= ~3;
+            hi = (hi + 3) & ~3;
+            if (hi > I.ld) hi = I.ld;
+        }
+        g.band[r] = make_int2(lo, hi);
+    }
 }
 
 cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
     const size_t smem = 4 * sizeof(double) * (size_t)c->max_nt;
+    prof_begin(c, PK_PRECOMPUTE);
     if (with_w) {
         k_precompute<true><<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->grid, c->d_Khi,
                                                                  c->d_Klo, c->d_Kwhi, c->d_Kwlo);
@@ -117,6 +140,7 @@ cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
                                                                   c->d_Klo, nullptr, nullptr);
     }
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 

@@ -100,20 +100,23 @@ __device__ __forceinline__ double at_q(const S* F, int gj, double wt) {
 
 // Writes a, b, u1, u2, u3 (stride ntot) for every node of instance I, and the diagonal stencil
 // quotients dA/ds, dB/ds at p_i (collocated).  xa, xb: the iterate (FP32 or FP64 storage).
+// Component c of node j goes to vec[c * vs + vb + j] (vs, vb: stride and instance base of the
+// layout in use; the FP32 vectors are padded, the FP64 ones use the global point index).
 template <typename S, typename T>
 __device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const S* xa,
-                                const S* xb, T* vec, T* dia) {
+                                const S* xb, T* vec, int vs, int vb, T* dia) {
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
         const int gj = I.x_off + j;
         const double wt = g.wt[gj];
         const double a = at_q(xa, gj, wt), b = at_q(xb, gj, wt);
         const double Q = g.sq[gj];
         const double e = g.W[gj] / (Q * a * a + b * b);
-        vec[gj] = (T)a;
-        vec[ntot + gj] = (T)b;
-        vec[2 * ntot + gj] = (T)(e * b);
-        vec[3 * ntot + gj] = (T)(e * a);
-        vec[4 * ntot + gj] = (T)(e * a * Q);
+        T* v = vec + vb + j;
+        v[0] = (T)a;
+        v[vs] = (T)b;
+        v[2 * vs] = (T)(e * b);
+        v[3 * vs] = (T)(e * a);
+        v[4 * vs] = (T)(e * a * Q);
         if (I.mode == QDSE_COLLOCATED) {
             const int s0 = I.x_off + g.sta[gj];
             const double* c = g.stc + 3 * (size_t)gj;
@@ -129,7 +132,8 @@ __device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const
 // delta a, delta b, delta u1, delta u2, delta u3 and the stencil of the direction.
 template <typename S, typename V, typename T>
 __device__ void prepare_tangent(const DevInst& I, const Grid& g, int ntot, const S* xa,
-                                const S* xb, const V* va, const V* vb, T* dvec, T* ddia) {
+                                const S* xb, const V* va, const V* vb, T* dvec, int vs, int vbase,
+                                T* ddia) {
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
         const int gj = I.x_off + j;
         const double wt = g.wt[gj];
@@ -140,11 +144,12 @@ __device__ void prepare_tangent(const DevInst& I, const Grid& g, int ntot, const
         const double e = g.W[gj] / d;
         const double de = -e * (2.0 * Q * a * da + 2.0 * b * db) / d;
         const double du2 = de * a + e * da;
-        dvec[gj] = (T)da;
-        dvec[ntot + gj] = (T)db;
-        dvec[2 * ntot + gj] = (T)(de * b + e * db);
-        dvec[3 * ntot + gj] = (T)du2;
-        dvec[4 * ntot + gj] = (T)(du2 * Q);
+        T* v = dvec + vbase + j;
+        v[0] = (T)da;
+        v[vs] = (T)db;
+        v[2 * vs] = (T)(de * b + e * db);
+        v[3 * vs] = (T)du2;
+        v[4 * vs] = (T)(du2 * Q);
         if (I.mode == QDSE_COLLOCATED) {
             const int s0 = I.x_off + g.sta[gj];
             const double* c = g.stc + 3 * (size_t)gj;
@@ -164,8 +169,9 @@ template <typename T, bool LO>
 __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi, T Ai, T Bi,
                                         const T* __restrict__ vec, const T* __restrict__ dia,
                                         int ntot, const float* __restrict__ Khi,
-                                        const float* __restrict__ Klo, int vertex, T& outA,
-                                        T& outB) {
+                                        const float* __restrict__ Klo, int vertex, int jlo,
+                                        int jhi, T& outA, T& outB) {
+    if (jhi > I.n) jhi = I.n;
     const long long plane = (long long)I.n * I.ld;
     const long long row = I.k_off + (long long)i * I.ld;
     const T* va = vec + I.x_off;
@@ -176,7 +182,7 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
     T sA = 0, sB = 0;
     if (vertex == QDSE_VERTEX_BC) {
 #pragma unroll 4
-        for (int j = lane; j < I.n; j += 32) {
+        for (int j = jlo + lane; j < jhi; j += 32) {
             const T a = va[j], b = vb[j], u1 = v1[j], u2 = v2[j], u3 = v3[j];
             const T K0 = kload<T, LO>(Khi, Klo, row + j);
             const T KT = kload<T, LO>(Khi, Klo, row + plane + j);
@@ -188,7 +194,7 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
         }
     } else {
 #pragma unroll 4
-        for (int j = lane; j < I.n; j += 32) {
+        for (int j = jlo + lane; j < jhi; j += 32) {
             const T K0 = kload<T, LO>(Khi, Klo, row + j);
             const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
             sA += v2[j] * K3;
@@ -215,15 +221,16 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
                                             const T* __restrict__ dvec,
                                             const T* __restrict__ ddia, int ntot,
                                             const float* __restrict__ Khi,
-                                            const float* __restrict__ Klo, int vertex, T& outA,
-                                            T& outB) {
+                                            const float* __restrict__ Klo, int vertex, int jlo,
+                                            int jhi, T& outA, T& outB) {
+    if (jhi > I.n) jhi = I.n;
     const long long plane = (long long)I.n * I.ld;
     const long long row = I.k_off + (long long)i * I.ld;
     const int o = I.x_off;
     T sA = 0, sB = 0;
     if (vertex == QDSE_VERTEX_BC) {
 #pragma unroll 2
-        for (int j = lane; j < I.n; j += 32) {
+        for (int j = jlo + lane; j < jhi; j += 32) {
             const T a = vec[o + j], b = vec[ntot + o + j];
             const T u1 = vec[2 * ntot + o + j], u2 = vec[3 * ntot + o + j],
                     u3 = vec[4 * ntot + o + j];
@@ -243,7 +250,7 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
         }
     } else {
 #pragma unroll 4
-        for (int j = lane; j < I.n; j += 32) {
+        for (int j = jlo + lane; j < jhi; j += 32) {
             const T K0 = kload<T, LO>(Khi, Klo, row + j);
             const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
             sA += dvec[3 * ntot + o + j] * K3;
@@ -265,48 +272,174 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
     outB = sB;
 }
 
-// One tick of the batched solve: every external point of every unfinished instance advances by
-// the operation its instance's phase asks for.
-__global__ void __launch_bounds__(256) k_tick(const DevInst* __restrict__ inst,
-                                              const DevState* __restrict__ state,
-                                              const Ctl* __restrict__ ctl, Grid g, Work w,
-                                              const float* __restrict__ Khi,
-                                              const float* __restrict__ Klo, const double* A,
-                                              const double* B, int ntot) {
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__device__ __forceinline__ float4 ld4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+// One (i, j) pair of the FP32 BC sweep (T^A_ij, T^B_ij of the header comment).
+__device__ __forceinline__ void pair32(float a, float b, float u1, float u2, float u3, float K0,
+                                       float KT, float K3, float Ai, float Bi, float Pi,
+                                       float& sA, float& sB) {
+    const float da = a - Ai, db = b - Bi, sa = Ai + a;
+    const float cT = fmaf(-u1, db, -0.5f * fmaf(Pi, u2, u3) * da);
+    sA = fmaf(cT, KT, fmaf(0.5f * u2 * sa, K3, sA));
+    sB = fmaf(fmaf(u1, da, -u2 * db), KT, fmaf(1.5f * u1 * sa, K0, sB));
+}
+
+// Its tangent in direction (ea, eb, e1, e2, e3 at q_j; dAi, dBi at p_i).
+__device__ __forceinline__ void tpair32(float a, float b, float u1, float u2, float u3, float ea,
+                                        float eb, float e1, float e2, float e3, float K0,
+                                        float KT, float K3, float Ai, float Bi, float dAi,
+                                        float dBi, float Pi, float& sA, float& sB) {
+    const float da = a - Ai, db = b - Bi, sa = Ai + a;
+    const float dda = ea - dAi, ddb = eb - dBi, dsa = dAi + ea;
+    const float t = fmaf(Pi, u2, u3), dt = fmaf(Pi, e2, e3);
+    const float dcT = -e1 * db - u1 * ddb - 0.5f * (dt * da + t * dda);
+    sA = fmaf(dcT, KT, fmaf(0.5f * fmaf(e2, sa, u2 * dsa), K3, sA));
+    sB = fmaf(e1 * da + u1 * dda - e2 * db - u2 * ddb, KT, fmaf(1.5f * fmaf(e1, sa, u1 * dsa), K0, sB));
+}
+
+// FP32 sweep (or, with TAN, tangent sweep) of the kRows external points i0.. of instance I:
+// one warp, lanes over 4-node column chunks (16-byte loads) inside the union of the rows'
+// nonzero bands; the node vectors of a chunk are loaded once and used for every row.
+template <bool TAN>
+__device__ __forceinline__ void group32(int lane, const DevInst& I, int i0, const Grid& g,
+                                        const Work& w, int ntot, const float* __restrict__ Khi,
+                                        int vertex, double scale) {
+    const int nr = min(kRows, I.n - i0);
+    const long long plane = (long long)I.n * I.ld;
+    const int o = I.x_off + i0;
+    const int nv = w.nv;
+    int jlo = I.ld, jhi = 0;
+    float Ai[kRows], Bi[kRows], Pi[kRows], dAi[kRows], dBi[kRows], sA[kRows], sB[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        sA[r] = 0.f;
+        sB[r] = 0.f;
+        Ai[r] = Bi[r] = Pi[r] = dAi[r] = dBi[r] = 0.f;
+        if (r < nr) {
+            const int2 bd = g.band[o + r];
+            jlo = min(jlo, bd.x);
+            jhi = max(jhi, bd.y);
+            Ai[r] = w.x32[o + r];
+            Bi[r] = w.x32[ntot + o + r];
+            Pi[r] = g.sp32[o + r];
+            if (TAN) {
+                dAi[r] = w.d32[o + r];
+                dBi[r] = w.d32[ntot + o + r];
+            }
+        }
+    }
+    const float* vb = w.vec32 + I.v_off;
+    const float* db_ = w.dvec32 + I.v_off;
+    const float* kb = Khi + I.k_off + (long long)i0 * I.ld;
+    const bool bc = (vertex == QDSE_VERTEX_BC);
+    for (int c = jlo + 4 * lane; c < jhi; c += 128) {
+        const float4 a = ld4(vb + c), b = ld4(vb + nv + c), u1 = ld4(vb + 2 * nv + c),
+                     u2 = ld4(vb + 3 * nv + c), u3 = ld4(vb + 4 * nv + c);
+        float4 ea, eb, e1, e2, e3;
+        if (TAN) {
+            ea = ld4(db_ + c);
+            eb = ld4(db_ + nv + c);
+            e1 = ld4(db_ + 2 * nv + c);
+            e2 = ld4(db_ + 3 * nv + c);
+            e3 = ld4(db_ + 4 * nv + c);
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            if (r < nr) {
+                const float* kr = kb + (long long)r * I.ld + c;
+                const float4 K0 = ld4(kr), K3 = ld4(kr + 2 * plane);
+                if (bc) {
+                    const float4 KT = ld4(kr + plane);
+                    if (!TAN) {
+                        pair32(a.x, b.x, u1.x, u2.x, u3.x, K0.x, KT.x, K3.x, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
+                        pair32(a.y, b.y, u1.y, u2.y, u3.y, K0.y, KT.y, K3.y, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
+                        pair32(a.z, b.z, u1.z, u2.z, u3.z, K0.z, KT.z, K3.z, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
+                        pair32(a.w, b.w, u1.w, u2.w, u3.w, K0.w, KT.w, K3.w, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
+                    } else {
+                        tpair32(a.x, b.x, u1.x, u2.x, u3.x, ea.x, eb.x, e1.x, e2.x, e3.x, K0.x, KT.x, K3.x, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
+                        tpair32(a.y, b.y, u1.y, u2.y, u3.y, ea.y, eb.y, e1.y, e2.y, e3.y, K0.y, KT.y, K3.y, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
+                        tpair32(a.z, b.z, u1.z, u2.z, u3.z, ea.z, eb.z, e1.z, e2.z, e3.z, K0.z, KT.z, K3.z, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
+                        tpair32(a.w, b.w, u1.w, u2.w, u3.w, ea.w, eb.w, e1.w, e2.w, e3.w, K0.w, KT.w, K3.w, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
+                    }
+                } else {
+                    const float4 p2 = TAN ? e2 : u2, p1 = TAN ? e1 : u1;
+                    sA[r] += p2.x * K3.x + p2.y * K3.y + p2.z * K3.z + p2.w * K3.w;
+                    sB[r] += 3.f * (p1.x * K0.x + p1.y * K0.y + p1.z * K0.z + p1.w * K0.w);
+                }
+            }
+        }
+    }
+    float myA = 0.f, myB = 0.f;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const float ra = warp_sum(sA[r]), rb = warp_sum(sB[r]);
+        if (lane == r) {
+            myA = ra;
+            myB = rb;
+        }
+    }
+    if (lane < nr) {
+        const int i = i0 + lane, gi = I.x_off + i;
+        if (bc && I.mode == QDSE_COLLOCATED) {
+            const float KTd = Khi[I.k_off + (long long)i * I.ld + plane + i];
+            const float u1 = vb[2 * nv + i], u2 = vb[3 * nv + i];
+            const float dA = w.dia32[gi], dB = w.dia32[ntot + gi];
+            const float P = g.sp32[gi];
+            if (!TAN) {
+                myA += (-u1 * dB - P * u2 * dA) * KTd;
+                myB += (u1 * dA - u2 * dB) * KTd;
+            } else {
+                const float e1 = db_[2 * nv + i], e2 = db_[3 * nv + i];
+                const float edA = w.ddia32[gi], edB = w.ddia32[ntot + gi];
+                myA += (-e1 * dB - u1 * edB - P * (e2 * dA + u2 * edA)) * KTd;
+                myB += (e1 * dA + u1 * edA - e2 * dB - u2 * edB) * KTd;
+            }
+        }
+        if (!TAN) {
+            w.xn32[gi] = (float)(1.0 + scale * (double)myA / g.sp[gi]);
+            w.xn32[ntot + gi] = (float)(I.m + scale * (double)myB);
+        } else {
+            w.xn32[gi] = (float)(scale * (double)myA / g.sp[gi]);
+            w.xn32[ntot + gi] = (float)(scale * (double)myB);
+        }
+    }
+}
+
+// One tick of the batched solve: every group of kRows external points of every unfinished
+// instance advances by the operation its instance's phase asks for (one warp per group).
+__global__ void __launch_bounds__(256, 2) k_tick(const DevInst* __restrict__ inst,
+                                                 const DevState* __restrict__ state,
+                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                 const float* __restrict__ Khi,
+                                                 const float* __restrict__ Klo, const double* A,
+                                                 const double* B, int ntot, int ngroups) {
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= ntot) return;
-    const int b = g.row_inst[r];
-    const int phase = state[b].phase;
+    if (gw >= ngroups) return;
+    const int2 grp = g.groups[gw];
+    const int phase = state[grp.x].phase;
     if (phase == PH_DONE) return;
-    const DevInst I = inst[b];
-    const int i = r - I.x_off;
+    const DevInst I = inst[grp.x];
     const int vertex = ctl->vertex;
     const double scale = ctl->kappa * I.D;
     if (phase == PH_PICARD32) {
-        float sA, sB;
-        row_map<float, false>(lane, I, i, g.sp32[r], w.x32[r], w.x32[ntot + r], w.vec32, w.dia32,
-                              ntot, Khi, Klo, vertex, sA, sB);
-        if (lane == 0) {
-            w.xn32[r] = (float)(1.0 + scale * (double)sA / g.sp[r]);
-            w.xn32[ntot + r] = (float)(I.m + scale * (double)sB);
-        }
+        group32<false>(lane, I, grp.y, g, w, ntot, Khi, vertex, scale);
     } else if (phase == PH_TANGENT32) {
-        float sA, sB;
-        row_tangent<float, false>(lane, I, i, g.sp32[r], w.x32[r], w.x32[ntot + r], w.d32[r],
-                                  w.d32[ntot + r], w.vec32, w.dia32, w.dvec32, w.ddia32, ntot,
-                                  Khi, Klo, vertex, sA, sB);
-        if (lane == 0) {
-            w.xn32[r] = (float)(scale * (double)sA / g.sp[r]);
-            w.xn32[ntot + r] = (float)(scale * (double)sB);
-        }
+        group32<true>(lane, I, grp.y, g, w, ntot, Khi, vertex, scale);
     } else {  // PH_RESID64 or PH_PICARD64 on the precomputed double-float kernels
-        double sA, sB;
-        row_map<double, true>(lane, I, i, g.sp[r], A[r], B[r], w.vec64, w.dia64, ntot, Khi, Klo,
-                              vertex, sA, sB);
-        if (lane == 0) {
-            w.xn64[r] = 1.0 + scale * sA / g.sp[r];
-            w.xn64[ntot + r] = I.m + scale * sB;
+        const int nr = min(kRows, I.n - grp.y);
+        for (int rr = 0; rr < nr; ++rr) {
+            const int i = grp.y + rr, r = I.x_off + i;
+            const int2 bd = g.band[r];
+            double sA, sB;
+            row_map<double, true>(lane, I, i, g.sp[r], A[r], B[r], w.vec64, w.dia64, ntot, Khi,
+                                  Klo, vertex, bd.x, bd.y, sA, sB);
+            if (lane == 0) {
+                w.xn64[r] = 1.0 + scale * sA / g.sp[r];
+                w.xn64[ntot + r] = I.m + scale * sB;
+            }
         }
     }
 }
@@ -395,12 +528,13 @@ __global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ i
 __device__ void prepare_phase(int phase, const DevInst& I, const Grid& g, const Work& w, int ntot,
                               const double* A, const double* B) {
     if (phase == PH_PICARD32) {
-        prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.dia32);
+        prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.nv, I.v_off,
+                                      w.dia32);
     } else if (phase == PH_RESID64 || phase == PH_PICARD64) {
-        prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, w.dia64);
+        prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, ntot, I.x_off, w.dia64);
     } else if (phase == PH_TANGENT32) {
         prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
-                                             w.d32 + ntot, w.dvec32, w.ddia32);
+                                             w.d32 + ntot, w.dvec32, w.nv, I.v_off, w.ddia32);
     }
 }
 
@@ -437,14 +571,28 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
 // Advance one instance after a tick.  One block (256 threads) per instance.
 __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst, DevState* state,
                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
-                                                double* A, double* B, int ntot, int* count) {
+                                                double* A, double* B, int ntot, int* count,
+                                                unsigned long long* ctr) {
     __shared__ double sh[32];
-    __shared__ int s_next;
     const int b = blockIdx.x;
     DevState s = state[b];
     if (s.phase == PH_DONE) return;
     const DevInst I = inst[b];
     const Ctl C = *ctl;
+    if (threadIdx.x == 0 && ctr) {
+        // work counters of the sweep this update completes: instance-sweeps by precision,
+        // algorithmic bytes (kernel rows + per-node vectors + own values and outputs) and
+        // BC-kernel evaluations n_p * n_q * n_theta
+        const unsigned long long n = (unsigned long long)I.n;
+        unsigned long long bytes;
+        if (s.phase == PH_PICARD32) bytes = 12ull * n * n + 36ull * n;
+        else if (s.phase == PH_TANGENT32) bytes = 12ull * n * n + 64ull * n;
+        else if (C.precision == QDSE_FP64) bytes = 56ull * n;
+        else bytes = 24ull * n * n + 72ull * n;
+        atomicAdd(ctr + ((s.phase == PH_PICARD32 || s.phase == PH_TANGENT32) ? 0 : 1), 1ull);
+        atomicAdd(ctr + 2, bytes);
+        atomicAdd(ctr + 3, n * n * (unsigned long long)I.nt);
+    }
     const int o = I.x_off;
     int next = s.phase;
     bool done = false;
@@ -522,7 +670,8 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
                     w.x32[ntot + gj] = (float)B[gj];
                 }
                 __syncthreads();
-                prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.dia32);
+                prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.nv,
+                                              I.v_off, w.dia32);
                 next = PH_TANGENT32;
                 s.inner = 0;
             }
@@ -583,11 +732,11 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
             prepare_phase(next, I, g, w, ntot, A, B);
         } else {
             prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
-                                                 w.d32 + ntot, w.dvec32, w.ddia32);
+                                                 w.d32 + ntot, w.dvec32, w.nv, I.v_off,
+                                                 w.ddia32);
         }
     }
     if (threadIdx.x == 0) {
-        s_next = next;
         s.phase = next;
         s.status = status;
         if (next == PH_PICARD32) s.loc = 1;
@@ -627,8 +776,10 @@ __global__ void k_finish(const DevInst* __restrict__ inst, const DevState* __res
 __global__ void k_prep64(const DevInst* __restrict__ inst, Grid g, Work w, const double* A,
                          const double* B, const double* vA, const double* vB, int ntot) {
     const DevInst I = inst[blockIdx.x];
-    prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, w.dia64);
-    if (vA) prepare_tangent<double, double, double>(I, g, ntot, A, B, vA, vB, w.dvec64, w.ddia64);
+    prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, ntot, I.x_off, w.dia64);
+    if (vA)
+        prepare_tangent<double, double, double>(I, g, ntot, A, B, vA, vB, w.dvec64, ntot, I.x_off,
+                                                w.ddia64);
 }
 
 // F(x) (homogeneous = 0) or F(x) - x0 (homogeneous = 1) on the double-float kernels.
@@ -644,8 +795,9 @@ __global__ void __launch_bounds__(256) k_row_map64(const DevInst* __restrict__ i
     const DevInst I = inst[g.row_inst[r]];
     const int i = r - I.x_off;
     double sA, sB;
+    const int2 bd = g.band[r];
     row_map<double, true>(lane, I, i, g.sp[r], A[r], B[r], w.vec64, w.dia64, ntot, Khi, Klo,
-                          ctl->vertex, sA, sB);
+                          ctl->vertex, bd.x, bd.y, sA, sB);
     if (lane == 0) {
         const double scale = ctl->kappa * I.D;
         FA[r] = (homogeneous ? 0.0 : 1.0) + scale * sA / g.sp[r];
@@ -666,8 +818,10 @@ __global__ void __launch_bounds__(256) k_row_jvp64(const DevInst* __restrict__ i
     const DevInst I = inst[g.row_inst[r]];
     const int i = r - I.x_off;
     double sA, sB;
+    const int2 bd = g.band[r];
     row_tangent<double, true>(lane, I, i, g.sp[r], A[r], B[r], vA[r], vB[r], w.vec64, w.dia64,
-                              w.dvec64, w.ddia64, ntot, Khi, Klo, ctl->vertex, sA, sB);
+                              w.dvec64, w.ddia64, ntot, Khi, Klo, ctl->vertex, bd.x, bd.y, sA,
+                              sB);
     if (lane == 0) {
         const double scale = ctl->kappa * I.D;
         JA[r] = scale * sA / g.sp[r];
@@ -701,58 +855,72 @@ static inline int row_blocks(int ntot) { return (ntot + 7) / 8; }
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0) {
     cudaError_t e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
+    prof_begin(c, PK_OTHER);
     k_init_state<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
                                                    c->work, A, B, c->n_total, phase0);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B) {
-    k_tick<<<row_blocks(c->n_total), 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl,
-                                                          c->grid, c->work, c->d_Khi, c->d_Klo, A,
-                                                          B, c->n_total);
+    prof_begin(c, PK_SWEEP);
+    k_tick<<<(c->n_groups + 7) / 8, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl,
+                                                         c->grid, c->work, c->d_Khi, c->d_Klo, A,
+                                                         B, c->n_total, c->n_groups);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
+    prof_begin(c, PK_UPDATE);
     k_update<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
-                                               A, B, c->n_total, c->d_count);
+                                               A, B, c->n_total, c->d_count, c->d_sweeps);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_otf(qdse_ctx* c, const double* A, const double* B, double* FA,
                              double* FB, int only_active) {
     const size_t smem = (4 * (size_t)c->max_nt + 32) * sizeof(double);
+    prof_begin(c, PK_SWEEP);
     k_sweep_otf<<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
                                                       c->work, A, B, FA, FB, c->n_total,
                                                       only_active);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish(qdse_ctx* c, double* A, double* B, double* change_out, int* iters,
                           int* status) {
+    prof_begin(c, PK_OTHER);
     k_finish<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, A, B, c->n_total,
                                                change_out, iters, status, 0);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish_timeout(qdse_ctx* c, double* A, double* B, double* change_out,
                                   int* iters, int* status) {
+    prof_begin(c, PK_OTHER);
     k_finish<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, A, B, c->n_total,
                                                change_out, iters, status, 1);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep64(qdse_ctx* c, const double* A, const double* B, const double* vA,
                           const double* vB) {
+    prof_begin(c, PK_OTHER);
     k_prep64<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->grid, c->work, A, B, vA, vB,
                                                c->n_total);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
@@ -761,13 +929,17 @@ cudaError_t launch_residual_fp64(qdse_ctx* c, const double* A, const double* B, 
                                  const float* Klo) {
     cudaError_t e = launch_prep64(c, A, B, nullptr, nullptr);
     if (e != cudaSuccess) return e;
+    prof_begin(c, PK_SWEEP);
     k_row_map64<<<row_blocks(c->n_total), 256, 0, c->stream>>>(
         c->d_inst, c->d_ctl, c->grid, c->work, Khi, Klo, A, B, FA, FB, c->n_total, homogeneous);
     c->launches++;
+    prof_end(c);
     e = cudaGetLastError();
     if (e != cudaSuccess || !rel) return e;
+    prof_begin(c, PK_OTHER);
     k_rel64<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, A, B, FA, FB, rel);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
@@ -775,17 +947,21 @@ cudaError_t launch_jvp(qdse_ctx* c, const double* A, const double* B, const doub
                        const double* vB, double* JA, double* JB) {
     cudaError_t e = launch_prep64(c, A, B, vA, vB);
     if (e != cudaSuccess) return e;
+    prof_begin(c, PK_SWEEP);
     k_row_jvp64<<<row_blocks(c->n_total), 256, 0, c->stream>>>(
         c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, vA, vB, JA, JB,
         c->n_total);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rel64(qdse_ctx* c, const double* A, const double* B, const double* FA,
                          const double* FB, double* rel) {
+    prof_begin(c, PK_OTHER);
     k_rel64<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, A, B, FA, FB, rel);
     c->launches++;
+    prof_end(c);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,8 @@ struct DevInst {          // per-instance descriptor, read-only during a solve
     long long k_off;      // first element of plane 0 in the kernel pool
     int ld;               // row stride of the kernel planes (n rounded up to 4)
     int mode;             // QDSE_COLLOCATED / QDSE_STAGGERED
+    int v_off;            // first element of this instance in the padded FP32 node vectors
+    int pad_;
     double D, omega, m;   // current parameters
 };
 
@@ -79,11 +81,14 @@ struct Work {
     double* d64;    // [2] correction delta (FP64 master)
     double* vec64;  // [5] per internal node: a, b, u1 = e b, u2 = e a, u3 = e a Q (FP64)
     double* dia64;  // [2] diagonal difference quotients dA/ds, dB/ds at p_i (collocated)
+    int nv;         // length of one component of vec32 / dvec32 (sum of ld, multiple of 4)
     float* x32;     // [2] FP32 iterate
     float* xn32;    // [2] FP32 sweep output (F(x) or J delta)
-    float* vec32;   // [5] FP32 copies of vec64 entries at the current iterate
+    float* vec32;   // [5] FP32 copies of vec64 entries at the current iterate, padded layout:
+                    //     component c of node j of instance b at [c * nv + v_off_b + j], zero in
+                    //     the padding so that 16-byte loads of 4 nodes stay aligned
     float* dia32;   // [2]
-    float* dvec32;  // [5] tangent: delta a, delta b, delta u1, delta u2, delta u3
+    float* dvec32;  // [5] tangent: delta a, delta b, delta u1, delta u2, delta u3 (padded layout)
     float* ddia32;  // [2] tangent: stencil of delta
     float* d32;     // [2] FP32 copy of the correction (delta A_i, delta B_i at p_i)
     double* dvec64; // [5] FP64 tangent vectors (Jacobian-vector products)
@@ -108,11 +113,16 @@ struct Grid {              // FP64 grid arrays on the device (global point index
     double* s2;            // 1 - z^2
     double* wz;            // angular weights
     int* row_inst;         // instance of every global point
+    int2* band;            // per external point: [jlo, jhi) outside which every kernel entry of
+                           // the row is exactly zero (jlo, jhi multiples of 4, jhi <= ld)
+    int2* groups;          // (instance, first row) of every group of kRows consecutive rows
 };
+
+constexpr int kRows = 4;   // external points per warp in the batched sweeps
 
 struct HostInst {
     qdse_grid g;
-    int x_off, t_off, ld;
+    int x_off, t_off, ld, v_off;
     long long k_off;
 };
 
@@ -121,6 +131,8 @@ struct HostInst {
 struct qdse_ctx {
     int n_inst = 0;
     int n_total = 0;
+    int nv_total = 0;        // sum of ld (padded FP32 vector length)
+    int n_groups = 0;        // row groups of kRows
     int t_total = 0;
     long long k_total = 0;   // floats per kernel plane set (sum of 3 n ld)
     int max_n = 0, max_nt = 0;
@@ -140,7 +152,8 @@ struct qdse_ctx {
     float* d_Kwhi = nullptr;  // omega-derivative kernels (allocated on first adjoint)
     float* d_Kwlo = nullptr;
     int* d_count = nullptr;   // [1] number of unfinished instances after the last update
-    unsigned long long* d_sweeps = nullptr;  // [2] instance-sweeps in FP32 / FP64 of the call
+    unsigned long long* d_sweeps = nullptr;  // [4] FP32 / FP64 instance-sweeps, algorithmic
+                                             // bytes of the sweeps, BC-kernel evaluations
     double* d_hostA = nullptr;  // staging for qdse_solve_host: [2 n_total] doubles
     int* d_hostI = nullptr;     // [2 n_inst] ints (iterations, status)
     int* h_count = nullptr;   // pinned mirror
@@ -148,12 +161,23 @@ struct qdse_ctx {
 
     std::string err;
     long long launches = 0, sweeps32 = 0, sweeps64 = 0, polls = 0;
+    // optional CUDA-event timing of every launch, by kind (see qdse::ProfKind)
+    int profiling = 0;
+    struct ProfRec { int kind; cudaEvent_t a, b; };
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfRec> prof;
     int k_valid_for = 0;     // 1 if the kernel pool matches the parameters in d_inst (w, grid)
     int kw_valid = 0;
     std::vector<double> k_omega;  // omega each instance's kernels were built for
 };
 
 namespace qdse {
+
+enum ProfKind : int { PK_PRECOMPUTE = 0, PK_SWEEP = 1, PK_UPDATE = 2, PK_OTHER = 3, PK_COUNT = 4 };
+// Record CUDA events around a launch when profiling is on (no-ops otherwise).
+void prof_begin(qdse_ctx* c, int kind);
+void prof_end(qdse_ctx* c);
 
 // ---- host grid construction (grid.cpp) -------------------------------------------------------
 int gauss_legendre_nodes(int n, double* t, double* v);

@@ -30,7 +30,7 @@ EXPORTS = ("qdse_default_options", "qdse_create", "qdse_create_ragged", "qdse_de
            "qdse_last_error", "qdse_sizes", "qdse_layout", "qdse_grid_nodes", "qdse_set_options",
            "qdse_iterate", "qdse_solve", "qdse_solve_host", "qdse_residual", "qdse_jvp",
            "qdse_vjp", "qdse_adjoint", "qdse_condensate", "qdse_condensate_vjp",
-           "qdse_last_stats")
+           "qdse_last_stats", "qdse_last_work", "qdse_set_profiling", "qdse_profile")
 
 
 class qdse_grid(ctypes.Structure):
@@ -91,6 +91,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qdse_condensate_vjp": (ip, [vp, vp, vp, vp, vp, vp]),
         "qdse_last_stats": (ip, [vp, P(ctypes.c_longlong), P(ctypes.c_longlong),
                                  P(ctypes.c_longlong), P(ctypes.c_longlong)]),
+        "qdse_last_work": (ip, [vp, P(dp), P(dp)]),
+        "qdse_set_profiling": (ip, [vp, ip]),
+        "qdse_profile": (ip, [vp, P(dp), P(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +270,21 @@ class Context:
         self._sync_stream()
         self._raise(self.lib.qdse_condensate_vjp(self.ptr, _ptr(A), _ptr(B), _ptr(cbar), _ptr(gA),
                                                  _ptr(gB)))
+
+    def qdse_last_work(self) -> dict:
+        b, e = ctypes.c_double(), ctypes.c_double()
+        self._raise(self.lib.qdse_last_work(self.ptr, ctypes.byref(b), ctypes.byref(e)))
+        return {"sweep_bytes": b.value, "kernel_evals": e.value}
+
+    def qdse_set_profiling(self, on: bool):
+        self._raise(self.lib.qdse_set_profiling(self.ptr, int(bool(on))))
+
+    def qdse_profile(self) -> dict:
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
+        self._raise(self.lib.qdse_profile(self.ptr, ms, n))
+        names = ("precompute", "sweep", "update", "other")
+        return {k: {"ms": ms[i], "launches": n[i]} for i, k in enumerate(names)}
 
     def qdse_last_stats(self) -> dict:
         v = [ctypes.c_longlong() for _ in range(4)]

@@ -284,13 +284,16 @@ def test_condensate_and_its_cotangent():
     gA = dev(np.zeros(inst.n_p)); gB = dev(np.zeros(inst.n_p))
     ctx.qdse_condensate_vjp(dev(Ar), dev(Br), dev([1.0]), gA, gB)
     h = 1e-6
-    for k in (0, 20, 40):
-        for arr, g in ((Ar, gA), (Br, gB)):
+    for arr, g in ((Ar, gA), (Br, gB)):
+        gh = host(g)
+        scale = np.abs(gh).max()
+        for k in (0, 20, 30, 40, 50):
             xp = arr.copy(); xp[k] += h; xm = arr.copy(); xm[k] -= h
             a1 = (xp, Br) if arr is Ar else (Ar, xp)
             a2 = (xm, Br) if arr is Ar else (Ar, xm)
             fd = (O.condensate(problem(inst), *a1) - O.condensate(problem(inst), *a2)) / (2 * h)
-            assert host(g)[k] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+            # central differences carry ~1e-16/h rounding: compare on the gradient's own scale
+            assert abs(gh[k] - fd) < 1e-6 * scale, (k, gh[k], fd)
 
 
 # ------------------------------------------------------------------------------------------------
