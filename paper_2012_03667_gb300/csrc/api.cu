@@ -4,7 +4,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <string>
@@ -104,7 +106,9 @@ void free_ctx(qdse_ctx* c) {
                     c->work.dvec32, c->work.ddia32, c->work.d32, c->work.dvec64, c->work.ddia64,
                     c->work.lam, c->work.lamn, c->d_Khi, c->d_Klo, c->d_Kwhi, c->d_Kwlo,
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
-                    c->grid.groups};
+                    c->grid.groups, c->grid.nnz, c->work.items, c->work.item_count,
+                    c->work.work_ctr, c->grid.gdesc, c->grid.gphase, c->work.ilist,
+                    c->work.glist, c->work.lcount};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -140,7 +144,7 @@ qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
         d.ld = h.ld;
         d.mode = h.g.grid_mode;
         d.v_off = h.v_off;
-        d.pad_ = 0;
+        d.g_off = h.g_off;
         d.D = p[b].D;
         d.omega = p[b].omega;
         d.m = p[b].m;
@@ -154,6 +158,7 @@ qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
 qdse_status ensure_kernels(qdse_ctx* c, const qdse_params* p, bool rebuild) {
     if (!rebuild) return QDSE_OK;
     QCHECK(c, launch_precompute(c, false), "precompute kernels");
+    QCHECK(c, launch_group_bands(c), "group bands");
     for (int b = 0; b < c->n_inst; ++b) c->k_omega[b] = p[b].omega;
     c->k_valid_for = 1;
     c->kw_valid = 0;
@@ -193,6 +198,7 @@ void reset_stats(qdse_ctx* c) {
 qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool& timed_out) {
     timed_out = false;
     const bool otf = (c->opt.precision == QDSE_FP64);
+    QCHECK(c, cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int), c->stream), "reset flags");
     const auto t0 = std::chrono::steady_clock::now();
     long long done_ticks = 0;
     int chunk = 4;
@@ -200,23 +206,32 @@ qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool
         const long long todo = (n_ticks >= 0) ? n_ticks - done_ticks : chunk;
         if (n_ticks >= 0 && todo <= 0) break;
         for (long long t = 0; t < todo; ++t) {
+            // the poll counts the instances still running after the chunk's last tick
+            if (t == todo - 1)
+                QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
             if (otf) {
                 QCHECK(c, launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1),
                        "fp64 sweep");
+                QCHECK(c, launch_update(c, A, B), "update");
+            } else if (c->sweep_kind == 1) {
+                QCHECK(c, launch_sweep32_tma(c, A, B), "sweep");
+                QCHECK(c, launch_update(c, A, B), "update");
             } else {
                 QCHECK(c, launch_tick(c, A, B), "sweep");
+                QCHECK(c, launch_update(c, A, B), "update");
             }
-            if (t == todo - 1)
-                QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
-            QCHECK(c, launch_update(c, A, B), "update");
         }
         done_ticks += todo;
         if (n_ticks >= 0) break;
-        QCHECK(c, cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost,
+        QCHECK(c, cudaMemcpyAsync(c->h_count, c->d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                   c->stream),
                "poll");
         QCHECK(c, cudaStreamSynchronize(c->stream), "poll sync");
         c->polls++;
+        if (c->h_count[1] != 0) {
+            timed_out = true;
+            return fail(c, QDSE_ERR_TIMEOUT, "a bounded device wait ran out in the sweep kernel");
+        }
         if (*c->h_count == 0) break;
         if (c->opt.time_limit > 0) {
             const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -275,6 +290,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         }
         h.t_off = t_of[h.g.n_theta];
         if (h.g.n_p > c->max_n) c->max_n = h.g.n_p;
+        if (h.ld > c->ld_max) c->ld_max = h.ld;
         if (h.g.n_theta > c->max_nt) c->max_nt = h.g.n_theta;
         if (h.g.grid_mode == QDSE_STAGGERED) c->any_staggered = true;
     }
@@ -289,9 +305,28 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     std::vector<double> sp(N), sq(N), W(N), wt(N), stc(3 * (size_t)N), rsp(N), rsq(N);
     std::vector<int> sta(N), row_inst(N);
     std::vector<int2> groups;
+    std::vector<GroupDesc> gdesc;
     groups.reserve(ng);
-    for (int b = 0; b < n_inst; ++b)
-        for (int i0 = 0; i0 < c->hinst[b].g.n_p; i0 += kRows) groups.push_back(make_int2(b, i0));
+    gdesc.reserve(ng);
+    for (int b = 0; b < n_inst; ++b) {
+        HostInst& h = c->hinst[b];
+        h.g_off = (int)groups.size();
+        for (int i0 = 0; i0 < h.g.n_p; i0 += kRows) {
+            groups.push_back(make_int2(b, i0));
+            GroupDesc d{};
+            d.b = b;
+            d.i0 = i0;
+            d.nr = std::min(kRows, h.g.n_p - i0);
+            d.jlo = 0;
+            d.jhi = h.ld;  // narrowed to the band union after every kernel precompute
+            d.v_off = h.v_off;
+            d.x_off = h.x_off;
+            d.ld = h.ld;
+            d.kbase = h.k_off + (long long)i0 * 3 * h.ld;
+            d.plane = h.ld;
+            gdesc.push_back(d);
+        }
+    }
     std::vector<float> sp32(N), sq32(N);
     for (int b = 0; b < n_inst; ++b) {
         const HostInst& h = c->hinst[b];
@@ -340,7 +375,29 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->grid.wz, t);
     CALLOC(c->grid.row_inst, N);
     CALLOC(c->grid.band, N);
+    CALLOC(c->grid.nnz, n_inst);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, dev);
+        long long it64 = 0;
+        for (int b = 0; b < n_inst; ++b) it64 += (c->hinst[b].g.n_p + 63) / 64;
+        c->work.rb = (it64 >= 4LL * (c->n_sms > 0 ? c->n_sms : 152)) ? 64 : 8;
+        long long mi = 0;
+        for (int b = 0; b < n_inst; ++b) mi += (c->hinst[b].g.n_p + c->work.rb - 1) / c->work.rb;
+        c->work.max_items = (int)mi;
+    }
+    CALLOC(c->work.items, 2 * (size_t)c->work.max_items);
+    CALLOC(c->work.item_count, 2);
+    CALLOC(c->work.work_ctr, 1);
+    CALLOC(c->work.ilist, 3 * (size_t)n_inst);
+    CALLOC(c->work.glist, 3 * (size_t)ng);
+    CALLOC(c->work.lcount, 6);
+    c->work.n_inst = n_inst;
+    c->work.n_groups = ng;
     CALLOC(c->grid.groups, ng);
+    CALLOC(c->grid.gdesc, ng);
+    CALLOC(c->grid.gphase, ng);
     CALLOC(c->work.xn64, 2 * (size_t)N);
     CALLOC(c->work.r64, 2 * (size_t)N);
     CALLOC(c->work.d64, 2 * (size_t)N);
@@ -359,12 +416,13 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->work.lamn, 2 * (size_t)N);
     CALLOC(c->d_Khi, (size_t)k);
     CALLOC(c->d_Klo, (size_t)k);
-    CALLOC(c->d_count, 1);
+    CALLOC(c->d_count, 2);
     CALLOC(c->d_sweeps, 4);
     CALLOC(c->d_hostA, 2 * (size_t)N);
     CALLOC(c->d_hostI, 2 * (size_t)n_inst);
 #undef CALLOC
-    cudaError_t e = cudaMallocHost((void**)&c->h_count, sizeof(int));
+    c->d_err = c->d_count + 1;
+    cudaError_t e = cudaMallocHost((void**)&c->h_count, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_inst_pinned, sizeof(DevInst) * n_inst);
     if (e != cudaSuccess) {
         qdse_status s = cuda_fail(nullptr, e, "pinned host allocation");
@@ -381,7 +439,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         {c->grid.y, y.data(), sizeof(double) * t}, {c->grid.s2, s2.data(), sizeof(double) * t},
         {c->grid.wz, wz.data(), sizeof(double) * t},
         {c->grid.row_inst, row_inst.data(), sizeof(int) * N},
-        {c->grid.groups, groups.data(), sizeof(int2) * ng}};
+        {c->grid.groups, groups.data(), sizeof(int2) * ng},
+        {c->grid.gdesc, gdesc.data(), sizeof(GroupDesc) * ng}};
     for (auto& u : ups) {
         e = cudaMemcpy(u.d, u.h, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -391,6 +450,14 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         }
     }
     c->work.nv = v;
+    c->use_tma = (c->n_sms > 0) && configure_sweep32_tma(c->ld_max) == cudaSuccess;
+    cudaGetLastError();
+    {
+        // sweep kernel: the row-group kernel by default; QDSE_SWEEP=items selects the bulk-copy
+        // work-list kernel (same results, kept for comparison on new hardware)
+        const char* k = std::getenv("QDSE_SWEEP");
+        c->sweep_kind = (k && std::string(k) == "items" && c->use_tma) ? 1 : 0;
+    }
     // zero the padding of the node vectors once; descriptors get their layout now and their
     // parameters on every call
     e = cudaMemset(c->work.vec32, 0, sizeof(float) * 5 * (size_t)v);
@@ -656,6 +723,7 @@ qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, con
     }
     if (rebuild || !c->kw_valid) {
         QCHECK(c, launch_precompute(c, true), "precompute kernels and omega derivatives");
+        QCHECK(c, launch_group_bands(c), "group bands");
         for (int b = 0; b < c->n_inst; ++b) c->k_omega[b] = p[b].omega;
         c->k_valid_for = 1;
         c->kw_valid = 1;

@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     const DevInst I = inst[bi];
     const int l = r - I.x_off;
     const int o = I.x_off;
-    const long long plane = (long long)I.n * I.ld;
-    const long long row = I.k_off + (long long)l * I.ld;
+    const long long plane = I.ld;  // planes of a row are adjacent
+    const long long row = I.k_off + (long long)l * 3 * I.ld;
     const double* va = w.vec64 + o;
     const double* vb = w.vec64 + ntot + o;
     const double* v1 = w.vec64 + 2 * ntot + o;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
         // removable-limit terms of every row i whose value depends on x_l
         const int i0 = l - 2 < 0 ? 0 : l - 2, i1 = l + 2 > I.n - 1 ? I.n - 1 : l + 2;
         for (int i = i0; i <= i1; ++i) {
-            const long long rowi = I.k_off + (long long)i * I.ld;
+            const long long rowi = I.k_off + (long long)i * 3 * I.ld;
             const double KTd = (double)Khi[rowi + plane + i] + (double)Klo[rowi + plane + i];
             const double ai = al[i], bi = be[i];
             const double u1 = v1[i], u2 = v2[i], Pi = sp[i];
@@ -229,7 +229,7 @@ __global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* sta
         if (ctr) {
             const unsigned long long n = (unsigned long long)I.n;
             atomicAdd(ctr + 1, 1ull);
-            atomicAdd(ctr + 2, 24ull * n * n + 96ull * n);
+            atomicAdd(ctr + 2, 24ull * n * n + 96ull * n);  // the transposed sweep reads whole rows
             atomicAdd(ctr + 3, n * n * (unsigned long long)I.nt);
         }
         s.iters += 1;

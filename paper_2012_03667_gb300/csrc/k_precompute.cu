@@ -54,8 +54,8 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
     const double iw2 = 1.0 / (w * w);
     const double pref = 8.0 * kPi * kPi / (w * w * w * w);
     const double fw0 = -4.0 / w, fw1 = 2.0 / (w * w * w);
-    const long long plane = (long long)I.n * I.ld;
-    const long long row = I.k_off + (long long)i * I.ld;
+    const long long plane = I.ld;  // planes of a row are adjacent
+    const long long row = I.k_off + (long long)i * 3 * I.ld;
 
     for (int j = threadIdx.x; j < I.ld; j += blockDim.x) {
         double K0 = 0.0, KT = 0.0, K3 = 0.0, W0 = 0.0, WT = 0.0, W3 = 0.0;
@@ -126,11 +126,15 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
             if (hi > I.ld) hi = I.ld;
         }
         g.band[r] = make_int2(lo, hi);
+        atomicAdd(g.nnz + b, (unsigned long long)(hi - lo));
     }
 }
 
 cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
     const size_t smem = 4 * sizeof(double) * (size_t)c->max_nt;
+    cudaError_t e0 = cudaMemsetAsync(c->grid.nnz, 0, sizeof(unsigned long long) * c->n_inst,
+                                     c->stream);
+    if (e0 != cudaSuccess) return e0;
     prof_begin(c, PK_PRECOMPUTE);
     if (with_w) {
         k_precompute<true><<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->grid, c->d_Khi,

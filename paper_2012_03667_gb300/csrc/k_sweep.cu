@@ -19,6 +19,7 @@
 // The vectors (a, b, u1, u2, u3) are formed once per sweep per instance (O(N)) by the update
 // kernel, which also owns the convergence test (Eq. jifenab2, relative form) and the phase
 // transitions of the mixed-precision solve.
+#include <algorithm>
 #include <cfloat>
 
 #include "qdse_internal.h"
@@ -72,6 +73,24 @@ __device__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// The set of threads that updates one instance: a whole block, or one warp (fused into a sweep).
+struct BlockTeam {
+    double* sh;
+    __device__ int tid() const { return threadIdx.x; }
+    __device__ int size() const { return blockDim.x; }
+    __device__ void sync() const { __syncthreads(); }
+    __device__ double max(double v) const { return block_max(v, sh); }
+    __device__ bool leader() const { return threadIdx.x == 0; }
+};
+
+struct WarpTeam {
+    __device__ int tid() const { return threadIdx.x & 31; }
+    __device__ int size() const { return 32; }
+    __device__ void sync() const { __syncwarp(); }
+    __device__ double max(double v) const { return warp_max(v); }
+    __device__ bool leader() const { return (threadIdx.x & 31) == 0; }
+};
+
 template <typename T, bool LO>
 __device__ __forceinline__ T kload(const float* __restrict__ hi, const float* __restrict__ lo,
                                    long long idx) {
@@ -104,8 +123,13 @@ __device__ __forceinline__ double at_q(const S* F, int gj, double wt) {
 // layout in use; the FP32 vectors are padded, the FP64 ones use the global point index).
 template <typename S, typename T>
 __device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const S* xa,
-                                const S* xb, T* vec, int vs, int vb, T* dia) {
-    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                                const S* xb, T* vec, int vs, int vb, T* dia, int tid = -1,
+                                int nth = 0) {
+    if (tid < 0) {
+        tid = threadIdx.x;
+        nth = blockDim.x;
+    }
+    for (int j = tid; j < I.n; j += nth) {
         const int gj = I.x_off + j;
         const double wt = g.wt[gj];
         const double a = at_q(xa, gj, wt), b = at_q(xb, gj, wt);
@@ -133,8 +157,12 @@ __device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const
 template <typename S, typename V, typename T>
 __device__ void prepare_tangent(const DevInst& I, const Grid& g, int ntot, const S* xa,
                                 const S* xb, const V* va, const V* vb, T* dvec, int vs, int vbase,
-                                T* ddia) {
-    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                                T* ddia, int tid = -1, int nth = 0) {
+    if (tid < 0) {
+        tid = threadIdx.x;
+        nth = blockDim.x;
+    }
+    for (int j = tid; j < I.n; j += nth) {
         const int gj = I.x_off + j;
         const double wt = g.wt[gj];
         const double a = at_q(xa, gj, wt), b = at_q(xb, gj, wt);
@@ -172,8 +200,8 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
                                         const float* __restrict__ Klo, int vertex, int jlo,
                                         int jhi, T& outA, T& outB) {
     if (jhi > I.n) jhi = I.n;
-    const long long plane = (long long)I.n * I.ld;
-    const long long row = I.k_off + (long long)i * I.ld;
+    const long long plane = I.ld;  // planes of a row are adjacent
+    const long long row = I.k_off + (long long)i * 3 * I.ld;
     const T* va = vec + I.x_off;
     const T* vb = vec + ntot + I.x_off;
     const T* v1 = vec + 2 * ntot + I.x_off;
@@ -224,8 +252,8 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
                                             const float* __restrict__ Klo, int vertex, int jlo,
                                             int jhi, T& outA, T& outB) {
     if (jhi > I.n) jhi = I.n;
-    const long long plane = (long long)I.n * I.ld;
-    const long long row = I.k_off + (long long)i * I.ld;
+    const long long plane = I.ld;  // planes of a row are adjacent
+    const long long row = I.k_off + (long long)i * 3 * I.ld;
     const int o = I.x_off;
     T sA = 0, sB = 0;
     if (vertex == QDSE_VERTEX_BC) {
@@ -299,42 +327,48 @@ __device__ __forceinline__ void tpair32(float a, float b, float u1, float u2, fl
     sB = fmaf(e1 * da + u1 * dda - e2 * db - u2 * ddb, KT, fmaf(1.5f * fmaf(e1, sa, u1 * dsa), K0, sB));
 }
 
-// FP32 sweep (or, with TAN, tangent sweep) of the kRows external points i0.. of instance I:
-// one warp, lanes over 4-node column chunks (16-byte loads) inside the union of the rows'
-// nonzero bands; the node vectors of a chunk are loaded once and used for every row.
+__device__ __forceinline__ float pick(const float4& v, int d) {
+    return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
+}
+
+// FP32 sweep (or, with TAN, tangent sweep) of one row group: one warp, lanes over 4-node column
+// chunks (16-byte loads) inside the union of the rows' nonzero bands.  The group descriptor carries
+// every offset, so all loads of the group issue after a single round trip; the node vectors of a
+// chunk serve every row; the removable-limit term of row i is added by the lane that holds column
+// i (its kernel entry K_T,ii and node vectors are already in that lane's registers).
 template <bool TAN>
-__device__ __forceinline__ void group32(int lane, const DevInst& I, int i0, const Grid& g,
+__device__ __forceinline__ void group32(int lane, const GroupDesc& d, const Grid& g,
                                         const Work& w, int ntot, const float* __restrict__ Khi,
-                                        int vertex, double scale) {
-    const int nr = min(kRows, I.n - i0);
-    const long long plane = (long long)I.n * I.ld;
-    const int o = I.x_off + i0;
+                                        int vertex, int collocated, double scale, double m) {
+    static_assert(kRows == 4, "the butterfly reduction below is written for 4 rows");
+    const int nr = d.nr;
+    const int o = d.x_off + d.i0;
     const int nv = w.nv;
-    int jlo = I.ld, jhi = 0;
     float Ai[kRows], Bi[kRows], Pi[kRows], dAi[kRows], dBi[kRows], sA[kRows], sB[kRows];
+    float qA[kRows], qB[kRows], eqA[kRows], eqB[kRows];
+    double Pd[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         sA[r] = 0.f;
         sB[r] = 0.f;
-        Ai[r] = Bi[r] = Pi[r] = dAi[r] = dBi[r] = 0.f;
-        if (r < nr) {
-            const int2 bd = g.band[o + r];
-            jlo = min(jlo, bd.x);
-            jhi = max(jhi, bd.y);
-            Ai[r] = w.x32[o + r];
-            Bi[r] = w.x32[ntot + o + r];
-            Pi[r] = g.sp32[o + r];
-            if (TAN) {
-                dAi[r] = w.d32[o + r];
-                dBi[r] = w.d32[ntot + o + r];
-            }
-        }
+        const bool v = r < nr;
+        Pd[r] = v ? g.sp[o + r] : 1.0;
+        Ai[r] = v ? w.x32[o + r] : 0.f;
+        Bi[r] = v ? w.x32[ntot + o + r] : 0.f;
+        Pi[r] = v ? g.sp32[o + r] : 0.f;
+        dAi[r] = (v && TAN) ? w.d32[o + r] : 0.f;
+        dBi[r] = (v && TAN) ? w.d32[ntot + o + r] : 0.f;
+        qA[r] = (v && collocated) ? w.dia32[o + r] : 0.f;
+        qB[r] = (v && collocated) ? w.dia32[ntot + o + r] : 0.f;
+        eqA[r] = (v && collocated && TAN) ? w.ddia32[o + r] : 0.f;
+        eqB[r] = (v && collocated && TAN) ? w.ddia32[ntot + o + r] : 0.f;
     }
-    const float* vb = w.vec32 + I.v_off;
-    const float* db_ = w.dvec32 + I.v_off;
-    const float* kb = Khi + I.k_off + (long long)i0 * I.ld;
+    const float* vb = w.vec32 + d.v_off;
+    const float* db_ = w.dvec32 + d.v_off;
+    const float* kb = Khi + d.kbase;
+    const long long plane = d.plane;
     const bool bc = (vertex == QDSE_VERTEX_BC);
-    for (int c = jlo + 4 * lane; c < jhi; c += 128) {
+    for (int c = d.jlo + 4 * lane; c < d.jhi; c += 128) {
         const float4 a = ld4(vb + c), b = ld4(vb + nv + c), u1 = ld4(vb + 2 * nv + c),
                      u2 = ld4(vb + 3 * nv + c), u3 = ld4(vb + 4 * nv + c);
         float4 ea, eb, e1, e2, e3;
@@ -348,7 +382,7 @@ __device__ __forceinline__ void group32(int lane, const DevInst& I, int i0, cons
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             if (r < nr) {
-                const float* kr = kb + (long long)r * I.ld + c;
+                const float* kr = kb + (long long)r * 3 * d.ld + c;
                 const float4 K0 = ld4(kr), K3 = ld4(kr + 2 * plane);
                 if (bc) {
                     const float4 KT = ld4(kr + plane);
@@ -363,6 +397,19 @@ __device__ __forceinline__ void group32(int lane, const DevInst& I, int i0, cons
                         tpair32(a.z, b.z, u1.z, u2.z, u3.z, ea.z, eb.z, e1.z, e2.z, e3.z, K0.z, KT.z, K3.z, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
                         tpair32(a.w, b.w, u1.w, u2.w, u3.w, ea.w, eb.w, e1.w, e2.w, e3.w, K0.w, KT.w, K3.w, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
                     }
+                    // removable limit q^2 -> p^2 of row i = i0 + r, by the lane holding column i
+                    const int dd = d.i0 + r - c;
+                    if (collocated && dd >= 0 && dd < 4) {
+                        const float KTd = pick(KT, dd), x1 = pick(u1, dd), x2 = pick(u2, dd);
+                        if (!TAN) {
+                            sA[r] += (-x1 * qB[r] - Pi[r] * x2 * qA[r]) * KTd;
+                            sB[r] += (x1 * qA[r] - x2 * qB[r]) * KTd;
+                        } else {
+                            const float y1 = pick(e1, dd), y2 = pick(e2, dd);
+                            sA[r] += (-y1 * qB[r] - x1 * eqB[r] - Pi[r] * (y2 * qA[r] + x2 * eqA[r])) * KTd;
+                            sB[r] += (y1 * qA[r] + x1 * eqA[r] - y2 * qB[r] - x2 * eqB[r]) * KTd;
+                        }
+                    }
                 } else {
                     const float4 p2 = TAN ? e2 : u2, p1 = TAN ? e1 : u1;
                     sA[r] += p2.x * K3.x + p2.y * K3.y + p2.z * K3.z + p2.w * K3.w;
@@ -371,67 +418,66 @@ __device__ __forceinline__ void group32(int lane, const DevInst& I, int i0, cons
             }
         }
     }
-    float myA = 0.f, myB = 0.f;
+    // reduce the 2 kRows partial sums at once: lane 4q ends with the total of value q
+    // (q < kRows: sA[q]; q >= kRows: sB[q - kRows]) after 4 + 2 + 1 + 2 shuffles
+    float v4[4];
+    {
+        const bool hi = (lane >> 4) & 1;
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const float ra = warp_sum(sA[r]), rb = warp_sum(sB[r]);
-        if (lane == r) {
-            myA = ra;
-            myB = rb;
+        for (int k = 0; k < 4; ++k) {
+            const float keep = hi ? sB[k] : sA[k], send = hi ? sA[k] : sB[k];
+            v4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
         }
     }
-    if (lane < nr) {
-        const int i = i0 + lane, gi = I.x_off + i;
-        if (bc && I.mode == QDSE_COLLOCATED) {
-            const float KTd = Khi[I.k_off + (long long)i * I.ld + plane + i];
-            const float u1 = vb[2 * nv + i], u2 = vb[3 * nv + i];
-            const float dA = w.dia32[gi], dB = w.dia32[ntot + gi];
-            const float P = g.sp32[gi];
-            if (!TAN) {
-                myA += (-u1 * dB - P * u2 * dA) * KTd;
-                myB += (u1 * dA - u2 * dB) * KTd;
-            } else {
-                const float e1 = db_[2 * nv + i], e2 = db_[3 * nv + i];
-                const float edA = w.ddia32[gi], edB = w.ddia32[ntot + gi];
-                myA += (-e1 * dB - u1 * edB - P * (e2 * dA + u2 * edA)) * KTd;
-                myB += (e1 * dA + u1 * edA - e2 * dB - u2 * edB) * KTd;
-            }
+    float v2[2];
+    {
+        const bool hi = (lane >> 3) & 1;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float keep = hi ? v4[k + 2] : v4[k], send = hi ? v4[k] : v4[k + 2];
+            v2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
         }
-        if (!TAN) {
-            w.xn32[gi] = (float)(1.0 + scale * (double)myA / g.sp[gi]);
-            w.xn32[ntot + gi] = (float)(I.m + scale * (double)myB);
+    }
+    float tot;
+    {
+        const bool hi = (lane >> 2) & 1;
+        const float keep = hi ? v2[1] : v2[0], send = hi ? v2[0] : v2[1];
+        tot = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    tot += __shfl_xor_sync(0xffffffffu, tot, 2);
+    tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+    const int q = lane >> 2;
+    const int r = q & 3;
+    if ((lane & 3) == 0 && r < nr) {
+        const int gi = o + r;
+        if (q < 4) {
+            w.xn32[gi] = TAN ? (float)(scale * (double)tot / Pd[r])
+                             : (float)(1.0 + scale * (double)tot / Pd[r]);
         } else {
-            w.xn32[gi] = (float)(scale * (double)myA / g.sp[gi]);
-            w.xn32[ntot + gi] = (float)(scale * (double)myB);
+            w.xn32[ntot + gi] = TAN ? (float)(scale * (double)tot) : (float)(m + scale * (double)tot);
         }
     }
 }
 
-// One tick of the batched solve: every group of kRows external points of every unfinished
-// instance advances by the operation its instance's phase asks for (one warp per group).
-__global__ void __launch_bounds__(256, 2) k_tick(const DevInst* __restrict__ inst,
-                                                 const DevState* __restrict__ state,
-                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
-                                                 const float* __restrict__ Khi,
-                                                 const float* __restrict__ Klo, const double* A,
-                                                 const double* B, int ntot, int ngroups) {
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (gw >= ngroups) return;
-    const int2 grp = g.groups[gw];
-    const int phase = state[grp.x].phase;
-    if (phase == PH_DONE) return;
-    const DevInst I = inst[grp.x];
+// One tick of the batched solve: every row group of every unfinished instance advances by the
+// operation its instance's phase asks for (one warp per group).
+// One row group of a tick; returns after its outputs are stored.
+__device__ __forceinline__ void tick_group(const GroupDesc& d, int phase, int lane,
+                                           const DevInst& I, const Ctl* __restrict__ ctl,
+                                           const Grid& g, const Work& w,
+                                           const float* __restrict__ Khi,
+                                           const float* __restrict__ Klo, const double* A,
+                                           const double* B, int ntot) {
     const int vertex = ctl->vertex;
+    const int collocated = (I.mode == QDSE_COLLOCATED) && vertex == QDSE_VERTEX_BC;
     const double scale = ctl->kappa * I.D;
     if (phase == PH_PICARD32) {
-        group32<false>(lane, I, grp.y, g, w, ntot, Khi, vertex, scale);
+        group32<false>(lane, d, g, w, ntot, Khi, vertex, collocated, scale, I.m);
     } else if (phase == PH_TANGENT32) {
-        group32<true>(lane, I, grp.y, g, w, ntot, Khi, vertex, scale);
+        group32<true>(lane, d, g, w, ntot, Khi, vertex, collocated, scale, I.m);
     } else {  // PH_RESID64 or PH_PICARD64 on the precomputed double-float kernels
-        const int nr = min(kRows, I.n - grp.y);
-        for (int rr = 0; rr < nr; ++rr) {
-            const int i = grp.y + rr, r = I.x_off + i;
+        for (int rr = 0; rr < d.nr; ++rr) {
+            const int i = d.i0 + rr, r = I.x_off + i;
             const int2 bd = g.band[r];
             double sA, sB;
             row_map<double, true>(lane, I, i, g.sp[r], A[r], B[r], w.vec64, w.dia64, ntot, Khi,
@@ -442,6 +488,22 @@ __global__ void __launch_bounds__(256, 2) k_tick(const DevInst* __restrict__ ins
             }
         }
     }
+}
+
+// Narrow every group's column range to the union of its rows' nonzero bands.
+__global__ void k_group_bands(Grid g, int ngroups) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ngroups) return;
+    GroupDesc d = g.gdesc[t];
+    int lo = 1 << 30, hi = 0;
+    for (int r = 0; r < d.nr; ++r) {
+        const int2 bd = g.band[d.x_off + d.i0 + r];
+        lo = min(lo, bd.x);
+        hi = max(hi, bd.y);
+    }
+    if (hi <= lo) lo = hi = 0;
+    g.gdesc[t].jlo = lo;
+    g.gdesc[t].jhi = hi;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -526,16 +588,27 @@ __global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ i
 // per-instance state machine
 // ------------------------------------------------------------------------------------------------
 __device__ void prepare_phase(int phase, const DevInst& I, const Grid& g, const Work& w, int ntot,
-                              const double* A, const double* B) {
+                              const double* A, const double* B, int tid = -1, int nth = 0) {
     if (phase == PH_PICARD32) {
         prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.nv, I.v_off,
-                                      w.dia32);
+                                      w.dia32, tid, nth);
     } else if (phase == PH_RESID64 || phase == PH_PICARD64) {
-        prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, ntot, I.x_off, w.dia64);
+        prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, ntot, I.x_off, w.dia64, tid,
+                                        nth);
     } else if (phase == PH_TANGENT32) {
         prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
-                                             w.d32 + ntot, w.dvec32, w.nv, I.v_off, w.ddia32);
+                                             w.d32 + ntot, w.dvec32, w.nv, I.v_off, w.ddia32, tid,
+                                             nth);
     }
+}
+
+// List the items (instance b, first row) of an unfinished instance for the next sweep.
+__device__ __forceinline__ void append_items(const Work& w, int buf, int b, int n) {
+    const int cnt = (n + w.rb - 1) / w.rb;
+    const int base = atomicAdd(w.item_count + buf, cnt);
+    if (base + cnt > w.max_items) return;  // cannot happen while the lists are reset every tick
+    int2* dst = w.items + (size_t)buf * w.max_items + base;
+    for (int t = 0; t < cnt; ++t) dst[t] = make_int2(b, t * w.rb);
 }
 
 // Set every instance to its first phase, convert the start to FP32 where needed and form the
@@ -564,31 +637,40 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         s.loc = (phase0 == PH_PICARD32) ? 1 : 0;
         s.pad = 0;
         state[b] = s;
+        append_items(w, 0, b, I.n);
+        w.ilist[atomicAdd(w.lcount + 0, 1)] = b;
+        const int ng = (I.n + kRows - 1) / kRows;
+        const int gb = atomicAdd(w.lcount + 3, ng);
+        for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
     }
+    for (int t = threadIdx.x; t < (I.n + kRows - 1) / kRows; t += blockDim.x) g.gphase[I.g_off + t] = phase0;
     prepare_phase(phase0, I, g, w, ntot, A, B);
 }
 
 // Advance one instance after a tick.  One block (256 threads) per instance.
-__global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst, DevState* state,
-                                                const Ctl* __restrict__ ctl, Grid g, Work w,
-                                                double* A, double* B, int ntot, int* count,
-                                                unsigned long long* ctr) {
-    __shared__ double sh[32];
-    const int b = blockIdx.x;
+// Sweep outputs (xn32, xn64) are read with L2-coherent loads (they come from other SMs; this keeps
+// the update correct even when it runs inside the kernel that wrote them).
+template <typename Team>
+__device__ void update_instance(const Team& T, int b, const DevInst* __restrict__ inst,
+                                DevState* state, const Ctl* __restrict__ ctl, const Grid& g,
+                                const Work& w, double* A, double* B, int ntot, int* count,
+                                unsigned long long* ctr, int next_list, int next_items,
+                                int list_items) {
     DevState s = state[b];
     if (s.phase == PH_DONE) return;
     const DevInst I = inst[b];
     const Ctl C = *ctl;
-    if (threadIdx.x == 0 && ctr) {
+    if (T.leader() && ctr) {
         // work counters of the sweep this update completes: instance-sweeps by precision,
         // algorithmic bytes (kernel rows + per-node vectors + own values and outputs) and
         // BC-kernel evaluations n_p * n_q * n_theta
-        const unsigned long long n = (unsigned long long)I.n;
+        // (kernel bytes: only the nonzero band of every row has to be read)
+        const unsigned long long n = (unsigned long long)I.n, nz = g.nnz[b];
         unsigned long long bytes;
-        if (s.phase == PH_PICARD32) bytes = 12ull * n * n + 36ull * n;
-        else if (s.phase == PH_TANGENT32) bytes = 12ull * n * n + 64ull * n;
+        if (s.phase == PH_PICARD32) bytes = 12ull * nz + 36ull * n;
+        else if (s.phase == PH_TANGENT32) bytes = 12ull * nz + 64ull * n;
         else if (C.precision == QDSE_FP64) bytes = 56ull * n;
-        else bytes = 24ull * n * n + 72ull * n;
+        else bytes = 24ull * nz + 72ull * n;
         atomicAdd(ctr + ((s.phase == PH_PICARD32 || s.phase == PH_TANGENT32) ? 0 : 1), 1ull);
         atomicAdd(ctr + 2, bytes);
         atomicAdd(ctr + 3, n * n * (unsigned long long)I.nt);
@@ -602,10 +684,10 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
         // relaxed Picard step (or the residual of one) and its R7 relative change
         const bool f32 = (s.phase == PH_PICARD32);
         double bmax = 0.0, bad = 0.0;
-        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
-            double fb = f32 ? (double)w.xn32[ntot + gj] : w.xn64[ntot + gj];
-            double fa = f32 ? (double)w.xn32[gj] : w.xn64[gj];
+            double fb = f32 ? (double)__ldcg(w.xn32 + ntot + gj) : __ldcg(w.xn64 + ntot + gj);
+            double fa = f32 ? (double)__ldcg(w.xn32 + gj) : __ldcg(w.xn64 + gj);
             double xb = f32 ? (double)w.x32[ntot + gj] : B[gj];
             double xa = f32 ? (double)w.x32[gj] : A[gj];
             if (s.phase != PH_RESID64) {
@@ -615,14 +697,14 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
             bmax = fmax(bmax, fabs(fb));
             if (!isfinite(fa) || !isfinite(fb)) bad = 1.0;
         }
-        bmax = block_max(bmax, sh);
-        bad = block_max(bad, sh);
+        bmax = T.max(bmax);
+        bad = T.max(bad);
         const double fl = 1e-12 * bmax;
         double ch = 0.0;
-        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
-            double fa = f32 ? (double)w.xn32[gj] : w.xn64[gj];
-            double fb = f32 ? (double)w.xn32[ntot + gj] : w.xn64[ntot + gj];
+            double fa = f32 ? (double)__ldcg(w.xn32 + gj) : __ldcg(w.xn64 + gj);
+            double fb = f32 ? (double)__ldcg(w.xn32 + ntot + gj) : __ldcg(w.xn64 + ntot + gj);
             const double xa = f32 ? (double)w.x32[gj] : A[gj];
             const double xb = f32 ? (double)w.x32[ntot + gj] : B[gj];
             if (s.phase != PH_RESID64) {
@@ -641,7 +723,7 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
                 w.r64[ntot + gj] = fb - xb;
             }
         }
-        ch = block_max(ch, sh);
+        ch = T.max(ch);
         s.change = ch;
         s.iters += 1;
         if (bad != 0.0) {
@@ -654,13 +736,13 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
         if (s.phase == PH_RESID64) {
             if (done && status == QDSE_OK) {
                 // accept the FP64 Picard step from the refined iterate
-                for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
-                    A[o + j] = w.xn64[o + j];
-                    B[o + j] = w.xn64[ntot + o + j];
+                for (int j = T.tid(); j < I.n; j += T.size()) {
+                    A[o + j] = __ldcg(w.xn64 + o + j);
+                    B[o + j] = __ldcg(w.xn64 + ntot + o + j);
                 }
             } else if (!done) {
                 // start a correction solve delta = J delta + r at the current x
-                for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+                for (int j = T.tid(); j < I.n; j += T.size()) {
                     const int gj = o + j;
                     w.d64[gj] = w.r64[gj];
                     w.d64[ntot + gj] = w.r64[ntot + gj];
@@ -669,9 +751,9 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
                     w.x32[gj] = (float)A[gj];
                     w.x32[ntot + gj] = (float)B[gj];
                 }
-                __syncthreads();
+                T.sync();
                 prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.nv,
-                                              I.v_off, w.dia32);
+                                              I.v_off, w.dia32, T.tid(), T.size());
                 next = PH_TANGENT32;
                 s.inner = 0;
             }
@@ -682,13 +764,13 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
     } else if (s.phase == PH_TANGENT32) {
         // delta <- delta + alpha (J delta + r - delta); relative change of delta (max norm)
         double dmax = 0.0, cmax = 0.0, bad = 0.0;
-        for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int k = c * ntot + gj;
                 const double d = w.d64[k];
-                const double dn = d + C.alpha * ((double)w.xn32[k] + w.r64[k] - d);
+                const double dn = d + C.alpha * ((double)__ldcg(w.xn32 + k) + w.r64[k] - d);
                 dmax = fmax(dmax, fabs(dn));
                 cmax = fmax(cmax, fabs(dn - d));
                 if (!isfinite(dn)) bad = 1.0;
@@ -696,9 +778,9 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
                 w.d32[k] = (float)dn;
             }
         }
-        dmax = block_max(dmax, sh);
-        cmax = block_max(cmax, sh);
-        bad = block_max(bad, sh);
+        dmax = T.max(dmax);
+        cmax = T.max(cmax);
+        bad = T.max(bad);
         s.iters += 1;
         s.inner += 1;
         s.dnorm = dmax > 0.0 ? cmax / dmax : 0.0;
@@ -706,7 +788,7 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
             done = true;
             status = QDSE_ERR_NONFINITE;
         } else if (s.dnorm <= C.inner_tol || s.inner >= C.max_inner) {
-            for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            for (int j = T.tid(); j < I.n; j += T.size()) {
                 A[o + j] += w.d64[o + j];
                 B[o + j] += w.d64[ntot + o + j];
             }
@@ -717,33 +799,90 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
         done = true;
         status = QDSE_ERR_NOT_CONVERGED;
     }
-    __syncthreads();
+    T.sync();
     if (done) {
         next = PH_DONE;
     } else {
         if (next == PH_RESID64 && s.phase == PH_PICARD32) {
-            for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+            for (int j = T.tid(); j < I.n; j += T.size()) {
                 A[o + j] = (double)w.x32[o + j];
                 B[o + j] = (double)w.x32[ntot + o + j];
             }
-            __syncthreads();
+            T.sync();
         }
         if (next != PH_TANGENT32 || s.phase == PH_TANGENT32) {
-            prepare_phase(next, I, g, w, ntot, A, B);
+            prepare_phase(next, I, g, w, ntot, A, B, T.tid(), T.size());
         } else {
             prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
                                                  w.d32 + ntot, w.dvec32, w.nv, I.v_off,
-                                                 w.ddia32);
+                                                 w.ddia32, T.tid(), T.size());
         }
     }
-    if (threadIdx.x == 0) {
+    for (int t = T.tid(); t < (I.n + kRows - 1) / kRows; t += T.size()) g.gphase[I.g_off + t] = next;
+    if (T.leader()) {
         s.phase = next;
         s.status = status;
         if (next == PH_PICARD32) s.loc = 1;
         else if (next != PH_DONE) s.loc = 0;
         state[b] = s;
-        if (!done && count) atomicAdd(count, 1);
+        if (!done) {
+            if (count) atomicAdd(count, 1);
+            if (list_items) append_items(w, next_items, b, I.n);
+            // the instance and its row groups stay on the active lists of the next tick
+            w.ilist[(size_t)next_list * w.n_inst + atomicAdd(w.lcount + next_list, 1)] = b;
+            const int ng = (I.n + kRows - 1) / kRows;
+            const int gb = atomicAdd(w.lcount + 3 + next_list, ng);
+            for (int t = 0; t < ng; ++t) w.glist[(size_t)next_list * w.n_groups + gb + t] = I.g_off + t;
+        }
     }
+    T.sync();
+}
+
+// One tick of the batched solve: persistent warps walk the active row groups (list t % 3 built by
+// the previous update) and advance each by the operation its instance's phase asks for.
+__global__ void __launch_bounds__(256, 2) k_tick(const DevInst* __restrict__ inst,
+                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                 const float* __restrict__ Khi,
+                                                 const float* __restrict__ Klo, const double* A,
+                                                 const double* B, int ntot, int list) {
+    const int lane = threadIdx.x & 31;
+    const int nact = w.lcount[3 + list];
+    const int* ids = w.glist + (size_t)list * w.n_groups;
+    const int stride = gridDim.x * (blockDim.x >> 5);
+    int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int id = (t < nact) ? ids[t] : 0;
+    while (t < nact) {
+        const int tn = t + stride;
+        const int idn = (tn < nact) ? ids[tn] : 0;  // prefetch the next group id
+        const GroupDesc d = g.gdesc[id];
+        const int phase = g.gphase[id];
+        const DevInst I = inst[d.b];
+        tick_group(d, phase, lane, I, ctl, g, w, Khi, Klo, A, B, ntot);
+        t = tn;
+        id = idn;
+    }
+}
+
+// Advance every instance on the current active list after a tick (persistent blocks; used after
+// the on-the-fly FP64 sweep and the work-list sweep, which do not update instances themselves).
+__global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst, DevState* state,
+                                                const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                double* A, double* B, int ntot, int* count,
+                                                unsigned long long* ctr, int list, int items_next,
+                                                int list_items) {
+    __shared__ double sh[32];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *w.work_ctr = 0;  // the next work-list sweep's item counter
+        const int clr = (list + 2) % 3;  // lists of two ticks ahead start empty
+        w.lcount[clr] = 0;
+        w.lcount[3 + clr] = 0;
+    }
+    const BlockTeam T{sh};
+    const int n = w.lcount[list];
+    const int* ids = w.ilist + (size_t)list * w.n_inst;
+    for (int k = blockIdx.x; k < n; k += gridDim.x)
+        update_instance(T, ids[k], inst, state, ctl, g, w, A, B, ntot, count, ctr,
+                        (list + 1) % 3, items_next, list_items);
 }
 
 // Copy the final iterate out of the FP32 store where needed and report per-instance results.
@@ -855,6 +994,11 @@ static inline int row_blocks(int ntot) { return (ntot + 7) / 8; }
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0) {
     cudaError_t e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c->work.item_count, 0, 2 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->work.work_ctr, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->work.lcount, 0, 6 * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    c->tick = 0;
     prof_begin(c, PK_OTHER);
     k_init_state<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
                                                    c->work, A, B, c->n_total, phase0);
@@ -863,11 +1007,19 @@ cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B,
     return cudaGetLastError();
 }
 
+cudaError_t launch_group_bands(qdse_ctx* c) {
+    prof_begin(c, PK_OTHER);
+    k_group_bands<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(c->grid, c->n_groups);
+    c->launches++;
+    prof_end(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B) {
     prof_begin(c, PK_SWEEP);
-    k_tick<<<(c->n_groups + 7) / 8, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl,
-                                                         c->grid, c->work, c->d_Khi, c->d_Klo, A,
-                                                         B, c->n_total, c->n_groups);
+    const int blocks = std::min((c->n_groups + 7) / 8, 2 * (c->n_sms > 0 ? c->n_sms : 152));
+    k_tick<<<blocks, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi,
+                                          c->d_Klo, A, B, c->n_total, (int)(c->tick % 3));
     c->launches++;
     prof_end(c);
     return cudaGetLastError();
@@ -875,8 +1027,12 @@ cudaError_t launch_tick(qdse_ctx* c, double* A, double* B) {
 
 cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
     prof_begin(c, PK_UPDATE);
-    k_update<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
-                                               A, B, c->n_total, c->d_count, c->d_sweeps);
+    const int blocks = std::min(c->n_inst, 8 * (c->n_sms > 0 ? c->n_sms : 152));
+    k_update<<<blocks, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
+                                            A, B, c->n_total, c->d_count, c->d_sweeps,
+                                            (int)(c->tick % 3), (int)((c->tick + 1) & 1),
+                                            (c->sweep_kind == 1 && c->opt.precision != QDSE_FP64) ? 1 : 0);
+    c->tick++;
     c->launches++;
     prof_end(c);
     return cudaGetLastError();

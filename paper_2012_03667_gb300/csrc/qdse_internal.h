@@ -5,9 +5,10 @@
 //                 FP64 grid arrays (s_p, s_q, W, ...) and every per-point work vector use this
 //                 index; vectors with several components are stored component-major with stride
 //                 n_total (component c of point g at [c * n_total + g]).
-//   kernel pool : instance b owns 3 planes of n_b x ld_b floats starting at k_off[b]
-//                 (plane 0 = K_0, 1 = K_T / (Q_j - P_i) (diagonal: K_T), 2 = K_3), rows i
-//                 (external p_i), columns j (internal q_j), ld_b = n_b rounded up to 4.  The
+//   kernel pool : instance b owns n_b rows (external p_i) of 3 planes x ld_b floats starting at
+//                 k_off[b]: entry (i, plane, j) at k_off + (3 i + plane) ld + j, plane 0 = K_0,
+//                 1 = K_T / (Q_j - P_i) (diagonal: K_T), 2 = K_3, columns j (internal q_j),
+//                 ld_b = n_b rounded up to 4 (the three planes of a row are adjacent).  The
 //                 same layout holds the low parts (double-float residues) in a second buffer and,
 //                 for the adjoint, the omega-derivatives of the three kernels.
 //   angular     : instance b owns nodes [t_off[b], t_off[b] + n_theta_b).
@@ -44,8 +45,15 @@ struct DevInst {          // per-instance descriptor, read-only during a solve
     int ld;               // row stride of the kernel planes (n rounded up to 4)
     int mode;             // QDSE_COLLOCATED / QDSE_STAGGERED
     int v_off;            // first element of this instance in the padded FP32 node vectors
-    int pad_;
+    int g_off;            // first row group of this instance
     double D, omega, m;   // current parameters
+};
+
+struct GroupDesc {        // one row group (kRows consecutive external points of one instance)
+    int b, i0, nr, jlo;   // instance, first row, rows in the group, band union start
+    int jhi, v_off, x_off, ld;  // band union end, node-vector base, point base, row stride
+    long long kbase;      // kernel-pool offset of row i0 (plane 0)
+    long long plane;      // distance between the planes of a row (= ld)
 };
 
 struct DevState {         // per-instance solver state, updated by the update kernel
@@ -95,6 +103,21 @@ struct Work {
     double* ddia64; // [2]
     double* lam;    // [2] adjoint iterate
     double* lamn;   // [2] adjoint sweep output
+    // work list of the bulk-copy sweep: items (instance, first row) of rb rows, two buffers
+    // (the update of tick t lists the items of tick t + 1)
+    int2* items;    // [2][max_items]
+    int* item_count;  // [2]
+    int* work_ctr;  // [1] next item to take in the current sweep
+    int rb;         // rows per item
+    int max_items;
+    // active lists: instances and row groups still running, three buffers (tick t reads list
+    // t % 3, appends the survivors to (t + 1) % 3 and empties (t + 2) % 3);
+    // lcount = {instances[0..2], groups[0..2]}
+    int* ilist;     // [3][n_inst]
+    int* glist;     // [3][n_groups]
+    int* lcount;    // [6]
+    int n_inst;
+    int n_groups;
 };
 
 struct Grid {              // FP64 grid arrays on the device (global point index)
@@ -116,13 +139,17 @@ struct Grid {              // FP64 grid arrays on the device (global point index
     int2* band;            // per external point: [jlo, jhi) outside which every kernel entry of
                            // the row is exactly zero (jlo, jhi multiples of 4, jhi <= ld)
     int2* groups;          // (instance, first row) of every group of kRows consecutive rows
+    struct GroupDesc* gdesc;  // per group: everything a sweep needs to start its loads
+    int* gphase;           // per group: the phase of its instance for the coming sweep
+    unsigned long long* nnz;  // per instance: sum over rows of the band widths (kernel entries a
+                              // sweep must read per plane)
 };
 
 constexpr int kRows = 4;   // external points per warp in the batched sweeps
 
 struct HostInst {
     qdse_grid g;
-    int x_off, t_off, ld, v_off;
+    int x_off, t_off, ld, v_off, g_off;
     long long k_off;
 };
 
@@ -151,12 +178,18 @@ struct qdse_ctx {
     float* d_Klo = nullptr;
     float* d_Kwhi = nullptr;  // omega-derivative kernels (allocated on first adjoint)
     float* d_Kwlo = nullptr;
-    int* d_count = nullptr;   // [1] number of unfinished instances after the last update
+    int* d_count = nullptr;   // [2] unfinished instances after the last update; error flag
     unsigned long long* d_sweeps = nullptr;  // [4] FP32 / FP64 instance-sweeps, algorithmic
                                              // bytes of the sweeps, BC-kernel evaluations
     double* d_hostA = nullptr;  // staging for qdse_solve_host: [2 n_total] doubles
     int* d_hostI = nullptr;     // [2 n_inst] ints (iterations, status)
-    int* h_count = nullptr;   // pinned mirror
+    int* h_count = nullptr;   // pinned mirror of d_count[0..1]
+    int* d_err = nullptr;     // = d_count + 1: set when a bounded device wait ran out
+    int n_sms = 0;
+    bool use_tma = false;     // bulk-copy pipelined FP32 sweep configured
+    int ld_max = 0;           // widest kernel row of the batch
+    int sweep_kind = 0;       // 0: row-group kernel, 1: bulk-copy work-list kernel
+    long long tick = 0;       // sweeps issued since the last init (selects the work-list buffer)
     qdse::DevInst* h_inst_pinned = nullptr;
 
     std::string err;
@@ -189,6 +222,9 @@ void build_angular(int nt, double* z, double* y, double* s2, double* w);
 cudaError_t launch_precompute(qdse_ctx* c, bool with_omega_derivative);
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
+cudaError_t launch_sweep32_tma(qdse_ctx* c, const double* A, const double* B);
+cudaError_t launch_group_bands(qdse_ctx* c);
+cudaError_t configure_sweep32_tma(int ldmax);
 cudaError_t launch_update(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_sweep_otf(qdse_ctx* c, const double* A, const double* B, double* FA,
                              double* FB, int only_active);
