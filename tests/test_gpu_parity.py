@@ -366,3 +366,28 @@ def test_host_buffer_entry_point_equals_device_path():
     assert st[0] == 0 and it[0] > 0
     np.testing.assert_array_equal(Ah, host(A))
     np.testing.assert_array_equal(Bh, host(B))
+
+
+def test_autograd_chiral_susceptibility_matches_finite_differences():
+    """torch.autograd through the solve (implicit adjoint) and the condensate: dC/dm, dC/dD,
+    dC/dw against central differences of converged solves (h = 1e-5)."""
+    from paper_2012_03667_gb300 import autograd as AG
+    insts = [inputs.Instance(48, 24, 0.55, 0.678, 0.02), inputs.Instance(40, 16, 0.6, 0.6, 0.05)]
+    ctx = Q.Context([grid(i) for i in insts], precision=Q.QDSE_MIXED, tol=1e-14, max_iter=40000)
+    theta = torch.tensor([[i.m, i.D, i.omega] for i in insts], dtype=torch.float64,
+                         requires_grad=True)
+    A, B = AG.gap_solve(ctx, theta)
+    C = AG.condensate(ctx, A, B)
+    C.sum().backward()
+    g = theta.grad.numpy()
+    h = 1e-5
+    for b, inst in enumerate(insts):
+        for t, key in enumerate(("m", "D", "omega")):
+            vals = []
+            for sgn in (1, -1):
+                kw = dict(inst.__dict__)
+                kw[key] += sgn * h
+                Ar, Br, _ = oracle_fixed_point(inputs.Instance(**kw))
+                vals.append(O.condensate(problem(inputs.Instance(**kw)), Ar, Br))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert g[b, t] == pytest.approx(fd, rel=2e-5, abs=1e-9), (b, key, g[b, t], fd)
