@@ -219,6 +219,23 @@ qdse_status qdse_set_profiling(qdse_ctx* ctx, int on);
  * residual and transposed-sweep kernels), 2 = per-instance updates, 3 = other.  Synchronises. */
 qdse_status qdse_profile(const qdse_ctx* ctx, double* ms, long long* launches);
 
+/* One FP64 sweep F(x) of a single instance that allocates no memory (the paper has no counterpart:
+ * this entry point serves callers that cannot call cudaMalloc, e.g. code inside a fixed memory
+ * arena or pool, or a loop that must not synchronise the device through the allocator).
+ * Computes the same map as qdse_residual in QDSE_FP64 precision (full (j, theta) double sum), but
+ * needs no context: the grid is built on the device into a scratch array compiled into the
+ * library (128 KB per GPU, held until exit), for n_p <= 512 and n_theta <= 256; larger sizes are
+ * rejected with QDSE_ERR_ARG.  g, p: host structs (p->mu must be 0); vertex: QDSE_VERTEX_*; cf:
+ * colour factor; A, B: device double[n_p] (input x); FA, FB: device double[n_p] (output F(x)).
+ * stream: cudaStream_t or NULL.  errbuf (host, errbuf_len bytes, may be NULL) receives a one-line
+ * message ("" on success).  No cudaMalloc, cudaFree or allocating library call is made.  The first
+ * call on each device looks up the scratch array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the one scratch array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  Asynchronous on `stream`. */
+qdse_status qdse_sweep_fp64_noalloc(const qdse_grid* g, const qdse_params* p, int vertex,
+                                    double cf, const double* A, const double* B, double* FA,
+                                    double* FB, void* stream, char* errbuf, int errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ EXPORTS = ("qdse_default_options", "qdse_create", "qdse_create_ragged", "qdse_de
            "qdse_last_error", "qdse_sizes", "qdse_layout", "qdse_grid_nodes", "qdse_set_options",
            "qdse_iterate", "qdse_solve", "qdse_solve_host", "qdse_residual", "qdse_jvp",
            "qdse_vjp", "qdse_adjoint", "qdse_condensate", "qdse_condensate_vjp",
-           "qdse_last_stats", "qdse_last_work", "qdse_set_profiling", "qdse_profile")
+           "qdse_last_stats", "qdse_last_work", "qdse_set_profiling", "qdse_profile",
+           "qdse_sweep_fp64_noalloc")
 
 
 class qdse_grid(ctypes.Structure):
