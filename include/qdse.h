@@ -178,7 +178,8 @@ qdse_status qdse_jvp(qdse_ctx* ctx, const qdse_params* p, const double* A, const
 qdse_status qdse_vjp(qdse_ctx* ctx, const qdse_params* p, const double* A, const double* B,
                      const double* wA, const double* wB, double* JtA, double* JtB);
 
-/* Implicit-function adjoint at a converged solution x* = F(x*) (collocated grids):
+/* Implicit-function adjoint at a converged solution x* = F(x*) (collocated grids; instances whose
+ * (A, B) is not a fixed point to 1e-6 relative are skipped with QDSE_ERR_NOT_CONVERGED):
  * solves lambda = J^T lambda + g, g = (gA, gB) the cotangent dL/d(A, B), and returns
  *     g_params[4 b + t] = dL/dtheta_t,  theta = (m, D, omega, mu),
  * with dF/dm = e_B, dF/dD = (F(x*) - x0)/D, dF/domega from the omega-derivative of the angular

@@ -108,10 +108,14 @@ void free_ctx(qdse_ctx* c) {
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
                     c->grid.groups, c->grid.nnz, c->work.items, c->work.item_count,
                     c->work.work_ctr, c->grid.gdesc, c->grid.gphase, c->work.ilist,
-                    c->work.glist, c->work.lcount};
+                    c->work.glist, c->work.lcount, c->d_tiles, c->d_rel};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->h_count) cudaFreeHost(c->h_count);
     if (c->h_inst_pinned) cudaFreeHost(c->h_inst_pinned);
     delete c;
@@ -192,45 +196,119 @@ void reset_stats(qdse_ctx* c) {
     if (c->d_sweeps) cudaMemsetAsync(c->d_sweeps, 0, 4 * sizeof(unsigned long long), c->stream);
 }
 
+// One tick: the sweep for the path in use and, where the sweep does not update instances itself,
+// the per-instance update.  `last` zeroes the poll counter first (it counts the instances still
+// running after this tick).
+cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
+    const bool otf = (c->opt.precision == QDSE_FP64);
+    cudaError_t e = cudaSuccess;
+    if (last) e = cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    if (otf) {
+        e = launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1);
+    } else if (c->sweep_kind == 1) {
+        e = launch_sweep32_tma(c, A, B);
+    } else {
+        e = launch_tick(c, A, B);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_update(c, A, B);
+}
+
+constexpr int kGraphTicks = 48;  // ticks per captured chunk: a multiple of 6 keeps the list
+                                 // buffers (mod 3) and work-item buffers (mod 2) in step
+
+// Capture kGraphTicks ticks on the internal stream into c->gexec (A, B fixed).
+qdse_status capture_chunk(qdse_ctx* c, double* A, double* B, int path) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    const long long tick0 = c->tick, launches0 = c->launches;
+    QCHECK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < kGraphTicks && e == cudaSuccess; ++t)
+        e = launch_one_tick(c, A, B, t == kGraphTicks - 1);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    c->tick = tick0;
+    c->g_launches = c->launches - launches0;
+    c->launches = launches0;
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(c, e, "capture a chunk of ticks");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, e, "instantiate the tick graph");
+    }
+    c->g_A = A;
+    c->g_B = B;
+    c->g_path = path;
+    return QDSE_OK;
+}
+
 // The batched successive approximation: ticks of (sweep rows, update instances) with the number
-// of unfinished instances polled every `chunk` ticks.  n_ticks < 0 means "until every instance
-// has finished"; otherwise exactly n_ticks ticks without polling.
+// of unfinished instances polled between chunks.  n_ticks < 0 means "until every instance has
+// finished"; otherwise exactly n_ticks ticks without polling.  Solves run on an internal stream
+// (ordered after and before the caller's stream by events) in replayed CUDA graphs of
+// kGraphTicks ticks, unless per-launch profiling is on.
 qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool& timed_out) {
     timed_out = false;
-    const bool otf = (c->opt.precision == QDSE_FP64);
     QCHECK(c, cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int), c->stream), "reset flags");
     const auto t0 = std::chrono::steady_clock::now();
-    long long done_ticks = 0;
+    if (n_ticks >= 0) {
+        for (long long t = 0; t < n_ticks; ++t) QCHECK(c, launch_one_tick(c, A, B, false), "tick");
+        return QDSE_OK;
+    }
+    const bool graphs = !c->profiling;
+    cudaStream_t user = c->stream;
+    if (graphs) {
+        QCHECK(c, cudaEventRecord(c->ev_in, user), "order the solve stream");
+        QCHECK(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "order the solve stream");
+        c->stream = c->gstream;
+    }
+    const int path = (c->opt.precision == QDSE_FP64) ? 2 : c->sweep_kind;
     int chunk = 4;
+    qdse_status st = QDSE_OK;
     while (true) {
-        const long long todo = (n_ticks >= 0) ? n_ticks - done_ticks : chunk;
-        if (n_ticks >= 0 && todo <= 0) break;
-        for (long long t = 0; t < todo; ++t) {
-            // the poll counts the instances still running after the chunk's last tick
-            if (t == todo - 1)
-                QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
-            if (otf) {
-                QCHECK(c, launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1),
-                       "fp64 sweep");
-                QCHECK(c, launch_update(c, A, B), "update");
-            } else if (c->sweep_kind == 1) {
-                QCHECK(c, launch_sweep32_tma(c, A, B), "sweep");
-                QCHECK(c, launch_update(c, A, B), "update");
-            } else {
-                QCHECK(c, launch_tick(c, A, B), "sweep");
-                QCHECK(c, launch_update(c, A, B), "update");
+        if (graphs) {
+            if (!c->gexec || c->g_A != A || c->g_B != B || c->g_path != path) {
+                st = capture_chunk(c, A, B, path);
+                if (st != QDSE_OK) break;
             }
+            cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+            if (e != cudaSuccess) {
+                st = cuda_fail(c, e, "launch the tick graph");
+                break;
+            }
+            c->tick += kGraphTicks;
+            c->launches += c->g_launches;
+        } else {
+            cudaError_t e = cudaSuccess;
+            for (int t = 0; t < chunk && e == cudaSuccess; ++t)
+                e = launch_one_tick(c, A, B, t == chunk - 1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(c, e, "tick");
+                break;
+            }
+            if (chunk < 64) chunk *= 2;
         }
-        done_ticks += todo;
-        if (n_ticks >= 0) break;
-        QCHECK(c, cudaMemcpyAsync(c->h_count, c->d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                                  c->stream),
-               "poll");
-        QCHECK(c, cudaStreamSynchronize(c->stream), "poll sync");
+        cudaError_t e = cudaMemcpyAsync(c->h_count, c->d_count, 2 * sizeof(int),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "poll");
+            break;
+        }
         c->polls++;
         if (c->h_count[1] != 0) {
             timed_out = true;
-            return fail(c, QDSE_ERR_TIMEOUT, "a bounded device wait ran out in the sweep kernel");
+            st = fail(c, QDSE_ERR_TIMEOUT, "a bounded device wait ran out in the sweep kernel");
+            break;
         }
         if (*c->h_count == 0) break;
         if (c->opt.time_limit > 0) {
@@ -240,9 +318,14 @@ qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool
                 break;
             }
         }
-        if (chunk < 64) chunk *= 2;
     }
-    return QDSE_OK;
+    if (graphs) {
+        c->stream = user;
+        cudaError_t e = cudaEventRecord(c->ev_out, c->gstream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(user, c->ev_out, 0);
+        if (e != cudaSuccess && st == QDSE_OK) st = cuda_fail(c, e, "order the caller's stream");
+    }
+    return st;
 }
 
 qdse_status check_ptr(qdse_ctx* c, const void* p, const char* name) {
@@ -304,6 +387,16 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     const int N = c->n_total;
     std::vector<double> sp(N), sq(N), W(N), wt(N), stc(3 * (size_t)N), rsp(N), rsq(N);
     std::vector<int> sta(N), row_inst(N);
+    // precompute tiles: collocated grids only the upper triangle (J >= I), staggered all
+    std::vector<int4> tiles;
+    for (int b = 0; b < n_inst; ++b) {
+        const HostInst& h = c->hinst[b];
+        const int T = (h.g.n_p + kTile - 1) / kTile;
+        for (int I = 0; I < T; ++I)
+            for (int J = (h.g.grid_mode == QDSE_COLLOCATED ? I : 0); J < T; ++J)
+                tiles.push_back(make_int4(b, I, J, 0));
+    }
+    c->n_tiles = (int)tiles.size();
     std::vector<int2> groups;
     std::vector<GroupDesc> gdesc;
     groups.reserve(ng);
@@ -397,6 +490,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     c->work.n_groups = ng;
     CALLOC(c->grid.groups, ng);
     CALLOC(c->grid.gdesc, ng);
+    CALLOC(c->d_tiles, c->n_tiles);
+    CALLOC(c->d_rel, n_inst);
     CALLOC(c->grid.gphase, ng);
     CALLOC(c->work.xn64, 2 * (size_t)N);
     CALLOC(c->work.r64, 2 * (size_t)N);
@@ -440,7 +535,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         {c->grid.wz, wz.data(), sizeof(double) * t},
         {c->grid.row_inst, row_inst.data(), sizeof(int) * N},
         {c->grid.groups, groups.data(), sizeof(int2) * ng},
-        {c->grid.gdesc, gdesc.data(), sizeof(GroupDesc) * ng}};
+        {c->grid.gdesc, gdesc.data(), sizeof(GroupDesc) * ng},
+        {c->d_tiles, tiles.data(), sizeof(int4) * c->n_tiles}};
     for (auto& u : ups) {
         e = cudaMemcpy(u.d, u.h, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -452,6 +548,20 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     c->work.nv = v;
     c->use_tma = (c->n_sms > 0) && configure_sweep32_tma(c->ld_max) == cudaSuccess;
     cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        qdse_status s = cuda_fail(nullptr, e, "create the solve stream");
+        free_ctx(c);
+        return s;
+    }
+    e = configure_precompute(c->max_nt);
+    if (e != cudaSuccess) {
+        qdse_status s = cuda_fail(nullptr, e, "configure the precompute kernel");
+        free_ctx(c);
+        return s;
+    }
     {
         // sweep kernel: the row-group kernel by default; QDSE_SWEEP=items selects the bulk-copy
         // work-list kernel (same results, kept for comparison on new hardware)
@@ -730,7 +840,11 @@ qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, con
     }
     Ctl ctl = make_ctl(c);
     QCHECK(c, cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream), "ctl");
-    QCHECK(c, launch_adjoint_init(c, c->work.lam, gA, gB), "adjoint init");
+    // the adjoint applies at a fixed point: check F(x*) = x* first (relative residual 1e-6)
+    QCHECK(c, launch_residual_fp64(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, c->d_rel, 0,
+                                   c->d_Khi, c->d_Klo),
+           "fixed-point check");
+    QCHECK(c, launch_adjoint_init(c, c->work.lam, gA, gB, c->d_rel, 1e-6), "adjoint init");
     QCHECK(c, launch_adjoint_prep(c, A, B), "adjoint prep");
     const auto t0 = std::chrono::steady_clock::now();
     bool timed_out = false;

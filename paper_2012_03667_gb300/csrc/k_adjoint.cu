@@ -120,8 +120,11 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     const double ca = -2.0 * el * Q * Al / d, cb = -2.0 * el * Bl / d;
     const double alpha_l = al[l], beta_l = be[l];
     double gAl = 0.0, gBl = 0.0;
+    // K_lm vanishes outside row l's band, and K_ml = K_lm: both parts only need the band
+    const int2 bd = g.band[r];
+    const int mlo = bd.x, mhi = min(bd.y, I.n);
     if (ctl->vertex == QDSE_VERTEX_BC) {
-        for (int m = lane; m < I.n; m += 32) {
+        for (int m = mlo + lane; m < mhi; m += 32) {
             const double K0 = (double)Khi[row + m] + (double)Klo[row + m];
             double KT = (double)Khi[row + plane + m] + (double)Klo[row + plane + m];
             const double K3 = (double)Khi[row + 2 * plane + m] + (double)Klo[row + 2 * plane + m];
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
             gBl += ai * (dTA_db + TAe * cb) + bi * (dTB_db + TBe * cb);
         }
     } else {
-        for (int m = lane; m < I.n; m += 32) {
+        for (int m = mlo + lane; m < mhi; m += 32) {
             const double K0 = (double)Khi[row + m] + (double)Klo[row + m];
             const double K3 = (double)Khi[row + 2 * plane + m] + (double)Klo[row + 2 * plane + m];
             const double ai = al[m], bi = be[m];
@@ -229,7 +232,7 @@ __global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* sta
         if (ctr) {
             const unsigned long long n = (unsigned long long)I.n;
             atomicAdd(ctr + 1, 1ull);
-            atomicAdd(ctr + 2, 24ull * n * n + 96ull * n);  // the transposed sweep reads whole rows
+            atomicAdd(ctr + 2, 24ull * g.nnz[blockIdx.x] + 96ull * n);
             atomicAdd(ctr + 3, n * n * (unsigned long long)I.nt);
         }
         s.iters += 1;
@@ -249,8 +252,11 @@ __global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* sta
     }
 }
 
+// lambda = g to start; instances whose state is not a fixed point (relative residual rel above
+// not_fixed; the implicit function theorem does not apply there) are marked finished at once.
 __global__ void k_adjoint_init(const DevInst* __restrict__ inst, DevState* state, Work w,
-                               const double* gA, const double* gB, int ntot) {
+                               const double* gA, const double* gB, int ntot, const double* rel,
+                               double not_fixed) {
     const DevInst I = inst[blockIdx.x];
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
         const int gj = I.x_off + j;
@@ -262,6 +268,7 @@ __global__ void k_adjoint_init(const DevInst* __restrict__ inst, DevState* state
         s.phase = PH_PICARD64;
         s.status = QDSE_ERR_NOT_CONVERGED;
         s.change = INFINITY;
+        if (rel && !(rel[blockIdx.x] <= not_fixed)) s.phase = PH_DONE;
         state[blockIdx.x] = s;
     }
 }
@@ -365,11 +372,12 @@ cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB) {
+cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB,
+                                const double* rel, double not_fixed) {
     (void)lam;
     prof_begin(c, PK_OTHER);
     k_adjoint_init<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, gA, gB,
-                                                     c->n_total);
+                                                     c->n_total, rel, not_fixed);
     c->launches++;
     prof_end(c);
     return cudaGetLastError();

@@ -1,7 +1,7 @@
 // k_precompute.cu -- angular kernel matrices of the Ball-Chiu gap equation.
 //
 // After the Dirac traces of Eqs. dsesys/dsesys2 every angular dependence of a sweep sits in three
-// kernels that do not depend on A or B (Sec. II; the reduction is derived in the solver notes):
+// kernels that do not depend on A or B:
 //   K_n(P_i, Q_j) = 8 pi^2/w^4 sum_k w_k exp(-k^2/w^2) g_n(P_i, Q_j, z_k),   n = 0, T, 3,
 //   g_0 = 1,  g_T = 2 P Q (1 - z^2)/k^2,  g_3 = [3 x (P + Q) - 4 x^2 - 2 P Q]/k^2,
 //   x = sqrt(P Q) z,  k^2 = (sqrt P - sqrt Q)^2 + 2 sqrt(P Q) (1 - z)  (no cancellation at z -> 1).
@@ -13,6 +13,12 @@
 // lo = fl32(K - hi)): the FP32 sweeps read hi, the FP64 residual reads hi + lo (about 48 bits).
 // Optionally the omega-derivatives dK_n/dw (factor -4/w + 2 k^2/w^3 on each term) are stored in a
 // second pool for the adjoint's dF/dw.
+//
+// Work is cut into 32 x 32 tiles of (i, j).  On a collocated grid g_n and k^2 are symmetric in
+// P <-> Q, so K_0 and K_3 are symmetric and K_T/(Q - P) is antisymmetric: only tiles with
+// J >= I are evaluated, and each writes itself and its transpose (through shared memory, so both
+// stores are coalesced).  Staggered grids evaluate every tile.  Tiles whose pairs all have
+// (sqrt P - sqrt Q)^2 / w^2 beyond kSkipExponent are written as exact zeros without evaluation.
 #include "qdse_internal.h"
 
 namespace qdse {
@@ -22,50 +28,52 @@ namespace qdse {
 constexpr double kSkipExponent = 130.0;
 
 template <bool WITH_W>
-__global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ inst, Grid g,
-                                                    float* __restrict__ Khi,
-                                                    float* __restrict__ Klo,
-                                                    float* __restrict__ Kwhi,
-                                                    float* __restrict__ Kwlo) {
+__global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restrict__ inst, Grid g,
+                                                          const int4* __restrict__ tiles,
+                                                          float* __restrict__ Khi,
+                                                          float* __restrict__ Klo,
+                                                          float* __restrict__ Kwhi,
+                                                          float* __restrict__ Kwlo) {
     extern __shared__ double sm[];
-    __shared__ int s_lo, s_hi;
-    const int r = blockIdx.x;  // global external point
-    const int b = g.row_inst[r];
-    const DevInst I = inst[b];
-    const int i = r - I.x_off;
-    double* sy = sm;
-    double* sz = sm + I.nt;
-    double* ss = sm + 2 * I.nt;
-    double* sw = sm + 3 * I.nt;
+    constexpr int S = kTile * (kTile + 1);  // one padded plane of the result tile
+    double* tileK = sm;                     // [set][plane][32][33], set 0 = K, set 1 = dK/dw
+    const int4 t = tiles[blockIdx.x];       // instance, tile row, tile column
+    const DevInst I = inst[t.x];
+    double* sy = tileK + (WITH_W ? 2 : 1) * 3 * S;
+    double* sz = sy + I.nt;
+    double* ss = sz + I.nt;
+    double* sw = ss + I.nt;
     for (int k = threadIdx.x; k < I.nt; k += blockDim.x) {
         sy[k] = g.y[I.t_off + k];
         sz[k] = g.z[I.t_off + k];
         ss[k] = g.s2[I.t_off + k];
         sw[k] = g.wz[I.t_off + k];
     }
-    if (threadIdx.x == 0) {
-        s_lo = I.ld;
-        s_hi = -1;
-    }
     __syncthreads();
-
-    const double P = g.sp[r], rP = g.rsp[r];
+    const int i0 = t.y * kTile, j0 = t.z * kTile;
     const double w = I.omega;
     const double iw2 = 1.0 / (w * w);
     const double pref = 8.0 * kPi * kPi / (w * w * w * w);
     const double fw0 = -4.0 / w, fw1 = 2.0 / (w * w * w);
-    const long long plane = I.ld;  // planes of a row are adjacent
-    const long long row = I.k_off + (long long)i * 3 * I.ld;
-
-    for (int j = threadIdx.x; j < I.ld; j += blockDim.x) {
+    const bool coll = (I.mode == QDSE_COLLOCATED);
+    // is the whole tile beyond the skip threshold?  (sqrt s grows with the index)
+    bool skip_tile;
+    {
+        const int i1 = min(i0 + kTile, I.n) - 1, j1 = min(j0 + kTile, I.n) - 1;
+        const double pl = g.rsp[I.x_off + i0], ph = g.rsp[I.x_off + i1];
+        const double ql = g.rsq[I.x_off + j0], qh = g.rsq[I.x_off + j1];
+        const double gap = fmax(0.0, fmax(ql - ph, pl - qh));
+        skip_tile = gap * gap * iw2 >= kSkipExponent;
+    }
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int li = e / kTile, lj = e % kTile;
+        const int i = i0 + li, j = j0 + lj;
         double K0 = 0.0, KT = 0.0, K3 = 0.0, W0 = 0.0, WT = 0.0, W3 = 0.0;
-        if (j < I.n) {
-            const int gj = I.x_off + j;
-            const double Q = g.sq[gj], rQ = g.rsq[gj];
+        if (!skip_tile && i < I.n && j < I.n) {
+            const double P = g.sp[I.x_off + i], rP = g.rsp[I.x_off + i];
+            const double Q = g.sq[I.x_off + j], rQ = g.rsq[I.x_off + j];
             const double dd = (rP - rQ) * (rP - rQ);
             if (dd * iw2 < kSkipExponent) {
-                atomicMin(&s_lo, j);
-                atomicMax(&s_hi, j);
                 const double c2 = 2.0 * rP * rQ, x0 = rP * rQ, PQ = P * Q, PpQ = P + Q;
                 for (int k = 0; k < I.nt; ++k) {
                     const double k2 = dd + c2 * sy[k];
@@ -84,7 +92,7 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
                         W3 += E * f * g3;
                     }
                 }
-                const double dq = (I.mode == QDSE_COLLOCATED && i == j) ? 1.0 : 1.0 / (Q - P);
+                const double dq = (coll && i == j) ? 1.0 : 1.0 / (Q - P);
                 K0 *= pref;
                 KT *= pref * dq;
                 K3 *= pref;
@@ -95,57 +103,129 @@ __global__ void __launch_bounds__(128) k_precompute(const DevInst* __restrict__ 
                 }
             }
         }
-        const double kv[3] = {K0, KT, K3};
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            const float hi = __double2float_rn(kv[p]);
-            Khi[row + p * plane + j] = hi;
-            Klo[row + p * plane + j] = __double2float_rn(kv[p] - (double)hi);
-        }
+        const int o = li * (kTile + 1) + lj;
+        tileK[0 * S + o] = K0;
+        tileK[1 * S + o] = KT;
+        tileK[2 * S + o] = K3;
         if (WITH_W) {
-            const double wv[3] = {W0, WT, W3};
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                const float hi = __double2float_rn(wv[p]);
-                Kwhi[row + p * plane + j] = hi;
-                Kwlo[row + p * plane + j] = __double2float_rn(wv[p] - (double)hi);
+            tileK[3 * S + o] = W0;
+            tileK[4 * S + o] = WT;
+            tileK[5 * S + o] = W3;
+        }
+    }
+    __syncthreads();
+    // store the tile (rows i, columns j) and, for an off-diagonal symmetric tile, its transpose
+    const int nsets = WITH_W ? 2 : 1;
+    const bool mirror = coll && t.z != t.y;
+    for (int set = 0; set < nsets; ++set) {
+        float* Hi = set ? Kwhi : Khi;
+        float* Lo = set ? Kwlo : Klo;
+        const double* T = tileK + set * 3 * S;
+        for (int e = threadIdx.x; e < 3 * kTile * kTile; e += blockDim.x) {
+            const int p = e / (kTile * kTile), r = (e / kTile) % kTile, cc = e % kTile;
+            // direct: row i0 + r, column j0 + cc (columns up to ld are written: zero padding)
+            const int i = i0 + r, j = j0 + cc;
+            if (i < I.n && j < I.ld) {
+                const double v = (j < I.n) ? T[p * S + r * (kTile + 1) + cc] : 0.0;
+                const float h = __double2float_rn(v);
+                const long long idx = I.k_off + (long long)(3 * i + p) * I.ld + j;
+                Hi[idx] = h;
+                Lo[idx] = __double2float_rn(v - (double)h);
+            }
+            if (mirror) {
+                // transposed: row j0 + r, column i0 + cc; K_0, K_3 symmetric, K_T/(Q-P) odd
+                const int it = j0 + r, jt = i0 + cc;
+                if (it < I.n && jt < I.ld) {
+                    double v = (jt < I.n) ? T[p * S + cc * (kTile + 1) + r] : 0.0;
+                    if (p == 1) v = -v;
+                    const float h = __double2float_rn(v);
+                    const long long idx = I.k_off + (long long)(3 * it + p) * I.ld + jt;
+                    Hi[idx] = h;
+                    Lo[idx] = __double2float_rn(v - (double)h);
+                }
             }
         }
     }
-    // the nonzero entries of a row are a contiguous range of j (|sqrt P - sqrt Q| grows
-    // monotonically away from it); store it widened to multiples of 4
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int lo = s_lo, hi = s_hi + 1;
-        if (hi <= lo) {
-            lo = 0;
-            hi = 0;
-        } else {
-            lo &= ~3;
-            hi = (hi + 3) & ~3;
-            if (hi > I.ld) hi = I.ld;
-        }
-        g.band[r] = make_int2(lo, hi);
-        atomicAdd(g.nnz + b, (unsigned long long)(hi - lo));
+}
+
+// Row bands: the nonzero entries of row i are the j with (sqrt P_i - sqrt Q_j)^2 / w^2 below the
+// skip threshold, a contiguous range because sqrt Q_j increases with j; stored widened to
+// multiples of 4.  One thread per external point; the same FP64 test as the tiles.
+__global__ void k_row_bands(const DevInst* __restrict__ inst, Grid g, int ntot) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ntot) return;
+    const int b = g.row_inst[r];
+    const DevInst I = inst[b];
+    const double iw2 = 1.0 / (I.omega * I.omega);
+    const double rP = g.rsp[r];
+    const double* rq = g.rsq + I.x_off;
+    auto inside = [&](int j) { return (rP - rq[j]) * (rP - rq[j]) * iw2 < kSkipExponent; };
+    // the internal node nearest to p_i (binary search on sqrt Q), then the two ends of the
+    // contiguous range around it (binary searches)
+    int lo = 0, hi = I.n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (rq[mid] < rP) lo = mid;
+        else hi = mid;
     }
+    const int c = (fabs(rq[lo] - rP) <= fabs(rq[hi] - rP)) ? lo : hi;
+    int jl = 0, jh = 0;
+    if (inside(c)) {
+        int a = -1, in = c;  // !inside(a) (or a = -1), inside(in)
+        while (in - a > 1) {
+            const int mid = (a + in) / 2;
+            if (inside(mid)) in = mid;
+            else a = mid;
+        }
+        jl = in;
+        int in2 = c, out = I.n;  // inside(in2), !inside(out) (or out = n)
+        while (out - in2 > 1) {
+            const int mid = (in2 + out) / 2;
+            if (inside(mid)) in2 = mid;
+            else out = mid;
+        }
+        jh = in2 + 1;
+        jl &= ~3;
+        jh = (jh + 3) & ~3;
+        if (jh > I.ld) jh = I.ld;
+    }
+    g.band[r] = make_int2(jl, jh);
+    atomicAdd(g.nnz + b, (unsigned long long)(jh - jl));
 }
 
 cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
-    const size_t smem = 4 * sizeof(double) * (size_t)c->max_nt;
-    cudaError_t e0 = cudaMemsetAsync(c->grid.nnz, 0, sizeof(unsigned long long) * c->n_inst,
-                                     c->stream);
-    if (e0 != cudaSuccess) return e0;
+    cudaError_t e = cudaMemsetAsync(c->grid.nnz, 0, sizeof(unsigned long long) * c->n_inst,
+                                    c->stream);
+    if (e != cudaSuccess) return e;
+    const size_t smem =
+        ((with_w ? 2 : 1) * 3 * kTile * (kTile + 1) + 4 * (size_t)c->max_nt) * sizeof(double);
     prof_begin(c, PK_PRECOMPUTE);
     if (with_w) {
-        k_precompute<true><<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->grid, c->d_Khi,
-                                                                 c->d_Klo, c->d_Kwhi, c->d_Kwlo);
+        k_precompute_tiles<true><<<c->n_tiles, 256, smem, c->stream>>>(
+            c->d_inst, c->grid, c->d_tiles, c->d_Khi, c->d_Klo, c->d_Kwhi, c->d_Kwlo);
     } else {
-        k_precompute<false><<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->grid, c->d_Khi,
-                                                                  c->d_Klo, nullptr, nullptr);
+        k_precompute_tiles<false><<<c->n_tiles, 256, smem, c->stream>>>(
+            c->d_inst, c->grid, c->d_tiles, c->d_Khi, c->d_Klo, nullptr, nullptr);
     }
     c->launches++;
     prof_end(c);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(c, PK_PRECOMPUTE);
+    k_row_bands<<<(c->n_total + 127) / 128, 128, 0, c->stream>>>(c->d_inst, c->grid, c->n_total);
+    c->launches++;
+    prof_end(c);
     return cudaGetLastError();
+}
+
+cudaError_t configure_precompute(int max_nt) {
+    const size_t smem = (2 * 3 * kTile * (kTile + 1) + 4 * (size_t)max_nt) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_precompute_tiles<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_precompute_tiles<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
 }
 
 }  // namespace qdse

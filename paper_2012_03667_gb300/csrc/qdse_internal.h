@@ -146,6 +146,7 @@ struct Grid {              // FP64 grid arrays on the device (global point index
 };
 
 constexpr int kRows = 4;   // external points per warp in the batched sweeps
+constexpr int kTile = 32;  // kernel precompute tile edge
 
 struct HostInst {
     qdse_grid g;
@@ -189,6 +190,17 @@ struct qdse_ctx {
     bool use_tma = false;     // bulk-copy pipelined FP32 sweep configured
     int ld_max = 0;           // widest kernel row of the batch
     int sweep_kind = 0;       // 0: row-group kernel, 1: bulk-copy work-list kernel
+    int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
+    double* d_rel = nullptr;  // [n_inst] relative residual of the adjoint's fixed point
+    // CUDA graph of a chunk of ticks, replayed between polls (captured on an internal stream)
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double* g_A = nullptr;
+    const double* g_B = nullptr;
+    int g_path = -1;
+    long long g_launches = 0;  // kernels per replay
+    int n_tiles = 0;
     long long tick = 0;       // sweeps issued since the last init (selects the work-list buffer)
     qdse::DevInst* h_inst_pinned = nullptr;
 
@@ -220,6 +232,7 @@ void build_angular(int nt, double* z, double* y, double* s2, double* w);
 
 // ---- kernel launchers (return cudaError_t of the launch) -------------------------------------
 cudaError_t launch_precompute(qdse_ctx* c, bool with_omega_derivative);
+cudaError_t configure_precompute(int max_nt);
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_sweep32_tma(qdse_ctx* c, const double* A, const double* B);
@@ -250,7 +263,8 @@ cudaError_t launch_prep64(qdse_ctx* c, const double* A, const double* B, const d
                           const double* vB);
 cudaError_t launch_rel64(qdse_ctx* c, const double* A, const double* B, const double* FA,
                          const double* FB, double* rel);
-cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB);
+cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB,
+                                const double* rel, double not_fixed);
 cudaError_t launch_adjoint_grads(qdse_ctx* c, const double* A, const double* B,
                                  const double* lam, const double* F, const double* Fw,
                                  double* g_params, int* inst_status);
