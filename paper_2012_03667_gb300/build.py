@@ -14,8 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqdse.so")
-SOURCES = ["api.cu", "k_sweep.cu", "k_sweep_tma.cu", "k_precompute.cu", "k_adjoint.cu",
-           "grid.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "k_sweep.cu", "k_precompute.cu", "k_adjoint.cu", "grid.cpp", "noalloc.cu"]
 HEADERS = ["qdse_internal.h", os.path.join("..", "..", "include", "qdse.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -108,7 +108,7 @@ void free_ctx(qdse_ctx* c) {
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
                     c->grid.groups, c->grid.nnz, c->work.items, c->work.item_count,
                     c->work.work_ctr, c->grid.gdesc, c->grid.gphase, c->work.ilist,
-                    c->work.glist, c->work.lcount, c->d_tiles, c->d_rel};
+                    c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -156,6 +156,7 @@ qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
     QCHECK(c, cudaMemcpyAsync(c->d_inst, c->h_inst_pinned, sizeof(DevInst) * c->n_inst,
                               cudaMemcpyHostToDevice, c->stream),
            "upload parameters");
+    QCHECK(c, launch_group_params(c), "group parameters");
     return QDSE_OK;
 }
 
@@ -207,7 +208,7 @@ cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
     if (otf) {
         e = launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1);
     } else if (c->sweep_kind == 1) {
-        e = launch_sweep32_tma(c, A, B);
+        e = launch_tick_ring(c, A, B);
     } else {
         e = launch_tick(c, A, B);
     }
@@ -271,7 +272,7 @@ qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool
         QCHECK(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "order the solve stream");
         c->stream = c->gstream;
     }
-    const int path = (c->opt.precision == QDSE_FP64) ? 2 : c->sweep_kind;
+    const int path = (c->opt.precision == QDSE_FP64) ? -2 : c->sweep_kind;
     int chunk = 4;
     qdse_status st = QDSE_OK;
     while (true) {
@@ -416,7 +417,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
             d.x_off = h.x_off;
             d.ld = h.ld;
             d.kbase = h.k_off + (long long)i0 * 3 * h.ld;
-            d.plane = h.ld;
+            d.mode = h.g.grid_mode;
             gdesc.push_back(d);
         }
     }
@@ -461,6 +462,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->grid.stc, 3 * (size_t)N);
     CALLOC(c->grid.sta, N);
     CALLOC(c->grid.sp32, N);
+    CALLOC(c->grid.ktd, N);
     CALLOC(c->grid.sq32, N);
     CALLOC(c->grid.z, t);
     CALLOC(c->grid.y, t);
@@ -546,8 +548,6 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         }
     }
     c->work.nv = v;
-    c->use_tma = (c->n_sms > 0) && configure_sweep32_tma(c->ld_max) == cudaSuccess;
-    cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
@@ -563,15 +563,19 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         return s;
     }
     {
-        // sweep kernel: the row-group kernel by default; QDSE_SWEEP=items selects the bulk-copy
-        // work-list kernel (same results, kept for comparison on new hardware)
+        // FP32 sweep kernel: the shared-memory ring by default; QDSE_SWEEP=groups selects the
+        // register-only row-group kernel (same results up to rounding order)
         const char* k = std::getenv("QDSE_SWEEP");
-        c->sweep_kind = (k && std::string(k) == "items" && c->use_tma) ? 1 : 0;
+        const bool ring_ok = configure_tick_ring() == cudaSuccess;
+        cudaGetLastError();
+        c->sweep_kind = ring_ok ? 1 : 0;
+        if (k && std::string(k) == "groups") c->sweep_kind = 0;
     }
     // zero the padding of the node vectors once; descriptors get their layout now and their
     // parameters on every call
     e = cudaMemset(c->work.vec32, 0, sizeof(float) * 5 * (size_t)v);
     if (e == cudaSuccess) e = cudaMemset(c->work.dvec32, 0, sizeof(float) * 5 * (size_t)v);
+    if (e == cudaSuccess) e = cudaMemset(c->grid.ktd, 0, sizeof(float) * (size_t)c->n_total);
     if (e == cudaSuccess) {
         std::vector<qdse_params> zero(n_inst, qdse_params{0.0, 1.0, 0.0, 0.0});
         bool rb = false;

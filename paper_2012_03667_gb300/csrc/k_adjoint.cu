@@ -103,8 +103,7 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     const DevInst I = inst[bi];
     const int l = r - I.x_off;
     const int o = I.x_off;
-    const long long plane = I.ld;  // planes of a row are adjacent
-    const long long row = I.k_off + (long long)l * 3 * I.ld;
+    const KRow row(I, l);
     const double* va = w.vec64 + o;
     const double* vb = w.vec64 + ntot + o;
     const double* v1 = w.vec64 + 2 * ntot + o;
@@ -125,9 +124,10 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     const int mlo = bd.x, mhi = min(bd.y, I.n);
     if (ctl->vertex == QDSE_VERTEX_BC) {
         for (int m = mlo + lane; m < mhi; m += 32) {
-            const double K0 = (double)Khi[row + m] + (double)Klo[row + m];
-            double KT = (double)Khi[row + plane + m] + (double)Klo[row + plane + m];
-            const double K3 = (double)Khi[row + 2 * plane + m] + (double)Klo[row + 2 * plane + m];
+            const long long o0 = row.off(0, m), o1 = row.off(1, m), o2 = row.off(2, m);
+            const double K0 = (double)Khi[o0] + (double)Klo[o0];
+            double KT = (double)Khi[o1] + (double)Klo[o1];
+            const double K3 = (double)Khi[o2] + (double)Klo[o2];
             if (m == l) KT = 0.0;
             // own part: l plays the row index, m the partner
             const double u1 = v1[m], u2 = v2[m], u3 = v3[m];
@@ -150,8 +150,9 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
         }
     } else {
         for (int m = mlo + lane; m < mhi; m += 32) {
-            const double K0 = (double)Khi[row + m] + (double)Klo[row + m];
-            const double K3 = (double)Khi[row + 2 * plane + m] + (double)Klo[row + 2 * plane + m];
+            const long long o0 = row.off(0, m), o2 = row.off(2, m);
+            const double K0 = (double)Khi[o0] + (double)Klo[o0];
+            const double K3 = (double)Khi[o2] + (double)Klo[o2];
             const double ai = al[m], bi = be[m];
             gAl += ai * (el + Al * ca) * K3 + bi * 3.0 * Bl * ca * K0;
             gBl += ai * Al * cb * K3 + bi * 3.0 * (el + Bl * cb) * K0;
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
         // removable-limit terms of every row i whose value depends on x_l
         const int i0 = l - 2 < 0 ? 0 : l - 2, i1 = l + 2 > I.n - 1 ? I.n - 1 : l + 2;
         for (int i = i0; i <= i1; ++i) {
-            const long long rowi = I.k_off + (long long)i * 3 * I.ld;
-            const double KTd = (double)Khi[rowi + plane + i] + (double)Klo[rowi + plane + i];
+            const long long od = KRow(I, i).off(1, i);
+            const double KTd = (double)Khi[od] + (double)Klo[od];
             const double ai = al[i], bi = be[i];
             const double u1 = v1[i], u2 = v2[i], Pi = sp[i];
             const double dA = w.dia64[o + i], dB = w.dia64[ntot + o + i];

@@ -11,6 +11,8 @@
 //
 // Every entry is evaluated in FP64 and stored as a double-float pair (hi = fl32(K),
 // lo = fl32(K - hi)): the FP32 sweeps read hi, the FP64 residual reads hi + lo (about 48 bits).
+// Both pools use the group-tile layout of kpos (qdse_internal.h); the collocated diagonal K_T of
+// every row is also kept in a per-point array.
 // Optionally the omega-derivatives dK_n/dw (factor -4/w + 2 k^2/w^3 on each term) are stored in a
 // second pool for the adjoint's dF/dw.
 //
@@ -117,32 +119,40 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
     // store the tile (rows i, columns j) and, for an off-diagonal symmetric tile, its transpose
     const int nsets = WITH_W ? 2 : 1;
     const bool mirror = coll && t.z != t.y;
+    // Threads walk the destination in layout order: row group rg of the tile, 4-column block
+    // cb, stored plane-row slot (plane-row m = slot ^ kswz), column inside the block; for full
+    // groups consecutive threads write consecutive floats.
+    static_assert(kTile % kRows == 0 && kTile % 4 == 0 && kPoolTile % kTile == 0,
+                  "precompute tiles must cover whole row groups and sit inside one pool tile");
+    constexpr int kRun = 3 * kRows * kTile;  // floats of one row group inside the tile
     for (int set = 0; set < nsets; ++set) {
         float* Hi = set ? Kwhi : Khi;
         float* Lo = set ? Kwlo : Klo;
         const double* T = tileK + set * 3 * S;
-        for (int e = threadIdx.x; e < 3 * kTile * kTile; e += blockDim.x) {
-            const int p = e / (kTile * kTile), r = (e / kTile) % kTile, cc = e % kTile;
-            // direct: row i0 + r, column j0 + cc (columns up to ld are written: zero padding)
-            const int i = i0 + r, j = j0 + cc;
-            if (i < I.n && j < I.ld) {
-                const double v = (j < I.n) ? T[p * S + r * (kTile + 1) + cc] : 0.0;
+        for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
+            // pass 0: rows i0.., columns j0..; pass 1 (mirror): rows j0.., columns i0.., the
+            // transposed values (K_0, K_3 symmetric, K_T/(Q-P) odd)
+            const int rb0 = pass ? j0 : i0, cb0 = pass ? i0 : j0;
+            for (int e = threadIdx.x; e < 3 * kTile * kTile; e += blockDim.x) {
+                const int rg = e / kRun, off = e % kRun;
+                const int cb = off / (3 * kRows * 4), wq = off % (3 * kRows * 4);
+                const int slot = wq >> 2, cc = cb * 4 + (wq & 3);
+                const int g0 = rb0 + rg * kRows;
+                const int nr = min(kRows, I.n - g0);
+                const int j = cb0 + cc;
+                if (nr <= 0 || slot >= 3 * nr || j >= I.ld) continue;
+                const int m = slot ^ kswz(nr, j >> 2);
+                const int rr = rg * kRows + m / 3, p = m % 3, i = rb0 + rr;
+                double v = 0.0;
+                if (j < I.n) {
+                    v = pass ? T[p * S + cc * (kTile + 1) + rr] : T[p * S + rr * (kTile + 1) + cc];
+                    if (pass && p == 1) v = -v;
+                }
                 const float h = __double2float_rn(v);
-                const long long idx = I.k_off + (long long)(3 * i + p) * I.ld + j;
+                const long long idx = kpos(I.k_off, I.n, I.ld, i, p, j);
                 Hi[idx] = h;
                 Lo[idx] = __double2float_rn(v - (double)h);
-            }
-            if (mirror) {
-                // transposed: row j0 + r, column i0 + cc; K_0, K_3 symmetric, K_T/(Q-P) odd
-                const int it = j0 + r, jt = i0 + cc;
-                if (it < I.n && jt < I.ld) {
-                    double v = (jt < I.n) ? T[p * S + cc * (kTile + 1) + r] : 0.0;
-                    if (p == 1) v = -v;
-                    const float h = __double2float_rn(v);
-                    const long long idx = I.k_off + (long long)(3 * it + p) * I.ld + jt;
-                    Hi[idx] = h;
-                    Lo[idx] = __double2float_rn(v - (double)h);
-                }
+                if (set == 0 && coll && p == 1 && i == j) g.ktd[I.x_off + i] = h;
             }
         }
     }

@@ -117,10 +117,17 @@ __device__ __forceinline__ double at_q(const S* F, int gj, double wt) {
     return v;
 }
 
-// Writes a, b, u1, u2, u3 (stride ntot) for every node of instance I, and the diagonal stencil
-// quotients dA/ds, dB/ds at p_i (collocated).  xa, xb: the iterate (FP32 or FP64 storage).
-// Component c of node j goes to vec[c * vs + vb + j] (vs, vb: stride and instance base of the
-// layout in use; the FP32 vectors are padded, the FP64 ones use the global point index).
+// Writes a, b, u1, u2, u3 for every node of instance I, and the diagonal stencil quotients
+// dA/ds, dB/ds at p_i (collocated).  xa, xb: the iterate (FP32 or FP64 storage).  FP64 vectors
+// put component c of node j at vec[c * vs + vb + j] (vs = ntot, vb = the instance's first global
+// point); FP32 vectors use the blocked layout vpos(vb + j, c) with vb = the instance's first
+// padded node (vs unused).
+template <typename T>
+__device__ __forceinline__ T& vslot(T* vec, int vs, int x, int c) {
+    if constexpr (sizeof(T) == sizeof(float)) return vec[vpos(x, c)];
+    else return vec[(size_t)c * vs + x];
+}
+
 template <typename S, typename T>
 __device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const S* xa,
                                 const S* xb, T* vec, int vs, int vb, T* dia, int tid = -1,
@@ -135,12 +142,11 @@ __device__ void prepare_vectors(const DevInst& I, const Grid& g, int ntot, const
         const double a = at_q(xa, gj, wt), b = at_q(xb, gj, wt);
         const double Q = g.sq[gj];
         const double e = g.W[gj] / (Q * a * a + b * b);
-        T* v = vec + vb + j;
-        v[0] = (T)a;
-        v[vs] = (T)b;
-        v[2 * vs] = (T)(e * b);
-        v[3 * vs] = (T)(e * a);
-        v[4 * vs] = (T)(e * a * Q);
+        vslot(vec, vs, vb + j, 0) = (T)a;
+        vslot(vec, vs, vb + j, 1) = (T)b;
+        vslot(vec, vs, vb + j, 2) = (T)(e * b);
+        vslot(vec, vs, vb + j, 3) = (T)(e * a);
+        vslot(vec, vs, vb + j, 4) = (T)(e * a * Q);
         if (I.mode == QDSE_COLLOCATED) {
             const int s0 = I.x_off + g.sta[gj];
             const double* c = g.stc + 3 * (size_t)gj;
@@ -172,12 +178,11 @@ __device__ void prepare_tangent(const DevInst& I, const Grid& g, int ntot, const
         const double e = g.W[gj] / d;
         const double de = -e * (2.0 * Q * a * da + 2.0 * b * db) / d;
         const double du2 = de * a + e * da;
-        T* v = dvec + vbase + j;
-        v[0] = (T)da;
-        v[vs] = (T)db;
-        v[2 * vs] = (T)(de * b + e * db);
-        v[3 * vs] = (T)du2;
-        v[4 * vs] = (T)(du2 * Q);
+        vslot(dvec, vs, vbase + j, 0) = (T)da;
+        vslot(dvec, vs, vbase + j, 1) = (T)db;
+        vslot(dvec, vs, vbase + j, 2) = (T)(de * b + e * db);
+        vslot(dvec, vs, vbase + j, 3) = (T)du2;
+        vslot(dvec, vs, vbase + j, 4) = (T)(du2 * Q);
         if (I.mode == QDSE_COLLOCATED) {
             const int s0 = I.x_off + g.sta[gj];
             const double* c = g.stc + 3 * (size_t)gj;
@@ -200,8 +205,7 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
                                         const float* __restrict__ Klo, int vertex, int jlo,
                                         int jhi, T& outA, T& outB) {
     if (jhi > I.n) jhi = I.n;
-    const long long plane = I.ld;  // planes of a row are adjacent
-    const long long row = I.k_off + (long long)i * 3 * I.ld;
+    const KRow row(I, i);
     const T* va = vec + I.x_off;
     const T* vb = vec + ntot + I.x_off;
     const T* v1 = vec + 2 * ntot + I.x_off;
@@ -212,9 +216,9 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
 #pragma unroll 4
         for (int j = jlo + lane; j < jhi; j += 32) {
             const T a = va[j], b = vb[j], u1 = v1[j], u2 = v2[j], u3 = v3[j];
-            const T K0 = kload<T, LO>(Khi, Klo, row + j);
-            const T KT = kload<T, LO>(Khi, Klo, row + plane + j);
-            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            const T K0 = kload<T, LO>(Khi, Klo, row.off(0, j));
+            const T KT = kload<T, LO>(Khi, Klo, row.off(1, j));
+            const T K3 = kload<T, LO>(Khi, Klo, row.off(2, j));
             const T da = a - Ai, db = b - Bi, sa = Ai + a;
             const T cT = -u1 * db - (T)0.5 * (Pi * u2 + u3) * da;
             sA += cT * KT + (T)0.5 * u2 * sa * K3;
@@ -223,8 +227,8 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
     } else {
 #pragma unroll 4
         for (int j = jlo + lane; j < jhi; j += 32) {
-            const T K0 = kload<T, LO>(Khi, Klo, row + j);
-            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            const T K0 = kload<T, LO>(Khi, Klo, row.off(0, j));
+            const T K3 = kload<T, LO>(Khi, Klo, row.off(2, j));
             sA += v2[j] * K3;
             sB += (T)3 * v1[j] * K0;
         }
@@ -232,7 +236,7 @@ __device__ __forceinline__ void row_map(int lane, const DevInst& I, int i, T Pi,
     sA = warp_sum(sA);
     sB = warp_sum(sB);
     if (vertex == QDSE_VERTEX_BC && I.mode == QDSE_COLLOCATED) {
-        const T KTd = kload<T, LO>(Khi, Klo, row + plane + i);
+        const T KTd = kload<T, LO>(Khi, Klo, row.off(1, i));
         const T dAi = dia[I.x_off + i], dBi = dia[ntot + I.x_off + i];
         sA += (-v1[i] * dBi - Pi * v2[i] * dAi) * KTd;
         sB += (v1[i] * dAi - v2[i] * dBi) * KTd;
@@ -252,8 +256,7 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
                                             const float* __restrict__ Klo, int vertex, int jlo,
                                             int jhi, T& outA, T& outB) {
     if (jhi > I.n) jhi = I.n;
-    const long long plane = I.ld;  // planes of a row are adjacent
-    const long long row = I.k_off + (long long)i * 3 * I.ld;
+    const KRow row(I, i);
     const int o = I.x_off;
     T sA = 0, sB = 0;
     if (vertex == QDSE_VERTEX_BC) {
@@ -265,9 +268,9 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
             const T ea = dvec[o + j], eb = dvec[ntot + o + j];
             const T e1 = dvec[2 * ntot + o + j], e2 = dvec[3 * ntot + o + j],
                     e3 = dvec[4 * ntot + o + j];
-            const T K0 = kload<T, LO>(Khi, Klo, row + j);
-            const T KT = kload<T, LO>(Khi, Klo, row + plane + j);
-            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            const T K0 = kload<T, LO>(Khi, Klo, row.off(0, j));
+            const T KT = kload<T, LO>(Khi, Klo, row.off(1, j));
+            const T K3 = kload<T, LO>(Khi, Klo, row.off(2, j));
             const T da = a - Ai, db = b - Bi, sa = Ai + a;
             const T dda = ea - dAi, ddb = eb - dBi, dsa = dAi + ea;
             const T t = Pi * u2 + u3, dt = Pi * e2 + e3;
@@ -279,8 +282,8 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
     } else {
 #pragma unroll 4
         for (int j = jlo + lane; j < jhi; j += 32) {
-            const T K0 = kload<T, LO>(Khi, Klo, row + j);
-            const T K3 = kload<T, LO>(Khi, Klo, row + 2 * plane + j);
+            const T K0 = kload<T, LO>(Khi, Klo, row.off(0, j));
+            const T K3 = kload<T, LO>(Khi, Klo, row.off(2, j));
             sA += dvec[3 * ntot + o + j] * K3;
             sB += (T)3 * dvec[2 * ntot + o + j] * K0;
         }
@@ -288,7 +291,7 @@ __device__ __forceinline__ void row_tangent(int lane, const DevInst& I, int i, T
     sA = warp_sum(sA);
     sB = warp_sum(sB);
     if (vertex == QDSE_VERTEX_BC && I.mode == QDSE_COLLOCATED) {
-        const T KTd = kload<T, LO>(Khi, Klo, row + plane + i);
+        const T KTd = kload<T, LO>(Khi, Klo, row.off(1, i));
         const int gi = o + i;
         const T u1 = vec[2 * ntot + gi], u2 = vec[3 * ntot + gi];
         const T e1 = dvec[2 * ntot + gi], e2 = dvec[3 * ntot + gi];
@@ -331,6 +334,106 @@ __device__ __forceinline__ float pick(const float4& v, int d) {
     return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
 }
 
+// Per-row state of the FP32 sweep of one row group (a lane's partial sums and the row constants).
+struct Rows32 {
+    float Ai[kRows], Bi[kRows], Pi[kRows], dAi[kRows], dBi[kRows], sA[kRows], sB[kRows];
+    float qA[kRows], qB[kRows], eqA[kRows], eqB[kRows];
+    double Pd[kRows];
+};
+
+template <bool TAN>
+__device__ __forceinline__ void rows32_load(Rows32& R, const GroupDesc& d, const Grid& g,
+                                            const Work& w, int ntot, int collocated) {
+    const int o = d.x_off + d.i0;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        R.sA[r] = 0.f;
+        R.sB[r] = 0.f;
+        const bool v = r < d.nr;
+        R.Pd[r] = v ? g.sp[o + r] : 1.0;
+        R.Ai[r] = v ? w.x32[o + r] : 0.f;
+        R.Bi[r] = v ? w.x32[ntot + o + r] : 0.f;
+        R.Pi[r] = v ? g.sp32[o + r] : 0.f;
+        R.dAi[r] = (v && TAN) ? w.d32[o + r] : 0.f;
+        R.dBi[r] = (v && TAN) ? w.d32[ntot + o + r] : 0.f;
+        R.qA[r] = (v && collocated) ? w.dia32[o + r] : 0.f;
+        R.qB[r] = (v && collocated) ? w.dia32[ntot + o + r] : 0.f;
+        R.eqA[r] = (v && collocated && TAN) ? w.ddia32[o + r] : 0.f;
+        R.eqB[r] = (v && collocated && TAN) ? w.ddia32[ntot + o + r] : 0.f;
+    }
+}
+
+// The pair sums of one lane's 4 consecutive columns for every row of the group.  K(r, p) returns
+// the 4 kernel entries of plane p of row r at those columns; dd0 = i0 - (first column) locates
+// the diagonal (the removable limit of row i0 + r sits at column offset dd0 + r when in [0, 4)).
+template <bool TAN, typename KLoad>
+__device__ __forceinline__ void rows32_chunk(Rows32& R, const KLoad& K, int nr, int dd0, bool bc,
+                                             int collocated, const float4& a, const float4& b,
+                                             const float4& u1, const float4& u2,
+                                             const float4& u3, const float4& ea,
+                                             const float4& eb, const float4& e1,
+                                             const float4& e2, const float4& e3) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        if (r < nr) {
+            const float4 K0 = K(r, 0), K3 = K(r, 2);
+            if (bc) {
+                const float4 KT = K(r, 1);
+                if (!TAN) {
+                    pair32(a.x, b.x, u1.x, u2.x, u3.x, K0.x, KT.x, K3.x, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.y, b.y, u1.y, u2.y, u3.y, K0.y, KT.y, K3.y, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.z, b.z, u1.z, u2.z, u3.z, K0.z, KT.z, K3.z, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.w, b.w, u1.w, u2.w, u3.w, K0.w, KT.w, K3.w, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                } else {
+                    tpair32(a.x, b.x, u1.x, u2.x, u3.x, ea.x, eb.x, e1.x, e2.x, e3.x, K0.x, KT.x, K3.x, R.Ai[r], R.Bi[r], R.dAi[r], R.dBi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    tpair32(a.y, b.y, u1.y, u2.y, u3.y, ea.y, eb.y, e1.y, e2.y, e3.y, K0.y, KT.y, K3.y, R.Ai[r], R.Bi[r], R.dAi[r], R.dBi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    tpair32(a.z, b.z, u1.z, u2.z, u3.z, ea.z, eb.z, e1.z, e2.z, e3.z, K0.z, KT.z, K3.z, R.Ai[r], R.Bi[r], R.dAi[r], R.dBi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    tpair32(a.w, b.w, u1.w, u2.w, u3.w, ea.w, eb.w, e1.w, e2.w, e3.w, K0.w, KT.w, K3.w, R.Ai[r], R.Bi[r], R.dAi[r], R.dBi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                }
+                // removable limit q^2 -> p^2 of row i = i0 + r, by the lane holding column i
+                const int dd = dd0 + r;
+                if (collocated && dd >= 0 && dd < 4) {
+                    const float KTd = pick(KT, dd), x1 = pick(u1, dd), x2 = pick(u2, dd);
+                    if (!TAN) {
+                        R.sA[r] += (-x1 * R.qB[r] - R.Pi[r] * x2 * R.qA[r]) * KTd;
+                        R.sB[r] += (x1 * R.qA[r] - x2 * R.qB[r]) * KTd;
+                    } else {
+                        const float y1 = pick(e1, dd), y2 = pick(e2, dd);
+                        R.sA[r] += (-y1 * R.qB[r] - x1 * R.eqB[r] -
+                                    R.Pi[r] * (y2 * R.qA[r] + x2 * R.eqA[r])) * KTd;
+                        R.sB[r] += (y1 * R.qA[r] + x1 * R.eqA[r] - y2 * R.qB[r] - x2 * R.eqB[r]) * KTd;
+                    }
+                }
+            } else {
+                const float4 p2 = TAN ? e2 : u2, p1 = TAN ? e1 : u1;
+                R.sA[r] += p2.x * K3.x + p2.y * K3.y + p2.z * K3.z + p2.w * K3.w;
+                R.sB[r] += 3.f * (p1.x * K0.x + p1.y * K0.y + p1.z * K0.z + p1.w * K0.w);
+            }
+        }
+    }
+}
+
+// Warp totals of the group's 2 kRows sums and the stores of F(x) (or J delta) for its rows.
+template <bool TAN>
+__device__ __forceinline__ void rows32_store(const Rows32& R, const GroupDesc& d, int lane,
+                                             const Work& w, int ntot, double scale, double m) {
+    const float tot = group_totals(R.sA, R.sB, lane);
+    const int qv = group_total_index(lane), r = qv % kRows;
+    double P = 1.0;  // p_i^2 of the lane's row (unrolled select keeps R in registers)
+#pragma unroll
+    for (int k = 0; k < kRows; ++k)
+        if (k == r) P = R.Pd[k];
+    if (group_total_leader(lane) && r < d.nr) {
+        const int gi = d.x_off + d.i0 + r;
+        if (qv < kRows) {
+            w.xn32[gi] = TAN ? (float)(scale * (double)tot / P)
+                             : (float)(1.0 + scale * (double)tot / P);
+        } else {
+            w.xn32[ntot + gi] = TAN ? (float)(scale * (double)tot) : (float)(m + scale * (double)tot);
+        }
+    }
+}
+
 // FP32 sweep (or, with TAN, tangent sweep) of one row group: one warp, lanes over 4-node column
 // chunks (16-byte loads) inside the union of the rows' nonzero bands.  The group descriptor carries
 // every offset, so all loads of the group issue after a single round trip; the node vectors of a
@@ -340,123 +443,32 @@ template <bool TAN>
 __device__ __forceinline__ void group32(int lane, const GroupDesc& d, const Grid& g,
                                         const Work& w, int ntot, const float* __restrict__ Khi,
                                         int vertex, int collocated, double scale, double m) {
-    static_assert(kRows == 4, "the butterfly reduction below is written for 4 rows");
-    const int nr = d.nr;
-    const int o = d.x_off + d.i0;
-    const int nv = w.nv;
-    float Ai[kRows], Bi[kRows], Pi[kRows], dAi[kRows], dBi[kRows], sA[kRows], sB[kRows];
-    float qA[kRows], qB[kRows], eqA[kRows], eqB[kRows];
-    double Pd[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        sA[r] = 0.f;
-        sB[r] = 0.f;
-        const bool v = r < nr;
-        Pd[r] = v ? g.sp[o + r] : 1.0;
-        Ai[r] = v ? w.x32[o + r] : 0.f;
-        Bi[r] = v ? w.x32[ntot + o + r] : 0.f;
-        Pi[r] = v ? g.sp32[o + r] : 0.f;
-        dAi[r] = (v && TAN) ? w.d32[o + r] : 0.f;
-        dBi[r] = (v && TAN) ? w.d32[ntot + o + r] : 0.f;
-        qA[r] = (v && collocated) ? w.dia32[o + r] : 0.f;
-        qB[r] = (v && collocated) ? w.dia32[ntot + o + r] : 0.f;
-        eqA[r] = (v && collocated && TAN) ? w.ddia32[o + r] : 0.f;
-        eqB[r] = (v && collocated && TAN) ? w.ddia32[ntot + o + r] : 0.f;
-    }
-    const float* vb = w.vec32 + d.v_off;
-    const float* db_ = w.dvec32 + d.v_off;
+    Rows32 R;
+    rows32_load<TAN>(R, d, g, w, ntot, collocated);
     const float* kb = Khi + d.kbase;
-    const long long plane = d.plane;
+    const int nb = 3 * d.nr * 4;  // floats of one 4-column block
     const bool bc = (vertex == QDSE_VERTEX_BC);
     for (int c = d.jlo + 4 * lane; c < d.jhi; c += 128) {
-        const float4 a = ld4(vb + c), b = ld4(vb + nv + c), u1 = ld4(vb + 2 * nv + c),
-                     u2 = ld4(vb + 3 * nv + c), u3 = ld4(vb + 4 * nv + c);
+        const float* vb = w.vec32 + vpos(d.v_off + c, 0);
+        const float4 a = ld4(vb), b = ld4(vb + 4), u1 = ld4(vb + 8), u2 = ld4(vb + 12),
+                     u3 = ld4(vb + 16);
         float4 ea, eb, e1, e2, e3;
         if (TAN) {
-            ea = ld4(db_ + c);
-            eb = ld4(db_ + nv + c);
-            e1 = ld4(db_ + 2 * nv + c);
-            e2 = ld4(db_ + 3 * nv + c);
-            e3 = ld4(db_ + 4 * nv + c);
+            const float* db_ = w.dvec32 + vpos(d.v_off + c, 0);
+            ea = ld4(db_);
+            eb = ld4(db_ + 4);
+            e1 = ld4(db_ + 8);
+            e2 = ld4(db_ + 12);
+            e3 = ld4(db_ + 16);
         }
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            if (r < nr) {
-                const float* kr = kb + (long long)r * 3 * d.ld + c;
-                const float4 K0 = ld4(kr), K3 = ld4(kr + 2 * plane);
-                if (bc) {
-                    const float4 KT = ld4(kr + plane);
-                    if (!TAN) {
-                        pair32(a.x, b.x, u1.x, u2.x, u3.x, K0.x, KT.x, K3.x, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
-                        pair32(a.y, b.y, u1.y, u2.y, u3.y, K0.y, KT.y, K3.y, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
-                        pair32(a.z, b.z, u1.z, u2.z, u3.z, K0.z, KT.z, K3.z, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
-                        pair32(a.w, b.w, u1.w, u2.w, u3.w, K0.w, KT.w, K3.w, Ai[r], Bi[r], Pi[r], sA[r], sB[r]);
-                    } else {
-                        tpair32(a.x, b.x, u1.x, u2.x, u3.x, ea.x, eb.x, e1.x, e2.x, e3.x, K0.x, KT.x, K3.x, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
-                        tpair32(a.y, b.y, u1.y, u2.y, u3.y, ea.y, eb.y, e1.y, e2.y, e3.y, K0.y, KT.y, K3.y, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
-                        tpair32(a.z, b.z, u1.z, u2.z, u3.z, ea.z, eb.z, e1.z, e2.z, e3.z, K0.z, KT.z, K3.z, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
-                        tpair32(a.w, b.w, u1.w, u2.w, u3.w, ea.w, eb.w, e1.w, e2.w, e3.w, K0.w, KT.w, K3.w, Ai[r], Bi[r], dAi[r], dBi[r], Pi[r], sA[r], sB[r]);
-                    }
-                    // removable limit q^2 -> p^2 of row i = i0 + r, by the lane holding column i
-                    const int dd = d.i0 + r - c;
-                    if (collocated && dd >= 0 && dd < 4) {
-                        const float KTd = pick(KT, dd), x1 = pick(u1, dd), x2 = pick(u2, dd);
-                        if (!TAN) {
-                            sA[r] += (-x1 * qB[r] - Pi[r] * x2 * qA[r]) * KTd;
-                            sB[r] += (x1 * qA[r] - x2 * qB[r]) * KTd;
-                        } else {
-                            const float y1 = pick(e1, dd), y2 = pick(e2, dd);
-                            sA[r] += (-y1 * qB[r] - x1 * eqB[r] - Pi[r] * (y2 * qA[r] + x2 * eqA[r])) * KTd;
-                            sB[r] += (y1 * qA[r] + x1 * eqA[r] - y2 * qB[r] - x2 * eqB[r]) * KTd;
-                        }
-                    }
-                } else {
-                    const float4 p2 = TAN ? e2 : u2, p1 = TAN ? e1 : u1;
-                    sA[r] += p2.x * K3.x + p2.y * K3.y + p2.z * K3.z + p2.w * K3.w;
-                    sB[r] += 3.f * (p1.x * K0.x + p1.y * K0.y + p1.z * K0.z + p1.w * K0.w);
-                }
-            }
-        }
+        const float* kc = kb + 3LL * d.nr * kPoolTile * (c / kPoolTile) +
+                          (long long)((c % kPoolTile) >> 2) * nb;
+        const int sw = kswz(d.nr, c >> 2);
+        auto K = [&](int r, int pl) { return ld4(kc + ((3 * r + pl) ^ sw) * 4); };
+        rows32_chunk<TAN>(R, K, d.nr, d.i0 - c, bc, collocated, a, b, u1, u2, u3, ea, eb, e1, e2,
+                          e3);
     }
-    // reduce the 2 kRows partial sums at once: lane 4q ends with the total of value q
-    // (q < kRows: sA[q]; q >= kRows: sB[q - kRows]) after 4 + 2 + 1 + 2 shuffles
-    float v4[4];
-    {
-        const bool hi = (lane >> 4) & 1;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float keep = hi ? sB[k] : sA[k], send = hi ? sA[k] : sB[k];
-            v4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
-    }
-    float v2[2];
-    {
-        const bool hi = (lane >> 3) & 1;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float keep = hi ? v4[k + 2] : v4[k], send = hi ? v4[k] : v4[k + 2];
-            v2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-    }
-    float tot;
-    {
-        const bool hi = (lane >> 2) & 1;
-        const float keep = hi ? v2[1] : v2[0], send = hi ? v2[0] : v2[1];
-        tot = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    tot += __shfl_xor_sync(0xffffffffu, tot, 2);
-    tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-    const int q = lane >> 2;
-    const int r = q & 3;
-    if ((lane & 3) == 0 && r < nr) {
-        const int gi = o + r;
-        if (q < 4) {
-            w.xn32[gi] = TAN ? (float)(scale * (double)tot / Pd[r])
-                             : (float)(1.0 + scale * (double)tot / Pd[r]);
-        } else {
-            w.xn32[ntot + gi] = TAN ? (float)(scale * (double)tot) : (float)(m + scale * (double)tot);
-        }
-    }
+    rows32_store<TAN>(R, d, lane, w, ntot, scale, m);
 }
 
 // One tick of the batched solve: every row group of every unfinished instance advances by the
@@ -488,6 +500,16 @@ __device__ __forceinline__ void tick_group(const GroupDesc& d, int phase, int la
             }
         }
     }
+}
+
+// Copy every instance's parameters into its row groups' descriptors (after each upload).
+__global__ void k_group_params(const DevInst* __restrict__ inst, Grid g, int ngroups) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ngroups) return;
+    const DevInst I = inst[g.gdesc[t].b];
+    g.gdesc[t].mode = I.mode;
+    g.gdesc[t].D = I.D;
+    g.gdesc[t].m = I.m;
 }
 
 // Narrow every group's column range to the union of its rows' nonzero bands.
@@ -838,9 +860,39 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
     T.sync();
 }
 
+// Pool offset of columns [c0, ...) of a row group's block; a column range inside one pool tile
+// is one contiguous run of (c1 - c0) * 3 nr floats from here (kpos).
+__device__ __forceinline__ long long group_run(const GroupDesc& d, int c0) {
+    return d.kbase + 3LL * d.nr * kPoolTile * (c0 / kPoolTile) +
+           (long long)((c0 % kPoolTile) >> 2) * 3 * d.nr * 4;
+}
+
+// Ask L2 to fetch the kernel block and node vectors of one row group ahead of its sweep: lane t
+// takes the part of the union band [jlo, jhi) in the t-th pool tile it touches, lane 31 the node
+// vectors (one run in the blocked layout).  All runs are 16-byte aligned multiples of 16 bytes.
+__device__ __forceinline__ void prefetch_group(const GroupDesc& d, int lane, const Work& w,
+                                               const float* __restrict__ Khi) {
+    if (d.jhi <= d.jlo) return;
+    const float* p = nullptr;
+    int bytes = 0;
+    const int t = d.jlo / kPoolTile + lane;
+    if (lane < 31 && t * kPoolTile < d.jhi) {
+        const int c0 = max(d.jlo, t * kPoolTile), c1 = min(d.jhi, (t + 1) * kPoolTile);
+        p = Khi + group_run(d, c0);
+        bytes = (c1 - c0) * 3 * d.nr * 4;
+    } else if (lane == 31) {
+        p = w.vec32 + vpos(d.v_off + d.jlo, 0);
+        bytes = (d.jhi - d.jlo) * 5 * 4;
+    }
+    if (p)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // One tick of the batched solve: persistent warps walk the active row groups (list t % 3 built by
-// the previous update) and advance each by the operation its instance's phase asks for.
-__global__ void __launch_bounds__(256, 2) k_tick(const DevInst* __restrict__ inst,
+// the previous update) and advance each by the operation its instance's phase asks for.  Each warp
+// keeps the group after next prefetching into L2 while it sweeps the current one, so the
+// dependent loads of a group (descriptor, own values, kernel rows) meet L2 instead of DRAM.
+__global__ void __launch_bounds__(256, kTickBlocksPerSM) k_tick(const DevInst* __restrict__ inst,
                                                  const Ctl* __restrict__ ctl, Grid g, Work w,
                                                  const float* __restrict__ Khi,
                                                  const float* __restrict__ Klo, const double* A,
@@ -850,16 +902,294 @@ __global__ void __launch_bounds__(256, 2) k_tick(const DevInst* __restrict__ ins
     const int* ids = w.glist + (size_t)list * w.n_groups;
     const int stride = gridDim.x * (blockDim.x >> 5);
     int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int id = (t < nact) ? ids[t] : 0;
+    if (t >= nact) return;
+    int id = ids[t];
+    int id1 = (t + stride < nact) ? ids[t + stride] : -1;
+    int id2 = (t + 2 * stride < nact) ? ids[t + 2 * stride] : -1;
+    prefetch_group(g.gdesc[id], lane, w, Khi);
+    if (id1 >= 0) prefetch_group(g.gdesc[id1], lane, w, Khi);
     while (t < nact) {
-        const int tn = t + stride;
-        const int idn = (tn < nact) ? ids[tn] : 0;  // prefetch the next group id
+        const int t3 = t + 3 * stride;
+        const int id3 = (t3 < nact) ? ids[t3] : -1;
+        GroupDesc d2;
+        if (id2 >= 0) d2 = g.gdesc[id2];
         const GroupDesc d = g.gdesc[id];
         const int phase = g.gphase[id];
         const DevInst I = inst[d.b];
         tick_group(d, phase, lane, I, ctl, g, w, Khi, Klo, A, B, ntot);
-        t = tn;
-        id = idn;
+        if (id2 >= 0) prefetch_group(d2, lane, w, Khi);
+        t += stride;
+        id = id1;
+        id1 = id2;
+        id2 = id3;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Ring sweep: the same tick, with each warp streaming its row groups through shared memory.
+// A warp owns SLOTS tile slots; a tile is up to 128 columns of one group: the group's kernel
+// block over those columns (one bulk copy, two where the columns cross a pool tile) and the node
+// vectors a, b, u1, u2, u3 there (one bulk copy in the blocked layout), completion counted in
+// bytes on the slot's mbarrier.  The warp is its own producer: after it finishes a tile it refills
+// the freed slot with the next tile of its group sequence, so the copies of the following tiles
+// are in flight while it computes.  Group descriptors (with the instance parameters) reach the
+// computing side through a small per-warp queue in shared memory, written when the copying side
+// moves onto a group (its descriptor was requested one group earlier).  The removable-limit term
+// of each row is added once per group by the lane that stores the row's total.  Groups in an FP64
+// phase take the global-memory path of tick_group and no slots.
+constexpr int kTileCols = 128;                         // columns per tile (4 per lane)
+constexpr int kVecOff = 3 * kRows * kTileCols;         // slot floats before the node vectors
+constexpr int kTileFloats = (3 * kRows + 5) * kTileCols;
+constexpr long long kRingWaitBudget = 2000000000LL;    // clock cycles (about 1 s)
+static_assert((kTileFloats * sizeof(float)) % 16 == 0, "tile slots must stay 16-byte aligned");
+static_assert(kPoolTile % kTileCols == 0 || kTileCols % 4 == 0, "tile columns");
+
+struct RingEntry {  // one queued group
+    GroupDesc d;
+    int phase, pad[3];
+};
+
+template <int WARPS, int SLOTS>
+struct RingCfg {
+    static constexpr int kWarps = WARPS, kSlots = SLOTS, kQueue = SLOTS + 2;
+    static constexpr size_t kTileBytes = (size_t)WARPS * SLOTS * kTileFloats * sizeof(float);
+    static constexpr size_t kBarBytes = (size_t)WARPS * SLOTS * 8;
+    static constexpr size_t kSmem = kTileBytes + kBarBytes + (size_t)WARPS * kQueue * sizeof(RingEntry);
+    static_assert(kSmem <= 227 * 1024, "ring sweep shared memory");
+};
+using RingSweep = RingCfg<12, 2>;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool ring_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase `parity` of a slot barrier; false once the budget has run out.
+__device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity) {
+    if (ring_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!ring_test(bar, parity)) {
+        if (clock64() - t0 > kRingWaitBudget) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy(float* dst, const float* src, int bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"((uint32_t)bytes), "r"(bar)
+        : "memory");
+}
+
+template <typename Cfg>
+__global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
+    k_tick_ring(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g, Work w,
+                const float* __restrict__ Khi, const float* __restrict__ Klo, const double* A,
+                const double* B, int ntot, int list, int* err) {
+    constexpr int S = Cfg::kSlots, Q = Cfg::kQueue;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * S * kTileFloats;
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(smem + Cfg::kTileBytes) + warp * S;
+    RingEntry* queue =
+        reinterpret_cast<RingEntry*>(smem + Cfg::kTileBytes + Cfg::kBarBytes) + warp * Q;
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[k]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+
+    const int nact = w.lcount[3 + list];
+    const int* ids = w.glist + (size_t)list * w.n_groups;
+    const int stride = gridDim.x * Cfg::kWarps;
+    const int t0 = blockIdx.x * Cfg::kWarps + warp;
+    const int nmine = t0 < nact ? (nact - 1 - t0) / stride + 1 : 0;
+    if (nmine == 0) return;
+    const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
+    const double kappa = ctl->kappa;
+
+    // copying side: current group pk (tiles from column pc while ptiles), the next group's
+    // descriptor and phase (nd, nph) and the id after it (nnid), already requested
+    int pk = -1, pc = 0;
+    bool ptiles = false;
+    GroupDesc pd = {};
+    const int nid = ids[t0];
+    GroupDesc nd = g.gdesc[nid];
+    int nph = g.gphase[nid];
+    int nnid = (nmine > 1) ? ids[t0 + stride] : 0;
+    unsigned issued = 0, consumed = 0;
+
+    // one step of the copying side: issue one tile, or move onto the next group; false when
+    // neither is possible (sequence done, or the queue would overrun the computing side at ck)
+    auto produce = [&](int ck) -> bool {
+        if (!ptiles) {
+            if (pk + 1 >= nmine || pk + 1 - ck >= Q) return false;
+            ++pk;
+            pd = nd;
+            const int pph = nph;
+            if (lane == 0) {
+                queue[pk % Q].d = pd;
+                queue[pk % Q].phase = pph;
+            }
+            if (pk + 1 < nmine) {
+                nd = g.gdesc[nnid];
+                nph = g.gphase[nnid];
+            }
+            if (pk + 2 < nmine) nnid = ids[t0 + (pk + 2) * stride];
+            ptiles = (pph == PH_PICARD32 || pph == PH_TANGENT32) && pd.jhi > pd.jlo;
+            pc = pd.jlo;
+            return true;
+        }
+        const int slot = issued % S;
+        const uint32_t bar = smem_addr(&bars[slot]);
+        const int cols = min(kTileCols, pd.jhi - pc);
+        const int split = min(cols, (pc / kPoolTile + 1) * kPoolTile - pc);  // columns in the
+                                                                             // first pool tile
+        // the slot's previous tile was read by this warp (generic proxy) before these copies
+        // (async proxy) overwrite it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"((uint32_t)(cols * (3 * pd.nr + 5) * 4))
+                         : "memory");
+        __syncwarp();
+        float* dst = ring + slot * kTileFloats;
+        if (lane == 0) {
+            bulk_copy(dst, Khi + group_run(pd, pc), split * 3 * pd.nr * 4, bar);
+        } else if (lane == 1 && split < cols) {
+            bulk_copy(dst + (split >> 2) * 3 * pd.nr * 4, Khi + group_run(pd, pc + split),
+                      (cols - split) * 3 * pd.nr * 4, bar);
+        } else if (lane == 2) {
+            bulk_copy(dst + kVecOff, w.vec32 + vpos(pd.v_off + pc, 0), cols * 5 * 4, bar);
+        }
+        ++issued;
+        pc += kTileCols;
+        if (pc >= pd.jhi) ptiles = false;
+        return true;
+    };
+    auto fill = [&](int ck) {
+        while (issued - consumed < (unsigned)S && produce(ck)) {
+        }
+    };
+
+    // the lane that stores a total: value qv (rows' A sums, then B sums) of row rr
+    const int qv = group_total_index(lane), rr = qv % kRows;
+    const bool isB = qv >= kRows;
+    bool ok = true;
+    for (int ck = 0; ck < nmine; ++ck) {
+        while (pk < ck && produce(ck)) {
+        }
+        fill(ck);
+        __syncwarp();
+        const GroupDesc d = queue[ck % Q].d;
+        const int phase = queue[ck % Q].phase;
+        if (phase != PH_PICARD32 && phase != PH_TANGENT32) {
+            tick_group(d, phase, lane, inst[d.b], ctl, g, w, Khi, Klo, A, B, ntot);
+            continue;
+        }
+        const bool tan = (phase == PH_TANGENT32);
+        const int collocated = (d.mode == QDSE_COLLOCATED) && bc;
+        const int o = d.x_off + d.i0;
+        Rows32 R;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const bool v = r < d.nr;
+            R.sA[r] = 0.f;
+            R.sB[r] = 0.f;
+            R.Ai[r] = v ? w.x32[o + r] : 0.f;
+            R.Bi[r] = v ? w.x32[ntot + o + r] : 0.f;
+            R.Pi[r] = v ? g.sp32[o + r] : 0.f;
+            R.dAi[r] = (v && tan) ? w.d32[o + r] : 0.f;
+            R.dBi[r] = (v && tan) ? w.d32[ntot + o + r] : 0.f;
+        }
+        // the storing lane's row: p_i^2 and the removable-limit term of Eq. (diag) inputs
+        const bool lead = group_total_leader(lane) && rr < d.nr;
+        float Pl = 1.f, KTd = 0.f, x1 = 0.f, x2 = 0.f, qA = 0.f, qB = 0.f;
+        float y1 = 0.f, y2 = 0.f, eqA = 0.f, eqB = 0.f;
+        if (lead) {
+            const int i = d.i0 + rr;
+            Pl = g.sp32[o + rr];
+            if (collocated) {
+                KTd = g.ktd[o + rr];
+                x1 = w.vec32[vpos(d.v_off + i, 2)];
+                x2 = w.vec32[vpos(d.v_off + i, 3)];
+                qA = w.dia32[o + rr];
+                qB = w.dia32[ntot + o + rr];
+                if (tan) {
+                    y1 = w.dvec32[vpos(d.v_off + i, 2)];
+                    y2 = w.dvec32[vpos(d.v_off + i, 3)];
+                    eqA = w.ddia32[o + rr];
+                    eqB = w.ddia32[ntot + o + rr];
+                }
+            }
+        }
+        for (int c = d.jlo; c < d.jhi; c += kTileCols) {
+            const int slot = consumed % S;
+            const bool got = ring_wait(smem_addr(&bars[slot]), (consumed / S) & 1);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            const int col = c + 4 * lane;
+            if (col < d.jhi) {
+                const float* sl = ring + slot * kTileFloats;
+                const float* kb = sl + lane * 3 * d.nr * 4;
+                const float* vb = sl + kVecOff + lane * 20;
+                auto V4 = [&](int comp) { return *reinterpret_cast<const float4*>(vb + 4 * comp); };
+                const float4 a = V4(0), b = V4(1), u1 = V4(2), u2 = V4(3), u3 = V4(4);
+                const int sw = kswz(d.nr, col >> 2);
+                auto K = [&](int r, int pl) {
+                    return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
+                };
+                if (tan) {
+                    const float* db_ = w.dvec32 + vpos(d.v_off + col, 0);
+                    const float4 ea = ld4(db_), eb = ld4(db_ + 4), e1 = ld4(db_ + 8),
+                                 e2 = ld4(db_ + 12), e3 = ld4(db_ + 16);
+                    rows32_chunk<true>(R, K, d.nr, 0, bc, 0, a, b, u1, u2, u3, ea, eb, e1, e2, e3);
+                } else {
+                    rows32_chunk<false>(R, K, d.nr, 0, bc, 0, a, b, u1, u2, u3, a, a, a, a, a);
+                }
+            }
+            __syncwarp();
+            ++consumed;
+            fill(ck);
+        }
+        if (!ok) break;
+        float tot = group_totals(R.sA, R.sB, lane);
+        if (lead) {
+            if (collocated) {
+                if (!tan) {
+                    tot += isB ? (x1 * qA - x2 * qB) * KTd : (-x1 * qB - Pl * x2 * qA) * KTd;
+                } else {
+                    tot += isB ? (y1 * qA + x1 * eqA - y2 * qB - x2 * eqB) * KTd
+                               : (-y1 * qB - x1 * eqB - Pl * (y2 * qA + x2 * eqA)) * KTd;
+                }
+            }
+            const float sc = (float)(kappa * d.D);
+            if (!isB) w.xn32[o + rr] = tan ? sc * tot / Pl : 1.f + sc * tot / Pl;
+            else w.xn32[ntot + o + rr] = tan ? sc * tot : (float)d.m + sc * tot;
+        }
+    }
+    if (!ok) {
+        // a copy never completed: report it, then wait (bounded) for this warp's copies still
+        // in flight so that none lands after the block has released its shared memory
+        if (lane == 0) atomicExch(err, 1);
+        for (unsigned u = consumed; u < issued; ++u)
+            ring_wait(smem_addr(&bars[u % S]), (u / S) & 1);
     }
 }
 
@@ -1015,9 +1345,37 @@ cudaError_t launch_group_bands(qdse_ctx* c) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_group_params(qdse_ctx* c) {
+    if (c->n_groups <= 0) return cudaSuccess;
+    k_group_params<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(c->d_inst, c->grid,
+                                                                      c->n_groups);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t configure_tick_ring() {
+    return cudaFuncSetAttribute(k_tick_ring<RingSweep>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RingSweep::kSmem);
+}
+
+cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B) {
+    prof_begin(c, PK_SWEEP);
+    const int sms = c->n_sms > 0 ? c->n_sms : 152;
+    const int blocks =
+        std::max(1, std::min((c->n_groups + RingSweep::kWarps - 1) / RingSweep::kWarps, sms));
+    k_tick_ring<RingSweep><<<blocks, RingSweep::kWarps * 32, RingSweep::kSmem, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
+        (int)(c->tick % 3), c->d_err);
+    c->launches++;
+    prof_end(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B) {
     prof_begin(c, PK_SWEEP);
-    const int blocks = std::min((c->n_groups + 7) / 8, 2 * (c->n_sms > 0 ? c->n_sms : 152));
+    const int blocks =
+        std::min((c->n_groups + 7) / 8, kTickBlocksPerSM * (c->n_sms > 0 ? c->n_sms : 152));
     k_tick<<<blocks, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi,
                                           c->d_Klo, A, B, c->n_total, (int)(c->tick % 3));
     c->launches++;

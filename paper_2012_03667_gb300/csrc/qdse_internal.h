@@ -41,19 +41,20 @@ struct DevInst {          // per-instance descriptor, read-only during a solve
     int nt;               // angular nodes
     int x_off;            // first global point
     int t_off;            // first angular node
-    long long k_off;      // first element of plane 0 in the kernel pool
-    int ld;               // row stride of the kernel planes (n rounded up to 4)
+    long long k_off;      // first element of this instance's block of the kernel pool
+    int ld;               // columns stored per kernel row (n rounded up to 4)
     int mode;             // QDSE_COLLOCATED / QDSE_STAGGERED
-    int v_off;            // first element of this instance in the padded FP32 node vectors
+    int v_off;            // first node of this instance in the padded FP32 node vectors
     int g_off;            // first row group of this instance
     double D, omega, m;   // current parameters
 };
 
 struct GroupDesc {        // one row group (kRows consecutive external points of one instance)
     int b, i0, nr, jlo;   // instance, first row, rows in the group, band union start
-    int jhi, v_off, x_off, ld;  // band union end, node-vector base, point base, row stride
-    long long kbase;      // kernel-pool offset of row i0 (plane 0)
-    long long plane;      // distance between the planes of a row (= ld)
+    int jhi, v_off, x_off, ld;  // band union end, node-vector base, point base, kernel columns
+    long long kbase;      // kernel-pool offset of the group's block (see kpos)
+    int mode, pad;        // grid mode of the instance
+    double D, m;          // instance parameters (refreshed with every parameter upload)
 };
 
 struct DevState {         // per-instance solver state, updated by the update kernel
@@ -143,16 +144,103 @@ struct Grid {              // FP64 grid arrays on the device (global point index
     int* gphase;           // per group: the phase of its instance for the coming sweep
     unsigned long long* nnz;  // per instance: sum over rows of the band widths (kernel entries a
                               // sweep must read per plane)
+    float* ktd;            // per external point: K_T at q = p (collocated grids; the entry the
+                           // removable-limit term multiplies), 0 on staggered grids
 };
 
-constexpr int kRows = 4;   // external points per warp in the batched sweeps
+constexpr int kRows = 4;   // external points per warp in the batched sweeps (1, 2 or 4)
+constexpr int kTickBlocksPerSM = kRows >= 4 ? 2 : 3;  // resident 256-thread sweep blocks per SM
 constexpr int kTile = 32;  // kernel precompute tile edge
+constexpr int kPoolTile = 128;  // kernel columns per pool tile (a multiple of 4)
+
+// Kernel pool layout.  The entries K_p(i, j) (plane p = 0, 1, 2 for K_0, K_T/(Q - P), K_3) of one
+// instance fill n * 3 * ld floats from k_off.  Rows come in groups of kRows (the last group may be
+// shorter, nr rows); a group's block starts at k_off + 3 i0 ld and holds its columns in pool
+// tiles of kPoolTile (the last one narrower); inside a tile, each 4-column block stores the
+// 3 nr plane-rows m = 3 r + p as consecutive float4.  So any column range of a tile is one
+// contiguous run (one bulk copy), and a lane reading one 4-column block gets all the group's
+// rows from adjacent 16-byte words.  For full groups of 4 rows the 12 plane-rows of block q are
+// stored in the order m ^ ((q >> 1) & 3), which makes 16-byte shared-memory reads of 8
+// consecutive blocks hit 8 different bank quads.
+__host__ __device__ inline int kswz(int nr, int q) {
+    return ((3 * nr) & 3) == 0 ? ((q >> 1) & 3) : 0;
+}
+__host__ __device__ inline long long kpos(long long k_off, int n, int ld, int i, int p, int j) {
+    const int i0 = i - i % kRows;
+    const int nr = (n - i0 < kRows) ? n - i0 : kRows;
+    const int m = 3 * (i - i0) + p, q = j >> 2;
+    return k_off + 3LL * i0 * ld + 3LL * nr * kPoolTile * (j / kPoolTile) +
+           ((long long)((j % kPoolTile) >> 2) * 3 * nr + (m ^ kswz(nr, q))) * 4 + (j & 3);
+}
+// FP32 node vectors (a, b, u1, u2, u3 and their tangents): component c of padded node x (= v_off
+// + j) at 20 (x / 4) + 4 c + x % 4, so the five components of a 4-node block are one 80-byte run
+// and any node range of an instance is contiguous.
+__host__ __device__ inline long long vpos(int x, int c) {
+    return 20LL * (x >> 2) + 4 * c + (x & 3);
+}
 
 struct HostInst {
     qdse_grid g;
     int x_off, t_off, ld, v_off, g_off;
     long long k_off;
 };
+
+#ifdef __CUDACC__
+// Pool offsets of one kernel row i (see kpos): off(p, j) for plane p, column j.
+struct KRow {
+    long long base;  // the group's block
+    int nr, m0;      // rows in the group, plane-row of (i, plane 0)
+    __device__ KRow(const DevInst& I, int i) {
+        const int i0 = i - i % kRows;
+        base = I.k_off + 3LL * i0 * I.ld;
+        nr = min(kRows, I.n - i0);
+        m0 = 3 * (i - i0);
+    }
+    __device__ long long off(int p, int j) const {
+        return base + 3LL * nr * kPoolTile * (j / kPoolTile) +
+               ((long long)((j % kPoolTile) >> 2) * 3 * nr + ((m0 + p) ^ kswz(nr, j >> 2))) * 4 +
+               (j & 3);
+    }
+};
+
+// Warp sums of 2 kRows values at once (v[0..kRows) = A sums, v[kRows..2 kRows) = B sums of the
+// group's rows): each butterfly step halves the values a lane carries, so the lane 32/(2 kRows) * q
+// ends with the total of value q after (2 kRows - 1) + log2(32/(2 kRows)) shuffles.
+__device__ __forceinline__ float group_totals(const float* sA, const float* sB, int lane) {
+    constexpr int NV = 2 * kRows;
+    float v[NV];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        v[r] = sA[r];
+        v[kRows + r] = sB[r];
+    }
+    int width = NV;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        if (width > 1) {
+            const bool hi = (lane & m) != 0;
+            const int half = width >> 1;
+#pragma unroll
+            for (int k = 0; k < NV / 2; ++k) {
+                if (k < half) {
+                    const float keep = hi ? v[k + half] : v[k], send = hi ? v[k] : v[k + half];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                }
+            }
+            width = half;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+        }
+    }
+    return v[0];
+}
+// index of the value whose total lane `lane` holds after group_totals
+__device__ __forceinline__ int group_total_index(int lane) { return lane / (32 / (2 * kRows)); }
+// lanes that hold a total first in their run
+__device__ __forceinline__ bool group_total_leader(int lane) {
+    return (lane % (32 / (2 * kRows))) == 0;
+}
+#endif
 
 }  // namespace qdse
 
@@ -187,9 +275,9 @@ struct qdse_ctx {
     int* h_count = nullptr;   // pinned mirror of d_count[0..1]
     int* d_err = nullptr;     // = d_count + 1: set when a bounded device wait ran out
     int n_sms = 0;
-    bool use_tma = false;     // bulk-copy pipelined FP32 sweep configured
     int ld_max = 0;           // widest kernel row of the batch
-    int sweep_kind = 0;       // 0: row-group kernel, 1: bulk-copy work-list kernel
+    int sweep_kind = 0;       // FP32 sweep: 1 ring (bulk copies through shared memory, the
+                              // default), 0 register-only row groups
     int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
     double* d_rel = nullptr;  // [n_inst] relative residual of the adjoint's fixed point
     // CUDA graph of a chunk of ticks, replayed between polls (captured on an internal stream)
@@ -235,9 +323,10 @@ cudaError_t launch_precompute(qdse_ctx* c, bool with_omega_derivative);
 cudaError_t configure_precompute(int max_nt);
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
-cudaError_t launch_sweep32_tma(qdse_ctx* c, const double* A, const double* B);
+cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B);
+cudaError_t configure_tick_ring();
 cudaError_t launch_group_bands(qdse_ctx* c);
-cudaError_t configure_sweep32_tma(int ldmax);
+cudaError_t launch_group_params(qdse_ctx* c);
 cudaError_t launch_update(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_sweep_otf(qdse_ctx* c, const double* A, const double* B, double* FA,
                              double* FB, int only_active);
