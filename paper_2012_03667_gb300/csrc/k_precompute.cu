@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
     // Threads walk the destination in layout order: row group rg of the tile, 4-column block
     // cb, stored plane-row slot (plane-row m = slot ^ kswz), column inside the block; for full
     // groups consecutive threads write consecutive floats.
-    static_assert(kTile % kRows == 0 && kTile % 4 == 0 && kPoolTile % kTile == 0,
-                  "precompute tiles must cover whole row groups and sit inside one pool tile");
+    static_assert(kTile % kRows == 0 && kTile % 4 == 0,
+                  "precompute tiles must cover whole row groups and 4-column blocks");
     constexpr int kRun = 3 * kRows * kTile;  // floats of one row group inside the tile
     for (int set = 0; set < nsets; ++set) {
         float* Hi = set ? Kwhi : Khi;

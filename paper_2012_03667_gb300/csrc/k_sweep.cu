@@ -461,8 +461,7 @@ __device__ __forceinline__ void group32(int lane, const GroupDesc& d, const Grid
             e2 = ld4(db_ + 12);
             e3 = ld4(db_ + 16);
         }
-        const float* kc = kb + 3LL * d.nr * kPoolTile * (c / kPoolTile) +
-                          (long long)((c % kPoolTile) >> 2) * nb;
+        const float* kc = kb + (long long)(c >> 2) * nb;
         const int sw = kswz(d.nr, c >> 2);
         auto K = [&](int r, int pl) { return ld4(kc + ((3 * r + pl) ^ sw) * 4); };
         rows32_chunk<TAN>(R, K, d.nr, d.i0 - c, bc, collocated, a, b, u1, u2, u3, ea, eb, e1, e2,
@@ -860,32 +859,21 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
     T.sync();
 }
 
-// Pool offset of columns [c0, ...) of a row group's block; a column range inside one pool tile
-// is one contiguous run of (c1 - c0) * 3 nr floats from here (kpos).
+// Pool offset of column c0 (a multiple of 4) of a row group's block; columns [c0, c1) are one
+// contiguous run of (c1 - c0) * 3 nr floats from here (kpos).
 __device__ __forceinline__ long long group_run(const GroupDesc& d, int c0) {
-    return d.kbase + 3LL * d.nr * kPoolTile * (c0 / kPoolTile) +
-           (long long)((c0 % kPoolTile) >> 2) * 3 * d.nr * 4;
+    return d.kbase + (long long)(c0 >> 2) * 3 * d.nr * 4;
 }
 
-// Ask L2 to fetch the kernel block and node vectors of one row group ahead of its sweep: lane t
-// takes the part of the union band [jlo, jhi) in the t-th pool tile it touches, lane 31 the node
-// vectors (one run in the blocked layout).  All runs are 16-byte aligned multiples of 16 bytes.
+// Ask L2 to fetch the kernel block and node vectors of one row group ahead of its sweep over the
+// union band [jlo, jhi): lane 0 the kernel run, lane 1 the node vectors (one run in the blocked
+// layout).  Both are 16-byte aligned multiples of 16 bytes.
 __device__ __forceinline__ void prefetch_group(const GroupDesc& d, int lane, const Work& w,
                                                const float* __restrict__ Khi) {
-    if (d.jhi <= d.jlo) return;
-    const float* p = nullptr;
-    int bytes = 0;
-    const int t = d.jlo / kPoolTile + lane;
-    if (lane < 31 && t * kPoolTile < d.jhi) {
-        const int c0 = max(d.jlo, t * kPoolTile), c1 = min(d.jhi, (t + 1) * kPoolTile);
-        p = Khi + group_run(d, c0);
-        bytes = (c1 - c0) * 3 * d.nr * 4;
-    } else if (lane == 31) {
-        p = w.vec32 + vpos(d.v_off + d.jlo, 0);
-        bytes = (d.jhi - d.jlo) * 5 * 4;
-    }
-    if (p)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+    if (d.jhi <= d.jlo || lane > 1) return;
+    const float* p = lane == 0 ? Khi + group_run(d, d.jlo) : w.vec32 + vpos(d.v_off + d.jlo, 0);
+    const int bytes = (d.jhi - d.jlo) * (lane == 0 ? 3 * d.nr : 5) * 4;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // One tick of the batched solve: persistent warps walk the active row groups (list t % 3 built by
@@ -927,35 +915,49 @@ __global__ void __launch_bounds__(256, kTickBlocksPerSM) k_tick(const DevInst* _
 
 // ---------------------------------------------------------------------------------------------
 // Ring sweep: the same tick, with each warp streaming its row groups through shared memory.
-// A warp owns SLOTS tile slots; a tile is up to 128 columns of one group: the group's kernel
-// block over those columns (one bulk copy, two where the columns cross a pool tile) and the node
-// vectors a, b, u1, u2, u3 there (one bulk copy in the blocked layout), completion counted in
-// bytes on the slot's mbarrier.  The warp is its own producer: after it finishes a tile it refills
-// the freed slot with the next tile of its group sequence, so the copies of the following tiles
-// are in flight while it computes.  Group descriptors (with the instance parameters) reach the
-// computing side through a small per-warp queue in shared memory, written when the copying side
-// moves onto a group (its descriptor was requested one group earlier).  The removable-limit term
-// of each row is added once per group by the lane that stores the row's total.  Groups in an FP64
-// phase take the global-memory path of tick_group and no slots.
+//
+// Tiles.  A warp owns SLOTS tile slots; a tile is up to 128 columns of one group: the group's
+// kernel block over those columns and the node vectors a, b, u1, u2, u3 there, one bulk copy each
+// (cp.async.bulk, completion counted in bytes on the slot's mbarrier).  After the warp finishes a
+// tile it refills the freed slot with the next tile of its group sequence, so the following
+// tiles are in flight while it computes.
+//
+// Groups.  Everything else a group needs travels through a per-warp queue of kRingQueue entries
+// in shared memory, filled by small asynchronous copies (cp.async, tracked with commit/wait
+// groups): when the copying side moves onto group k it reads k's descriptor from entry k, and
+// requests the row constants of group k (entry k), the descriptor and phase of group k + 1 (whose
+// list id entry k + 1 already holds) and the list id of group k + 2.  So it never waits on a
+// global load, and the computing side finds a group's descriptor, phase and row constants in
+// shared memory.  The removable-limit term of each row is added once per group by the lane that
+// stores the row's total.  Groups in an FP64 phase take the global-memory path of tick_group and
+// no slots.
 constexpr int kTileCols = 128;                         // columns per tile (4 per lane)
 constexpr int kVecOff = 3 * kRows * kTileCols;         // slot floats before the node vectors
 constexpr int kTileFloats = (3 * kRows + 5) * kTileCols;
+constexpr int kRingQueue = 5;                          // queue entries per warp
 constexpr long long kRingWaitBudget = 2000000000LL;    // clock cycles (about 1 s)
 static_assert((kTileFloats * sizeof(float)) % 16 == 0, "tile slots must stay 16-byte aligned");
-static_assert(kPoolTile % kTileCols == 0 || kTileCols % 4 == 0, "tile columns");
+static_assert(kRows == 4, "the queue's row-constant copies are laid out for groups of 4 rows");
 
-struct RingEntry {  // one queued group
-    GroupDesc d;
-    int phase, pad[3];
+struct RingEntry {        // one group on its way from the copying to the computing side
+    GroupDesc d;          // descriptor (with the instance parameters)
+    int phase, id, pad[2];
+    float rc[6][kRows];   // per row: A_i, B_i (FP32 iterate), P_i, stencil dA/ds, dB/ds, K_T(i,i)
+    float vd[2][4];       // u1, u2 at the group's own nodes (collocated removable limit)
+    float tc[4][kRows];   // tangent: dA_i, dB_i, stencil of the direction (A, B)
+    float td[2][4];       // tangent: du1, du2 at the group's own nodes
 };
+static_assert(sizeof(RingEntry) % 16 == 0, "queue entries must stay 16-byte aligned");
 
 template <int WARPS, int SLOTS>
 struct RingCfg {
-    static constexpr int kWarps = WARPS, kSlots = SLOTS, kQueue = SLOTS + 2;
+    static constexpr int kWarps = WARPS, kSlots = SLOTS;
     static constexpr size_t kTileBytes = (size_t)WARPS * SLOTS * kTileFloats * sizeof(float);
     static constexpr size_t kBarBytes = (size_t)WARPS * SLOTS * 8;
-    static constexpr size_t kSmem = kTileBytes + kBarBytes + (size_t)WARPS * kQueue * sizeof(RingEntry);
+    static constexpr size_t kSmem =
+        kTileBytes + kBarBytes + (size_t)WARPS * kRingQueue * sizeof(RingEntry);
     static_assert(kSmem <= 227 * 1024, "ring sweep shared memory");
+    static_assert(kBarBytes % 16 == 0, "queue must start 16-byte aligned");
 };
 using RingSweep = RingCfg<12, 2>;
 
@@ -992,12 +994,45 @@ __device__ __forceinline__ void bulk_copy(float* dst, const float* src, int byte
         : "memory");
 }
 
+// The same for data read once per sweep (the kernel pool): an L2 evict-first policy keeps the
+// pool's stream from displacing the small per-point arrays every group reads.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_copy_evict_first(float* dst, const float* src, int bytes,
+                                                      uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+        "[%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"((uint32_t)bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
+
+// Small asynchronous global -> shared copies (4 or 16 bytes) and their commit / wait groups.
+__device__ __forceinline__ void cp4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n (0, 1 or 2) of this thread's most recent copy groups are pending
+__device__ __forceinline__ void cp_wait(int n) {
+    if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;" ::: "memory");
+}
+
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     k_tick_ring(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g, Work w,
                 const float* __restrict__ Khi, const float* __restrict__ Klo, const double* A,
                 const double* B, int ntot, int list, int* err) {
-    constexpr int S = Cfg::kSlots, Q = Cfg::kQueue;
+    constexpr int S = Cfg::kSlots, Q = kRingQueue;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * S * kTileFloats;
@@ -1021,64 +1056,103 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     if (nmine == 0) return;
     const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
     const double kappa = ctl->kappa;
+    const uint64_t pol = evict_first_policy();
 
-    // copying side: current group pk (tiles from column pc while ptiles), the next group's
-    // descriptor and phase (nd, nph) and the id after it (nnid), already requested
-    int pk = -1, pc = 0;
+    // prologue: list ids of groups 0 and 1, then the descriptor and phase of group 0
+    if (lane == 0) cp4(&queue[0].id, ids + t0);
+    if (lane == 1 && nmine > 1) cp4(&queue[1].id, ids + t0 + stride);
+    cp_commit();
+    cp_wait(0);
+    __syncwarp();
+    if (lane < 4) cp16(reinterpret_cast<int4*>(&queue[0].d) + lane,
+                       reinterpret_cast<const int4*>(g.gdesc + queue[0].id) + lane);
+    if (lane == 4) cp4(&queue[0].phase, g.gphase + queue[0].id);
+    cp_commit();
+
+    // copying side: current group pk, its tiles from column pc while ptiles
+    int pk = -1, pc = 0, pjhi = 0, pnr = 0, pvoff = 0;
+    long long pkbase = 0;
     bool ptiles = false;
-    GroupDesc pd = {};
-    const int nid = ids[t0];
-    GroupDesc nd = g.gdesc[nid];
-    int nph = g.gphase[nid];
-    int nnid = (nmine > 1) ? ids[t0 + stride] : 0;
     unsigned issued = 0, consumed = 0;
 
     // one step of the copying side: issue one tile, or move onto the next group; false when
     // neither is possible (sequence done, or the queue would overrun the computing side at ck)
     auto produce = [&](int ck) -> bool {
         if (!ptiles) {
-            if (pk + 1 >= nmine || pk + 1 - ck >= Q) return false;
-            ++pk;
-            pd = nd;
-            const int pph = nph;
-            if (lane == 0) {
-                queue[pk % Q].d = pd;
-                queue[pk % Q].phase = pph;
+            const int k = pk + 1;
+            if (k >= nmine || k + 2 - ck >= Q) return false;
+            pk = k;
+            cp_wait(0);  // entry k's descriptor and phase, entry k + 1's list id
+            __syncwarp();
+            RingEntry& e = queue[k % Q];
+            const int ph = e.phase;
+            const int o = e.d.x_off + e.d.i0, nr = e.d.nr, ib = e.d.v_off + e.d.i0;
+            pjhi = e.d.jhi;
+            pnr = nr;
+            pvoff = e.d.v_off;
+            pkbase = e.d.kbase;
+            pc = e.d.jlo;
+            ptiles = (ph == PH_PICARD32 || ph == PH_TANGENT32) && pjhi > pc;
+            // row constants of group k
+            if (lane < 6 * kRows) {
+                const int arr = lane / kRows, r = lane % kRows;
+                const float* src = arr == 0   ? w.x32 + o
+                                   : arr == 1 ? w.x32 + ntot + o
+                                   : arr == 2 ? g.sp32 + o
+                                   : arr == 3 ? w.dia32 + o
+                                   : arr == 4 ? w.dia32 + ntot + o
+                                              : g.ktd + o;
+                if (r < nr) cp4(&e.rc[arr][r], src + r);
+            } else if (lane < 6 * kRows + 2) {
+                cp16(e.vd[lane - 6 * kRows], w.vec32 + vpos(ib, 2 + lane - 6 * kRows));
+            } else if (lane < 6 * kRows + 6) {
+                // descriptor of group k + 1 (16 bytes per lane) and its phase
+                if (k + 1 < nmine) {
+                    RingEntry& n1 = queue[(k + 1) % Q];
+                    cp16(reinterpret_cast<int4*>(&n1.d) + (lane - 6 * kRows - 2),
+                         reinterpret_cast<const int4*>(g.gdesc + n1.id) + (lane - 6 * kRows - 2));
+                }
+            } else if (lane == 6 * kRows + 6) {
+                if (k + 1 < nmine) cp4(&queue[(k + 1) % Q].phase, g.gphase + queue[(k + 1) % Q].id);
+            } else if (lane == 6 * kRows + 7) {
+                if (k + 2 < nmine) cp4(&queue[(k + 2) % Q].id, ids + t0 + (k + 2) * stride);
             }
-            if (pk + 1 < nmine) {
-                nd = g.gdesc[nnid];
-                nph = g.gphase[nnid];
+            if (ph == PH_TANGENT32) {
+                if (lane < 4 * kRows) {
+                    const int arr = lane / kRows, r = lane % kRows;
+                    const float* src = arr == 0   ? w.d32 + o
+                                       : arr == 1 ? w.d32 + ntot + o
+                                       : arr == 2 ? w.ddia32 + o
+                                                  : w.ddia32 + ntot + o;
+                    if (r < nr) cp4(&e.tc[arr][r], src + r);
+                } else if (lane < 4 * kRows + 2) {
+                    cp16(e.td[lane - 4 * kRows], w.dvec32 + vpos(ib, 2 + lane - 4 * kRows));
+                }
             }
-            if (pk + 2 < nmine) nnid = ids[t0 + (pk + 2) * stride];
-            ptiles = (pph == PH_PICARD32 || pph == PH_TANGENT32) && pd.jhi > pd.jlo;
-            pc = pd.jlo;
+            cp_commit();
             return true;
         }
         const int slot = issued % S;
         const uint32_t bar = smem_addr(&bars[slot]);
-        const int cols = min(kTileCols, pd.jhi - pc);
-        const int split = min(cols, (pc / kPoolTile + 1) * kPoolTile - pc);  // columns in the
-                                                                             // first pool tile
+        const int cols = min(kTileCols, pjhi - pc);
         // the slot's previous tile was read by this warp (generic proxy) before these copies
         // (async proxy) overwrite it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (lane == 0)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                         "r"((uint32_t)(cols * (3 * pd.nr + 5) * 4))
+                         "r"((uint32_t)(cols * (3 * pnr + 5) * 4))
                          : "memory");
         __syncwarp();
         float* dst = ring + slot * kTileFloats;
         if (lane == 0) {
-            bulk_copy(dst, Khi + group_run(pd, pc), split * 3 * pd.nr * 4, bar);
-        } else if (lane == 1 && split < cols) {
-            bulk_copy(dst + (split >> 2) * 3 * pd.nr * 4, Khi + group_run(pd, pc + split),
-                      (cols - split) * 3 * pd.nr * 4, bar);
-        } else if (lane == 2) {
-            bulk_copy(dst + kVecOff, w.vec32 + vpos(pd.v_off + pc, 0), cols * 5 * 4, bar);
+            bulk_copy_evict_first(dst, Khi + pkbase + (long long)(pc >> 2) * 3 * pnr * 4,
+                                  cols * 3 * pnr * 4, bar, pol);
+        } else if (lane == 1) {
+            bulk_copy(dst + kVecOff, w.vec32 + vpos(pvoff + pc, 0), cols * 5 * 4, bar);
         }
         ++issued;
         pc += kTileCols;
-        if (pc >= pd.jhi) ptiles = false;
+        if (pc >= pjhi) ptiles = false;
         return true;
     };
     auto fill = [&](int ck) {
@@ -1094,50 +1168,31 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         while (pk < ck && produce(ck)) {
         }
         fill(ck);
+        cp_wait(pk - ck);  // entry ck's row constants
         __syncwarp();
-        const GroupDesc d = queue[ck % Q].d;
-        const int phase = queue[ck % Q].phase;
+        const RingEntry& e = queue[ck % Q];
+        const GroupDesc& d = e.d;
+        const int phase = e.phase;
         if (phase != PH_PICARD32 && phase != PH_TANGENT32) {
-            tick_group(d, phase, lane, inst[d.b], ctl, g, w, Khi, Klo, A, B, ntot);
+            const GroupDesc dc = d;
+            tick_group(dc, phase, lane, inst[dc.b], ctl, g, w, Khi, Klo, A, B, ntot);
             continue;
         }
         const bool tan = (phase == PH_TANGENT32);
         const int collocated = (d.mode == QDSE_COLLOCATED) && bc;
-        const int o = d.x_off + d.i0;
+        const int nr = d.nr, jlo = d.jlo, jhi = d.jhi, i0 = d.i0, o = d.x_off + i0;
         Rows32 R;
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            const bool v = r < d.nr;
             R.sA[r] = 0.f;
             R.sB[r] = 0.f;
-            R.Ai[r] = v ? w.x32[o + r] : 0.f;
-            R.Bi[r] = v ? w.x32[ntot + o + r] : 0.f;
-            R.Pi[r] = v ? g.sp32[o + r] : 0.f;
-            R.dAi[r] = (v && tan) ? w.d32[o + r] : 0.f;
-            R.dBi[r] = (v && tan) ? w.d32[ntot + o + r] : 0.f;
+            R.Ai[r] = e.rc[0][r];
+            R.Bi[r] = e.rc[1][r];
+            R.Pi[r] = e.rc[2][r];
+            R.dAi[r] = tan ? e.tc[0][r] : 0.f;
+            R.dBi[r] = tan ? e.tc[1][r] : 0.f;
         }
-        // the storing lane's row: p_i^2 and the removable-limit term of Eq. (diag) inputs
-        const bool lead = group_total_leader(lane) && rr < d.nr;
-        float Pl = 1.f, KTd = 0.f, x1 = 0.f, x2 = 0.f, qA = 0.f, qB = 0.f;
-        float y1 = 0.f, y2 = 0.f, eqA = 0.f, eqB = 0.f;
-        if (lead) {
-            const int i = d.i0 + rr;
-            Pl = g.sp32[o + rr];
-            if (collocated) {
-                KTd = g.ktd[o + rr];
-                x1 = w.vec32[vpos(d.v_off + i, 2)];
-                x2 = w.vec32[vpos(d.v_off + i, 3)];
-                qA = w.dia32[o + rr];
-                qB = w.dia32[ntot + o + rr];
-                if (tan) {
-                    y1 = w.dvec32[vpos(d.v_off + i, 2)];
-                    y2 = w.dvec32[vpos(d.v_off + i, 3)];
-                    eqA = w.ddia32[o + rr];
-                    eqB = w.ddia32[ntot + o + rr];
-                }
-            }
-        }
-        for (int c = d.jlo; c < d.jhi; c += kTileCols) {
+        for (int c = jlo; c < jhi; c += kTileCols) {
             const int slot = consumed % S;
             const bool got = ring_wait(smem_addr(&bars[slot]), (consumed / S) & 1);
             if (!__all_sync(0xffffffffu, got)) {
@@ -1145,13 +1200,13 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                 break;
             }
             const int col = c + 4 * lane;
-            if (col < d.jhi) {
+            if (col < jhi) {
                 const float* sl = ring + slot * kTileFloats;
-                const float* kb = sl + lane * 3 * d.nr * 4;
+                const float* kb = sl + lane * 3 * nr * 4;
                 const float* vb = sl + kVecOff + lane * 20;
                 auto V4 = [&](int comp) { return *reinterpret_cast<const float4*>(vb + 4 * comp); };
                 const float4 a = V4(0), b = V4(1), u1 = V4(2), u2 = V4(3), u3 = V4(4);
-                const int sw = kswz(d.nr, col >> 2);
+                const int sw = kswz(nr, col >> 2);
                 auto K = [&](int r, int pl) {
                     return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
                 };
@@ -1159,9 +1214,9 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                     const float* db_ = w.dvec32 + vpos(d.v_off + col, 0);
                     const float4 ea = ld4(db_), eb = ld4(db_ + 4), e1 = ld4(db_ + 8),
                                  e2 = ld4(db_ + 12), e3 = ld4(db_ + 16);
-                    rows32_chunk<true>(R, K, d.nr, 0, bc, 0, a, b, u1, u2, u3, ea, eb, e1, e2, e3);
+                    rows32_chunk<true>(R, K, nr, 0, bc, 0, a, b, u1, u2, u3, ea, eb, e1, e2, e3);
                 } else {
-                    rows32_chunk<false>(R, K, d.nr, 0, bc, 0, a, b, u1, u2, u3, a, a, a, a, a);
+                    rows32_chunk<false>(R, K, nr, 0, bc, 0, a, b, u1, u2, u3, a, a, a, a, a);
                 }
             }
             __syncwarp();
@@ -1170,23 +1225,31 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         }
         if (!ok) break;
         float tot = group_totals(R.sA, R.sB, lane);
-        if (lead) {
+        if (group_total_leader(lane) && rr < nr) {
+            const float Pl = e.rc[2][rr];
             if (collocated) {
+                // removable limit q^2 -> p^2 of row i0 + rr (K_T(i,i) times the stencil
+                // quotients and the node vectors at p_i)
+                const float KTd = e.rc[5][rr], qA = e.rc[3][rr], qB = e.rc[4][rr];
+                const float x1 = e.vd[0][rr], x2 = e.vd[1][rr];
                 if (!tan) {
                     tot += isB ? (x1 * qA - x2 * qB) * KTd : (-x1 * qB - Pl * x2 * qA) * KTd;
                 } else {
+                    const float y1 = e.td[0][rr], y2 = e.td[1][rr];
+                    const float eqA = e.tc[2][rr], eqB = e.tc[3][rr];
                     tot += isB ? (y1 * qA + x1 * eqA - y2 * qB - x2 * eqB) * KTd
                                : (-y1 * qB - x1 * eqB - Pl * (y2 * qA + x2 * eqA)) * KTd;
                 }
             }
             const float sc = (float)(kappa * d.D);
-            if (!isB) w.xn32[o + rr] = tan ? sc * tot / Pl : 1.f + sc * tot / Pl;
+            if (!isB) w.xn32[o + rr] = tan ? __fdividef(sc * tot, Pl) : 1.f + __fdividef(sc * tot, Pl);
             else w.xn32[ntot + o + rr] = tan ? sc * tot : (float)d.m + sc * tot;
         }
     }
+    cp_wait(0);  // no small copy may land after the block has released its shared memory
     if (!ok) {
-        // a copy never completed: report it, then wait (bounded) for this warp's copies still
-        // in flight so that none lands after the block has released its shared memory
+        // a tile copy never completed: report it, then wait (bounded) for this warp's copies
+        // still in flight so that none lands after the block has released its shared memory
         if (lane == 0) atomicExch(err, 1);
         for (unsigned u = consumed; u < issued; ++u)
             ring_wait(smem_addr(&bars[u % S]), (u / S) & 1);

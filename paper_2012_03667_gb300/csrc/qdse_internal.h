@@ -151,16 +151,13 @@ struct Grid {              // FP64 grid arrays on the device (global point index
 constexpr int kRows = 4;   // external points per warp in the batched sweeps (1, 2 or 4)
 constexpr int kTickBlocksPerSM = kRows >= 4 ? 2 : 3;  // resident 256-thread sweep blocks per SM
 constexpr int kTile = 32;  // kernel precompute tile edge
-constexpr int kPoolTile = 128;  // kernel columns per pool tile (a multiple of 4)
-
 // Kernel pool layout.  The entries K_p(i, j) (plane p = 0, 1, 2 for K_0, K_T/(Q - P), K_3) of one
 // instance fill n * 3 * ld floats from k_off.  Rows come in groups of kRows (the last group may be
-// shorter, nr rows); a group's block starts at k_off + 3 i0 ld and holds its columns in pool
-// tiles of kPoolTile (the last one narrower); inside a tile, each 4-column block stores the
-// 3 nr plane-rows m = 3 r + p as consecutive float4.  So any column range of a tile is one
-// contiguous run (one bulk copy), and a lane reading one 4-column block gets all the group's
-// rows from adjacent 16-byte words.  For full groups of 4 rows the 12 plane-rows of block q are
-// stored in the order m ^ ((q >> 1) & 3), which makes 16-byte shared-memory reads of 8
+// shorter, nr rows); a group's block starts at k_off + 3 i0 ld, and each 4-column block q of it
+// stores the 3 nr plane-rows m = 3 r + p as consecutive float4.  So any column range of a group
+// is one contiguous run (one bulk copy), and a lane reading one 4-column block gets all the
+// group's rows from adjacent 16-byte words.  For full groups of 4 rows the 12 plane-rows of block
+// q are stored in the order m ^ ((q >> 1) & 3), which makes 16-byte shared-memory reads of 8
 // consecutive blocks hit 8 different bank quads.
 __host__ __device__ inline int kswz(int nr, int q) {
     return ((3 * nr) & 3) == 0 ? ((q >> 1) & 3) : 0;
@@ -169,8 +166,7 @@ __host__ __device__ inline long long kpos(long long k_off, int n, int ld, int i,
     const int i0 = i - i % kRows;
     const int nr = (n - i0 < kRows) ? n - i0 : kRows;
     const int m = 3 * (i - i0) + p, q = j >> 2;
-    return k_off + 3LL * i0 * ld + 3LL * nr * kPoolTile * (j / kPoolTile) +
-           ((long long)((j % kPoolTile) >> 2) * 3 * nr + (m ^ kswz(nr, q))) * 4 + (j & 3);
+    return k_off + 3LL * i0 * ld + ((long long)q * 3 * nr + (m ^ kswz(nr, q))) * 4 + (j & 3);
 }
 // FP32 node vectors (a, b, u1, u2, u3 and their tangents): component c of padded node x (= v_off
 // + j) at 20 (x / 4) + 4 c + x % 4, so the five components of a 4-node block are one 80-byte run
@@ -197,9 +193,7 @@ struct KRow {
         m0 = 3 * (i - i0);
     }
     __device__ long long off(int p, int j) const {
-        return base + 3LL * nr * kPoolTile * (j / kPoolTile) +
-               ((long long)((j % kPoolTile) >> 2) * 3 * nr + ((m0 + p) ^ kswz(nr, j >> 2))) * 4 +
-               (j & 3);
+        return base + ((long long)(j >> 2) * 3 * nr + ((m0 + p) ^ kswz(nr, j >> 2))) * 4 + (j & 3);
     }
 };
 
