@@ -106,9 +106,9 @@ void free_ctx(qdse_ctx* c) {
                     c->work.dvec32, c->work.ddia32, c->work.d32, c->work.dvec64, c->work.ddia64,
                     c->work.lam, c->work.lamn, c->d_Khi, c->d_Klo, c->d_Kwhi, c->d_Kwlo,
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
-                    c->grid.groups, c->grid.nnz, c->work.items, c->work.item_count,
-                    c->work.work_ctr, c->grid.gdesc, c->grid.gphase, c->work.ilist,
-                    c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd};
+                    c->grid.groups, c->grid.nnz, c->grid.gdesc, c->grid.gphase, c->work.ilist,
+                    c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd,
+                    c->grid.W32, c->grid.wt32, c->grid.stc32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -216,8 +216,8 @@ cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
     return launch_update(c, A, B);
 }
 
-constexpr int kGraphTicks = 48;  // ticks per captured chunk: a multiple of 6 keeps the list
-                                 // buffers (mod 3) and work-item buffers (mod 2) in step
+constexpr int kGraphTicks = 48;  // ticks per captured chunk: a multiple of 3 keeps the
+                                 // active-list buffers (mod 3) in step
 
 // Capture kGraphTicks ticks on the internal stream into c->gexec (A, B fixed).
 qdse_status capture_chunk(qdse_ctx* c, double* A, double* B, int path) {
@@ -421,7 +421,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
             gdesc.push_back(d);
         }
     }
-    std::vector<float> sp32(N), sq32(N);
+    std::vector<float> sp32(N), sq32(N), W32(N), wt32(N), stc32(3 * (size_t)N);
     for (int b = 0; b < n_inst; ++b) {
         const HostInst& h = c->hinst[b];
         const int o0 = h.x_off;
@@ -434,6 +434,9 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         rsq[j] = std::sqrt(sq[j]);
         sp32[j] = (float)sp[j];
         sq32[j] = (float)sq[j];
+        W32[j] = (float)W[j];
+        wt32[j] = (float)wt[j];
+        for (int k = 0; k < 3; ++k) stc32[3 * (size_t)j + k] = (float)stc[3 * (size_t)j + k];
     }
     std::vector<double> z(t), y(t), s2(t), wz(t);
     for (auto& kv : t_of) build_angular(kv.first, &z[kv.second], &y[kv.second], &s2[kv.second], &wz[kv.second]);
@@ -463,6 +466,9 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->grid.sta, N);
     CALLOC(c->grid.sp32, N);
     CALLOC(c->grid.ktd, N);
+    CALLOC(c->grid.W32, N);
+    CALLOC(c->grid.wt32, N);
+    CALLOC(c->grid.stc32, 3 * (size_t)N);
     CALLOC(c->grid.sq32, N);
     CALLOC(c->grid.z, t);
     CALLOC(c->grid.y, t);
@@ -475,16 +481,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, dev);
-        long long it64 = 0;
-        for (int b = 0; b < n_inst; ++b) it64 += (c->hinst[b].g.n_p + 63) / 64;
-        c->work.rb = (it64 >= 4LL * (c->n_sms > 0 ? c->n_sms : 152)) ? 64 : 8;
-        long long mi = 0;
-        for (int b = 0; b < n_inst; ++b) mi += (c->hinst[b].g.n_p + c->work.rb - 1) / c->work.rb;
-        c->work.max_items = (int)mi;
     }
-    CALLOC(c->work.items, 2 * (size_t)c->work.max_items);
-    CALLOC(c->work.item_count, 2);
-    CALLOC(c->work.work_ctr, 1);
     CALLOC(c->work.ilist, 3 * (size_t)n_inst);
     CALLOC(c->work.glist, 3 * (size_t)ng);
     CALLOC(c->work.lcount, 6);
@@ -532,7 +529,10 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         {c->grid.rsq, rsq.data(), sizeof(double) * N}, {c->grid.wt, wt.data(), sizeof(double) * N},
         {c->grid.stc, stc.data(), sizeof(double) * 3 * (size_t)N},
         {c->grid.sta, sta.data(), sizeof(int) * N}, {c->grid.sp32, sp32.data(), sizeof(float) * N},
-        {c->grid.sq32, sq32.data(), sizeof(float) * N}, {c->grid.z, z.data(), sizeof(double) * t},
+        {c->grid.sq32, sq32.data(), sizeof(float) * N}, {c->grid.W32, W32.data(), sizeof(float) * N},
+        {c->grid.wt32, wt32.data(), sizeof(float) * N},
+        {c->grid.stc32, stc32.data(), sizeof(float) * 3 * (size_t)N},
+        {c->grid.z, z.data(), sizeof(double) * t},
         {c->grid.y, y.data(), sizeof(double) * t}, {c->grid.s2, s2.data(), sizeof(double) * t},
         {c->grid.wz, wz.data(), sizeof(double) * t},
         {c->grid.row_inst, row_inst.data(), sizeof(int) * N},

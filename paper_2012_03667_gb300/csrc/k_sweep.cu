@@ -73,7 +73,7 @@ __device__ double block_sum(double v, double* sh) {
     return r;
 }
 
-// The set of threads that updates one instance: a whole block, or one warp (fused into a sweep).
+// The set of threads that updates one instance: a whole block.
 struct BlockTeam {
     double* sh;
     __device__ int tid() const { return threadIdx.x; }
@@ -81,14 +81,15 @@ struct BlockTeam {
     __device__ void sync() const { __syncthreads(); }
     __device__ double max(double v) const { return block_max(v, sh); }
     __device__ bool leader() const { return threadIdx.x == 0; }
-};
-
-struct WarpTeam {
-    __device__ int tid() const { return threadIdx.x & 31; }
-    __device__ int size() const { return 32; }
-    __device__ void sync() const { __syncwarp(); }
-    __device__ double max(double v) const { return warp_max(v); }
-    __device__ bool leader() const { return (threadIdx.x & 31) == 0; }
+    // the leader's v to every thread
+    __device__ int bcast(int v) const {
+        __syncthreads();
+        if (threadIdx.x == 0) reinterpret_cast<int*>(sh)[0] = v;
+        __syncthreads();
+        v = reinterpret_cast<const int*>(sh)[0];
+        __syncthreads();
+        return v;
+    }
 };
 
 template <typename T, bool LO>
@@ -192,6 +193,46 @@ __device__ void prepare_tangent(const DevInst& I, const Grid& g, int ntot, const
                                   c[2] * (double)vb[s0 + 2]);
         }
     }
+}
+
+// FP32 node vectors from the FP32 iterate, computed in FP32 (they are stored in FP32): the same
+// quantities as prepare_vectors, the stencil quotient in the difference form
+// c0 (x0 - x1) + c2 (x2 - x1) (the coefficients of a derivative stencil sum to zero), which keeps
+// FP32 accuracy where the iterate is flat.
+__device__ void prepare_vectors32(const DevInst& I, const Grid& g, int ntot, const float* xa,
+                                  const float* xb, float* vec, int vb, float* dia, int tid,
+                                  int nth) {
+    for (int j = tid; j < I.n; j += nth) {
+        const int gj = I.x_off + j;
+        const float wt = g.wt32[gj];
+        float a = xa[gj], b = xb[gj];
+        if (wt != 0.f) {
+            a = fmaf(wt, xa[gj + 1] - a, a);
+            b = fmaf(wt, xb[gj + 1] - b, b);
+        }
+        const float Q = g.sq32[gj];
+        const float e = g.W32[gj] / fmaf(Q * a, a, b * b);
+        const float ea = e * a;
+        vec[vpos(vb + j, 0)] = a;
+        vec[vpos(vb + j, 1)] = b;
+        vec[vpos(vb + j, 2)] = e * b;
+        vec[vpos(vb + j, 3)] = ea;
+        vec[vpos(vb + j, 4)] = ea * Q;
+        if (I.mode == QDSE_COLLOCATED) {
+            const int s0 = I.x_off + g.sta[gj];
+            const float* c = g.stc32 + 3 * (size_t)gj;
+            dia[gj] = fmaf(c[0], xa[s0] - xa[s0 + 1], c[2] * (xa[s0 + 2] - xa[s0 + 1]));
+            dia[ntot + gj] = fmaf(c[0], xb[s0] - xb[s0 + 1], c[2] * (xb[s0 + 2] - xb[s0 + 1]));
+        }
+    }
+}
+
+// R7 relative change in FP32: |d| / max(|x_new|, floor); 0 when d == 0.
+__device__ __forceinline__ float rel_change32(float d, float xnew, float floor_) {
+    d = fabsf(d);
+    if (d == 0.f) return 0.f;
+    const float den = fmaxf(fabsf(xnew), floor_);
+    return den > 0.f ? d / den : INFINITY;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -611,8 +652,11 @@ __global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ i
 __device__ void prepare_phase(int phase, const DevInst& I, const Grid& g, const Work& w, int ntot,
                               const double* A, const double* B, int tid = -1, int nth = 0) {
     if (phase == PH_PICARD32) {
-        prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.nv, I.v_off,
-                                      w.dia32, tid, nth);
+        if (tid < 0) {
+            tid = threadIdx.x;
+            nth = blockDim.x;
+        }
+        prepare_vectors32(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, I.v_off, w.dia32, tid, nth);
     } else if (phase == PH_RESID64 || phase == PH_PICARD64) {
         prepare_vectors<double, double>(I, g, ntot, A, B, w.vec64, ntot, I.x_off, w.dia64, tid,
                                         nth);
@@ -623,14 +667,6 @@ __device__ void prepare_phase(int phase, const DevInst& I, const Grid& g, const 
     }
 }
 
-// List the items (instance b, first row) of an unfinished instance for the next sweep.
-__device__ __forceinline__ void append_items(const Work& w, int buf, int b, int n) {
-    const int cnt = (n + w.rb - 1) / w.rb;
-    const int base = atomicAdd(w.item_count + buf, cnt);
-    if (base + cnt > w.max_items) return;  // cannot happen while the lists are reset every tick
-    int2* dst = w.items + (size_t)buf * w.max_items + base;
-    for (int t = 0; t < cnt; ++t) dst[t] = make_int2(b, t * w.rb);
-}
 
 // Set every instance to its first phase, convert the start to FP32 where needed and form the
 // vectors of the first sweep.  One block per instance.
@@ -658,7 +694,6 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         s.loc = (phase0 == PH_PICARD32) ? 1 : 0;
         s.pad = 0;
         state[b] = s;
-        append_items(w, 0, b, I.n);
         w.ilist[atomicAdd(w.lcount + 0, 1)] = b;
         const int ng = (I.n + kRows - 1) / kRows;
         const int gb = atomicAdd(w.lcount + 3, ng);
@@ -675,8 +710,7 @@ template <typename Team>
 __device__ void update_instance(const Team& T, int b, const DevInst* __restrict__ inst,
                                 DevState* state, const Ctl* __restrict__ ctl, const Grid& g,
                                 const Work& w, double* A, double* B, int ntot, int* count,
-                                unsigned long long* ctr, int next_list, int next_items,
-                                int list_items) {
+                                unsigned long long* ctr, int next_list) {
     DevState s = state[b];
     if (s.phase == PH_DONE) return;
     const DevInst I = inst[b];
@@ -701,16 +735,53 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
     bool done = false;
     int status = s.status;
 
-    if (s.phase == PH_PICARD32 || s.phase == PH_PICARD64 || s.phase == PH_RESID64) {
+    if (s.phase == PH_PICARD32) {
+        // relaxed FP32 Picard step and its R7 relative change, in FP32 like the iterate
+        const float al = (float)C.alpha, am = (float)(1.0 - C.alpha);
+        float bmax = 0.f;
+        bool badj = false;
+        for (int j = T.tid(); j < I.n; j += T.size()) {
+            const int gj = o + j;
+            const float fa = am * w.x32[gj] + al * __ldcg(w.xn32 + gj);
+            const float fb = am * w.x32[ntot + gj] + al * __ldcg(w.xn32 + ntot + gj);
+            bmax = fmaxf(bmax, fabsf(fb));
+            badj = badj || !isfinite(fa) || !isfinite(fb);
+        }
+        bmax = (float)T.max((double)bmax);
+        const bool bad = T.max(badj ? 1.0 : 0.0) != 0.0;
+        const float fl = 1e-12f * bmax;
+        float ch = 0.f;
+        for (int j = T.tid(); j < I.n; j += T.size()) {
+            const int gj = o + j;
+            const float xa = w.x32[gj], xb = w.x32[ntot + gj];
+            const float fa = am * xa + al * __ldcg(w.xn32 + gj);
+            const float fb = am * xb + al * __ldcg(w.xn32 + ntot + gj);
+            ch = fmaxf(ch, fmaxf(rel_change32(fa - xa, fa, 0.f), rel_change32(fb - xb, fb, fl)));
+            w.x32[gj] = fa;
+            w.x32[ntot + gj] = fb;
+        }
+        s.change = T.max((double)ch);
+        s.iters += 1;
+        if (bad) {
+            done = true;
+            status = QDSE_ERR_NONFINITE;
+        } else if (C.final_phase == PH_PICARD32) {
+            // FP32-only solves finish here; mixed solves always finish in FP64
+            if (!C.never_converge && s.change <= C.tol) {
+                done = true;
+                status = QDSE_OK;
+            }
+        } else if (s.change <= C.sw_tol || s.iters >= C.max_fp32) {
+            next = PH_RESID64;  // hand the FP32 iterate to the FP64 refinement
+        }
+    } else if (s.phase == PH_PICARD64 || s.phase == PH_RESID64) {
         // relaxed Picard step (or the residual of one) and its R7 relative change
-        const bool f32 = (s.phase == PH_PICARD32);
         double bmax = 0.0, bad = 0.0;
         for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
-            double fb = f32 ? (double)__ldcg(w.xn32 + ntot + gj) : __ldcg(w.xn64 + ntot + gj);
-            double fa = f32 ? (double)__ldcg(w.xn32 + gj) : __ldcg(w.xn64 + gj);
-            double xb = f32 ? (double)w.x32[ntot + gj] : B[gj];
-            double xa = f32 ? (double)w.x32[gj] : A[gj];
+            double fb = __ldcg(w.xn64 + ntot + gj);
+            double fa = __ldcg(w.xn64 + gj);
+            const double xb = B[gj], xa = A[gj];
             if (s.phase != PH_RESID64) {
                 fa = (1.0 - C.alpha) * xa + C.alpha * fa;
                 fb = (1.0 - C.alpha) * xb + C.alpha * fb;
@@ -724,19 +795,15 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         double ch = 0.0;
         for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
-            double fa = f32 ? (double)__ldcg(w.xn32 + gj) : __ldcg(w.xn64 + gj);
-            double fb = f32 ? (double)__ldcg(w.xn32 + ntot + gj) : __ldcg(w.xn64 + ntot + gj);
-            const double xa = f32 ? (double)w.x32[gj] : A[gj];
-            const double xb = f32 ? (double)w.x32[ntot + gj] : B[gj];
+            double fa = __ldcg(w.xn64 + gj);
+            double fb = __ldcg(w.xn64 + ntot + gj);
+            const double xa = A[gj], xb = B[gj];
             if (s.phase != PH_RESID64) {
                 fa = (1.0 - C.alpha) * xa + C.alpha * fa;
                 fb = (1.0 - C.alpha) * xb + C.alpha * fb;
             }
             ch = fmax(ch, fmax(rel_change(fa - xa, fa, 0.0), rel_change(fb - xb, fb, fl)));
-            if (s.phase == PH_PICARD32) {
-                w.x32[gj] = (float)fa;
-                w.x32[ntot + gj] = (float)fb;
-            } else if (s.phase == PH_PICARD64) {
+            if (s.phase == PH_PICARD64) {
                 A[gj] = fa;
                 B[gj] = fb;
             } else {  // residual: keep r = F(x) - x for the correction solve
@@ -773,14 +840,11 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
                     w.x32[ntot + gj] = (float)B[gj];
                 }
                 T.sync();
-                prepare_vectors<float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, w.nv,
-                                              I.v_off, w.dia32, T.tid(), T.size());
+                prepare_vectors32(I, g, ntot, w.x32, w.x32 + ntot, w.vec32, I.v_off, w.dia32,
+                                  T.tid(), T.size());
                 next = PH_TANGENT32;
                 s.inner = 0;
             }
-        } else if (s.phase == PH_PICARD32 && !done && C.final_phase != PH_PICARD32 &&
-                   (ch <= C.sw_tol || s.iters >= C.max_fp32)) {
-            next = PH_RESID64;  // hand the FP32 iterate to the FP64 refinement
         }
     } else if (s.phase == PH_TANGENT32) {
         // delta <- delta + alpha (J delta + r - delta); relative change of delta (max norm)
@@ -848,13 +912,16 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         state[b] = s;
         if (!done) {
             if (count) atomicAdd(count, 1);
-            if (list_items) append_items(w, next_items, b, I.n);
-            // the instance and its row groups stay on the active lists of the next tick
+            // the instance stays on the active list of the next tick
             w.ilist[(size_t)next_list * w.n_inst + atomicAdd(w.lcount + next_list, 1)] = b;
-            const int ng = (I.n + kRows - 1) / kRows;
-            const int gb = atomicAdd(w.lcount + 3 + next_list, ng);
-            for (int t = 0; t < ng; ++t) w.glist[(size_t)next_list * w.n_groups + gb + t] = I.g_off + t;
         }
+    }
+    if (!done) {
+        // ... and so do its row groups
+        const int ng = (I.n + kRows - 1) / kRows;
+        const int gb = T.bcast(T.leader() ? atomicAdd(w.lcount + 3 + next_list, ng) : 0);
+        for (int t = T.tid(); t < ng; t += T.size())
+            w.glist[(size_t)next_list * w.n_groups + gb + t] = I.g_off + t;
     }
     T.sync();
 }
@@ -1261,11 +1328,9 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
 __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst, DevState* state,
                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
                                                 double* A, double* B, int ntot, int* count,
-                                                unsigned long long* ctr, int list, int items_next,
-                                                int list_items) {
+                                                unsigned long long* ctr, int list) {
     __shared__ double sh[32];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *w.work_ctr = 0;  // the next work-list sweep's item counter
         const int clr = (list + 2) % 3;  // lists of two ticks ahead start empty
         w.lcount[clr] = 0;
         w.lcount[3 + clr] = 0;
@@ -1275,7 +1340,7 @@ __global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst
     const int* ids = w.ilist + (size_t)list * w.n_inst;
     for (int k = blockIdx.x; k < n; k += gridDim.x)
         update_instance(T, ids[k], inst, state, ctl, g, w, A, B, ntot, count, ctr,
-                        (list + 1) % 3, items_next, list_items);
+                        (list + 1) % 3);
 }
 
 // Copy the final iterate out of the FP32 store where needed and report per-instance results.
@@ -1387,9 +1452,7 @@ static inline int row_blocks(int ntot) { return (ntot + 7) / 8; }
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0) {
     cudaError_t e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c->work.item_count, 0, 2 * sizeof(int), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->work.work_ctr, 0, sizeof(int), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->work.lcount, 0, 6 * sizeof(int), c->stream);
+    e = cudaMemsetAsync(c->work.lcount, 0, 6 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     c->tick = 0;
     prof_begin(c, PK_OTHER);
@@ -1451,8 +1514,7 @@ cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
     const int blocks = std::min(c->n_inst, 8 * (c->n_sms > 0 ? c->n_sms : 152));
     k_update<<<blocks, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
                                             A, B, c->n_total, c->d_count, c->d_sweeps,
-                                            (int)(c->tick % 3), (int)((c->tick + 1) & 1),
-                                            (c->sweep_kind == 1 && c->opt.precision != QDSE_FP64) ? 1 : 0);
+                                            (int)(c->tick % 3));
     c->tick++;
     c->launches++;
     prof_end(c);

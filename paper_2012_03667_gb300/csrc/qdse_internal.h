@@ -104,13 +104,6 @@ struct Work {
     double* ddia64; // [2]
     double* lam;    // [2] adjoint iterate
     double* lamn;   // [2] adjoint sweep output
-    // work list of the bulk-copy sweep: items (instance, first row) of rb rows, two buffers
-    // (the update of tick t lists the items of tick t + 1)
-    int2* items;    // [2][max_items]
-    int* item_count;  // [2]
-    int* work_ctr;  // [1] next item to take in the current sweep
-    int rb;         // rows per item
-    int max_items;
     // active lists: instances and row groups still running, three buffers (tick t reads list
     // t % 3, appends the survivors to (t + 1) % 3 and empties (t + 2) % 3);
     // lcount = {instances[0..2], groups[0..2]}
@@ -130,8 +123,11 @@ struct Grid {              // FP64 grid arrays on the device (global point index
     double* wt;            // staggered: weight of the upper bracket point (0 at the last node)
     double* stc;           // [3] collocated: Lagrange derivative coefficients (per s) of the stencil
     int* sta;              // collocated: first point of the stencil (local index)
-    float* sp32;           // float copies
+    float* sp32;           // float copies (for the FP32 sweeps and their updates)
     float* sq32;
+    float* W32;
+    float* wt32;
+    float* stc32;          // [3]
     double* z;             // angular nodes (per instance slice)
     double* y;             // 1 - z
     double* s2;            // 1 - z^2
