@@ -25,9 +25,18 @@
 
 namespace qdse {
 
-// Pairs with (sqrt P - sqrt Q)^2 / w^2 beyond this have every term below the smallest FP32
-// subnormal once stored, so they are written as exact zeros without evaluating the sum.
-constexpr double kSkipExponent = 130.0;
+// Pairs with (sqrt P - sqrt Q)^2 / w^2 beyond this are written as exact zeros without
+// evaluating the sum.  Every term of such a pair carries exp(-k^2/w^2) <= e^-70 (k^2 >=
+// (sqrt P - sqrt Q)^2); the polynomial factors of the integrand and of the weights W_j/(Q A^2 +
+// B^2) grow by at most (Q_far / Q_near)^3 <~ 1e6 across the grids and w of interest before the
+// Gaussian takes over, so the dropped entries change a row's sum by less than 1e-20 of it, far
+// below FP64 resolution.
+constexpr double kSkipExponent = 70.0;
+// Inside a pair, the angular terms have exponents k^2/w^2 increasing with the node index (1 - z
+// increases); once a term's exponent exceeds the first term's by this much, it and every later
+// term are below e^-60 of the first, times polynomial ratios (g_n, 1/k^2) of at most about 1e4
+// (nodes down to theta = pi/129): the sum stops there.
+constexpr double kAngularCut = 60.0;
 
 template <bool WITH_W>
 __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restrict__ inst, Grid g,
@@ -77,8 +86,10 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
             const double dd = (rP - rQ) * (rP - rQ);
             if (dd * iw2 < kSkipExponent) {
                 const double c2 = 2.0 * rP * rQ, x0 = rP * rQ, PQ = P * Q, PpQ = P + Q;
+                const double ex_last = (dd + c2 * sy[0]) * iw2 + kAngularCut;
                 for (int k = 0; k < I.nt; ++k) {
                     const double k2 = dd + c2 * sy[k];
+                    if (k2 * iw2 > ex_last) break;
                     const double E = sw[k] * exp(-k2 * iw2);
                     const double rk = 1.0 / k2;
                     const double x = x0 * sz[k];

@@ -989,40 +989,50 @@ __global__ void __launch_bounds__(256, kTickBlocksPerSM) k_tick(const DevInst* _
 // tile it refills the freed slot with the next tile of its group sequence, so the following
 // tiles are in flight while it computes.
 //
-// Groups.  Everything else a group needs travels through a per-warp queue of kRingQueue entries
-// in shared memory, filled by small asynchronous copies (cp.async, tracked with commit/wait
-// groups): when the copying side moves onto group k it reads k's descriptor from entry k, and
-// requests the row constants of group k (entry k), the descriptor and phase of group k + 1 (whose
-// list id entry k + 1 already holds) and the list id of group k + 2.  So it never waits on a
-// global load, and the computing side finds a group's descriptor, phase and row constants in
-// shared memory.  The removable-limit term of each row is added once per group by the lane that
+// Groups.  Everything else a group needs travels through small per-warp rings in shared memory,
+// filled by small asynchronous copies (cp.async, tracked with commit/wait groups): when the
+// copying side moves onto group k it reads k's descriptor and phase (requested two moves
+// earlier), and requests the row constants of group k, the descriptor and phase of group k + 2
+// (whose list id arrived two moves earlier) and the list id of group k + 4.  So it never waits on
+// a global load, even when it moves over several short groups in a row, and the computing side
+// finds a group's descriptor, phase and row constants in shared memory.  The removable-limit term of each row is added once per group by the lane that
 // stores the row's total.  Groups in an FP64 phase take the global-memory path of tick_group and
 // no slots.
 constexpr int kTileCols = 128;                         // columns per tile (4 per lane)
 constexpr int kVecOff = 3 * kRows * kTileCols;         // slot floats before the node vectors
 constexpr int kTileFloats = (3 * kRows + 5) * kTileCols;
-constexpr int kRingQueue = 5;                          // queue entries per warp
+constexpr int kRcRing = 3;    // row-constant entries per warp (groups k .. k + 2 in use)
+constexpr int kDescRing = 5;  // descriptor entries per warp (up to group k + 4)
+constexpr int kIdRing = 8;    // list-id entries per warp (up to group k + 6)
 constexpr long long kRingWaitBudget = 2000000000LL;    // clock cycles (about 1 s)
 static_assert((kTileFloats * sizeof(float)) % 16 == 0, "tile slots must stay 16-byte aligned");
 static_assert(kRows == 4, "the queue's row-constant copies are laid out for groups of 4 rows");
 
-struct RingEntry {        // one group on its way from the copying to the computing side
-    GroupDesc d;          // descriptor (with the instance parameters)
-    int phase, id, pad[2];
+struct RingDesc {         // a group's descriptor (with the instance parameters) and phase
+    GroupDesc d;
+    int phase, pad[3];
+};
+struct RingRows {         // a group's row constants
     float rc[6][kRows];   // per row: A_i, B_i (FP32 iterate), P_i, stencil dA/ds, dB/ds, K_T(i,i)
     float vd[2][4];       // u1, u2 at the group's own nodes (collocated removable limit)
     float tc[4][kRows];   // tangent: dA_i, dB_i, stencil of the direction (A, B)
     float td[2][4];       // tangent: du1, du2 at the group's own nodes
 };
-static_assert(sizeof(RingEntry) % 16 == 0, "queue entries must stay 16-byte aligned");
+struct RingQueue {        // one warp's rings
+    RingDesc desc[kDescRing];
+    RingRows rows[kRcRing];
+    int id[kIdRing];
+};
+static_assert(sizeof(RingDesc) % 16 == 0 && sizeof(RingRows) % 16 == 0 &&
+                  sizeof(RingQueue) % 16 == 0,
+              "ring entries must stay 16-byte aligned");
 
 template <int WARPS, int SLOTS>
 struct RingCfg {
     static constexpr int kWarps = WARPS, kSlots = SLOTS;
     static constexpr size_t kTileBytes = (size_t)WARPS * SLOTS * kTileFloats * sizeof(float);
     static constexpr size_t kBarBytes = (size_t)WARPS * SLOTS * 8;
-    static constexpr size_t kSmem =
-        kTileBytes + kBarBytes + (size_t)WARPS * kRingQueue * sizeof(RingEntry);
+    static constexpr size_t kSmem = kTileBytes + kBarBytes + (size_t)WARPS * sizeof(RingQueue);
     static_assert(kSmem <= 227 * 1024, "ring sweep shared memory");
     static_assert(kBarBytes % 16 == 0, "queue must start 16-byte aligned");
 };
@@ -1099,14 +1109,13 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     k_tick_ring(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g, Work w,
                 const float* __restrict__ Khi, const float* __restrict__ Klo, const double* A,
                 const double* B, int ntot, int list, int* err) {
-    constexpr int S = Cfg::kSlots, Q = kRingQueue;
+    constexpr int S = Cfg::kSlots;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * S * kTileFloats;
     unsigned long long* bars =
         reinterpret_cast<unsigned long long*>(smem + Cfg::kTileBytes) + warp * S;
-    RingEntry* queue =
-        reinterpret_cast<RingEntry*>(smem + Cfg::kTileBytes + Cfg::kBarBytes) + warp * Q;
+    RingQueue& q = reinterpret_cast<RingQueue*>(smem + Cfg::kTileBytes + Cfg::kBarBytes)[warp];
     if (lane == 0) {
         for (int k = 0; k < S; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[k]))
@@ -1115,26 +1124,48 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     }
     __syncwarp();
 
+    // The block takes every gridDim.x-th entry of the active group list (a sample of all the
+    // instances, so blocks get even shares); its warps claim those groups one at a time (a shared
+    // counter), each claiming four groups ahead of its copying side, so warps that drew short
+    // groups take more of them.
+    __shared__ int s_next;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
     const int nact = w.lcount[3 + list];
-    const int* ids = w.glist + (size_t)list * w.n_groups;
-    const int stride = gridDim.x * Cfg::kWarps;
-    const int t0 = blockIdx.x * Cfg::kWarps + warp;
-    const int nmine = t0 < nact ? (nact - 1 - t0) / stride + 1 : 0;
-    if (nmine == 0) return;
+    const int G = gridDim.x;
+    const int cnt = (int)blockIdx.x < nact ? (nact - 1 - (int)blockIdx.x) / G + 1 : 0;
+    const int* ids = w.glist + (size_t)list * w.n_groups + blockIdx.x;
+    auto claim = [&]() -> int {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&s_next, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        return c < cnt ? c * G : -1;
+    };
+    int nmine = 1 << 30;  // groups this warp claimed: known once a claim fails
     const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
     const double kappa = ctl->kappa;
     const uint64_t pol = evict_first_policy();
 
-    // prologue: list ids of groups 0 and 1, then the descriptor and phase of group 0
-    if (lane == 0) cp4(&queue[0].id, ids + t0);
-    if (lane == 1 && nmine > 1) cp4(&queue[1].id, ids + t0 + stride);
+    // prologue: claim groups 0 .. 3 and fetch their list ids, then the descriptors and phases of
+    // groups 0 and 1, as two commit groups (the first move waits for all but the most recent one)
+    for (int k = 0; k < 4 && k < nmine; ++k) {
+        const int c = claim();
+        if (c < 0) nmine = k;
+        else if (lane == 0) cp4(&q.id[k], ids + c);
+    }
+    if (nmine == 0) return;
     cp_commit();
     cp_wait(0);
     __syncwarp();
-    if (lane < 4) cp16(reinterpret_cast<int4*>(&queue[0].d) + lane,
-                       reinterpret_cast<const int4*>(g.gdesc + queue[0].id) + lane);
-    if (lane == 4) cp4(&queue[0].phase, g.gphase + queue[0].id);
+    if (lane < 10 && (lane / 5) < nmine) {
+        const int k = lane / 5, part = lane % 5;
+        const int id = q.id[k];
+        if (part < 4) cp16(reinterpret_cast<int4*>(&q.desc[k].d) + part,
+                           reinterpret_cast<const int4*>(g.gdesc + id) + part);
+        else cp4(&q.desc[k].phase, g.gphase + id);
+    }
     cp_commit();
+    cp_commit();  // an empty group: the first move's wait for "all but one" covers the above
 
     // copying side: current group pk, its tiles from column pc while ptiles
     int pk = -1, pc = 0, pjhi = 0, pnr = 0, pvoff = 0;
@@ -1147,11 +1178,12 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     auto produce = [&](int ck) -> bool {
         if (!ptiles) {
             const int k = pk + 1;
-            if (k >= nmine || k + 2 - ck >= Q) return false;
+            if (k >= nmine || k - ck > 2) return false;
             pk = k;
-            cp_wait(0);  // entry k's descriptor and phase, entry k + 1's list id
+            cp_wait(1);  // group k's descriptor and phase, group k + 2's list id
             __syncwarp();
-            RingEntry& e = queue[k % Q];
+            const RingDesc& e = q.desc[k % kDescRing];
+            RingRows& rw = q.rows[k % kRcRing];
             const int ph = e.phase;
             const int o = e.d.x_off + e.d.i0, nr = e.d.nr, ib = e.d.v_off + e.d.i0;
             pjhi = e.d.jhi;
@@ -1160,8 +1192,8 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
             pkbase = e.d.kbase;
             pc = e.d.jlo;
             ptiles = (ph == PH_PICARD32 || ph == PH_TANGENT32) && pjhi > pc;
-            // row constants of group k
             if (lane < 6 * kRows) {
+                // row constants of group k
                 const int arr = lane / kRows, r = lane % kRows;
                 const float* src = arr == 0   ? w.x32 + o
                                    : arr == 1 ? w.x32 + ntot + o
@@ -1169,20 +1201,18 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                                    : arr == 3 ? w.dia32 + o
                                    : arr == 4 ? w.dia32 + ntot + o
                                               : g.ktd + o;
-                if (r < nr) cp4(&e.rc[arr][r], src + r);
+                if (r < nr) cp4(&rw.rc[arr][r], src + r);
             } else if (lane < 6 * kRows + 2) {
-                cp16(e.vd[lane - 6 * kRows], w.vec32 + vpos(ib, 2 + lane - 6 * kRows));
-            } else if (lane < 6 * kRows + 6) {
-                // descriptor of group k + 1 (16 bytes per lane) and its phase
-                if (k + 1 < nmine) {
-                    RingEntry& n1 = queue[(k + 1) % Q];
-                    cp16(reinterpret_cast<int4*>(&n1.d) + (lane - 6 * kRows - 2),
-                         reinterpret_cast<const int4*>(g.gdesc + n1.id) + (lane - 6 * kRows - 2));
+                cp16(rw.vd[lane - 6 * kRows], w.vec32 + vpos(ib, 2 + lane - 6 * kRows));
+            } else if (lane < 6 * kRows + 7) {
+                // descriptor (4 x 16 bytes) and phase of group k + 2
+                if (k + 2 < nmine) {
+                    const int part = lane - 6 * kRows - 2, id = q.id[(k + 2) % kIdRing];
+                    RingDesc& n2 = q.desc[(k + 2) % kDescRing];
+                    if (part < 4) cp16(reinterpret_cast<int4*>(&n2.d) + part,
+                                       reinterpret_cast<const int4*>(g.gdesc + id) + part);
+                    else cp4(&n2.phase, g.gphase + id);
                 }
-            } else if (lane == 6 * kRows + 6) {
-                if (k + 1 < nmine) cp4(&queue[(k + 1) % Q].phase, g.gphase + queue[(k + 1) % Q].id);
-            } else if (lane == 6 * kRows + 7) {
-                if (k + 2 < nmine) cp4(&queue[(k + 2) % Q].id, ids + t0 + (k + 2) * stride);
             }
             if (ph == PH_TANGENT32) {
                 if (lane < 4 * kRows) {
@@ -1191,10 +1221,15 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                                        : arr == 1 ? w.d32 + ntot + o
                                        : arr == 2 ? w.ddia32 + o
                                                   : w.ddia32 + ntot + o;
-                    if (r < nr) cp4(&e.tc[arr][r], src + r);
+                    if (r < nr) cp4(&rw.tc[arr][r], src + r);
                 } else if (lane < 4 * kRows + 2) {
-                    cp16(e.td[lane - 4 * kRows], w.dvec32 + vpos(ib, 2 + lane - 4 * kRows));
+                    cp16(rw.td[lane - 4 * kRows], w.dvec32 + vpos(ib, 2 + lane - 4 * kRows));
                 }
+            }
+            if (k + 4 < nmine) {
+                const int c = claim();  // list id of group k + 4
+                if (c < 0) nmine = k + 4;
+                else if (lane == 0) cp4(&q.id[(k + 4) % kIdRing], ids + c);
             }
             cp_commit();
             return true;
@@ -1235,11 +1270,11 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         while (pk < ck && produce(ck)) {
         }
         fill(ck);
-        cp_wait(pk - ck);  // entry ck's row constants
+        cp_wait(pk - ck);  // group ck's row constants
         __syncwarp();
-        const RingEntry& e = queue[ck % Q];
-        const GroupDesc& d = e.d;
-        const int phase = e.phase;
+        const GroupDesc& d = q.desc[ck % kDescRing].d;
+        const int phase = q.desc[ck % kDescRing].phase;
+        const RingRows& e = q.rows[ck % kRcRing];
         if (phase != PH_PICARD32 && phase != PH_TANGENT32) {
             const GroupDesc dc = d;
             tick_group(dc, phase, lane, inst[dc.b], ctl, g, w, Khi, Klo, A, B, ntot);
