@@ -73,13 +73,30 @@ __device__ double block_sum(double v, double* sh) {
     return r;
 }
 
-// The set of threads that updates one instance: a whole block.
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The set of threads that updates one instance: a whole block (blockDim.x a multiple of 32).
 struct BlockTeam {
-    double* sh;
+    double* sh;  // at least 32 doubles of shared memory
     __device__ int tid() const { return threadIdx.x; }
     __device__ int size() const { return blockDim.x; }
     __device__ void sync() const { __syncthreads(); }
     __device__ double max(double v) const { return block_max(v, sh); }
+    __device__ float maxf(float v) const {
+        float* f = reinterpret_cast<float*>(sh);
+        v = warp_maxf(v);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) f[threadIdx.x >> 5] = v;
+        __syncthreads();
+        const int l = threadIdx.x & 31;
+        v = (l < (int)(blockDim.x >> 5)) ? f[l] : 0.f;
+        return warp_maxf(v);  // every warp reduces the per-warp maxima itself
+    }
+    __device__ bool any(bool v) const { return __syncthreads_or(v) != 0; }
     __device__ bool leader() const { return threadIdx.x == 0; }
     // the leader's v to every thread
     __device__ int bcast(int v) const {
@@ -747,8 +764,8 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             bmax = fmaxf(bmax, fabsf(fb));
             badj = badj || !isfinite(fa) || !isfinite(fb);
         }
-        bmax = (float)T.max((double)bmax);
-        const bool bad = T.max(badj ? 1.0 : 0.0) != 0.0;
+        bmax = T.maxf(bmax);
+        const bool bad = T.any(badj);
         const float fl = 1e-12f * bmax;
         float ch = 0.f;
         for (int j = T.tid(); j < I.n; j += T.size()) {
@@ -760,7 +777,7 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             w.x32[gj] = fa;
             w.x32[ntot + gj] = fb;
         }
-        s.change = T.max((double)ch);
+        s.change = (double)T.maxf(ch);
         s.iters += 1;
         if (bad) {
             done = true;
@@ -1360,17 +1377,17 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
 
 // Advance every instance on the current active list after a tick (persistent blocks; used after
 // the on-the-fly FP64 sweep and the work-list sweep, which do not update instances themselves).
-__global__ void __launch_bounds__(256) k_update(const DevInst* __restrict__ inst, DevState* state,
+__global__ void __launch_bounds__(128) k_update(const DevInst* __restrict__ inst, DevState* state,
                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
                                                 double* A, double* B, int ntot, int* count,
                                                 unsigned long long* ctr, int list) {
-    __shared__ double sh[32];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int clr = (list + 2) % 3;  // lists of two ticks ahead start empty
         w.lcount[clr] = 0;
         w.lcount[3 + clr] = 0;
     }
-    const BlockTeam T{sh};
+    __shared__ double sh[32];
+    const BlockTeam T{sh};  // one block per instance
     const int n = w.lcount[list];
     const int* ids = w.ilist + (size_t)list * w.n_inst;
     for (int k = blockIdx.x; k < n; k += gridDim.x)
@@ -1546,8 +1563,8 @@ cudaError_t launch_tick(qdse_ctx* c, double* A, double* B) {
 
 cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
     prof_begin(c, PK_UPDATE);
-    const int blocks = std::min(c->n_inst, 8 * (c->n_sms > 0 ? c->n_sms : 152));
-    k_update<<<blocks, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
+    const int blocks = std::min(c->n_inst, 16 * (c->n_sms > 0 ? c->n_sms : 152));
+    k_update<<<blocks, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
                                             A, B, c->n_total, c->d_count, c->d_sweeps,
                                             (int)(c->tick % 3));
     c->tick++;
