@@ -1081,22 +1081,21 @@ __device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-__device__ __forceinline__ void bulk_copy(float* dst, const float* src, int bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_addr(dst)), "l"(src), "r"((uint32_t)bytes), "r"(bar)
-        : "memory");
-}
-
-// The same for data read once per sweep (the kernel pool): an L2 evict-first policy keeps the
-// pool's stream from displacing the small per-point arrays every group reads.
+// The same with an L2 policy: evict-first for data read once per sweep (the kernel pool), so the
+// pool's stream does not displace the small per-point arrays every group reads; evict-last for
+// the node vectors, which every group of an instance reads again.
 __device__ __forceinline__ uint64_t evict_first_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
-__device__ __forceinline__ void bulk_copy_evict_first(float* dst, const float* src, int bytes,
-                                                      uint32_t bar, uint64_t pol) {
+__device__ __forceinline__ uint64_t evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_copy_hint(float* dst, const float* src, int bytes,
+                                               uint32_t bar, uint64_t pol) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
         "[%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
@@ -1161,7 +1160,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     int nmine = 1 << 30;  // groups this warp claimed: known once a claim fails
     const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
     const double kappa = ctl->kappa;
-    const uint64_t pol = evict_first_policy();
+    const uint64_t pol = lane == 0 ? evict_first_policy() : evict_last_policy();
 
     // prologue: claim groups 0 .. 3 and fetch their list ids, then the descriptors and phases of
     // groups 0 and 1, as two commit groups (the first move waits for all but the most recent one)
@@ -1262,12 +1261,12 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                          "r"((uint32_t)(cols * (3 * pnr + 5) * 4))
                          : "memory");
         __syncwarp();
-        float* dst = ring + slot * kTileFloats;
-        if (lane == 0) {
-            bulk_copy_evict_first(dst, Khi + pkbase + (long long)(pc >> 2) * 3 * pnr * 4,
-                                  cols * 3 * pnr * 4, bar, pol);
-        } else if (lane == 1) {
-            bulk_copy(dst + kVecOff, w.vec32 + vpos(pvoff + pc, 0), cols * 5 * 4, bar);
+        if (lane < 2) {
+            // lane 0: the kernel run, lane 1: the node vectors (one instruction for both)
+            float* dst = ring + slot * kTileFloats + (lane ? kVecOff : 0);
+            const float* src = lane ? w.vec32 + vpos(pvoff + pc, 0)
+                                    : Khi + pkbase + (long long)(pc >> 2) * 3 * pnr * 4;
+            bulk_copy_hint(dst, src, cols * (lane ? 5 : 3 * pnr) * 4, bar, pol);
         }
         ++issued;
         pc += kTileCols;
