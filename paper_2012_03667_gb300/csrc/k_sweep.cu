@@ -1299,6 +1299,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         const bool tan = (phase == PH_TANGENT32);
         const int collocated = (d.mode == QDSE_COLLOCATED) && bc;
         const int nr = d.nr, jlo = d.jlo, jhi = d.jhi, i0 = d.i0, o = d.x_off + i0;
+        const bool full = !tan && bc && nr == kRows;
         Rows32 R;
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
@@ -1320,10 +1321,19 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
             const int col = c + 4 * lane;
             if (col < jhi) {
                 const float* sl = ring + slot * kTileFloats;
-                const float* kb = sl + lane * 3 * nr * 4;
                 const float* vb = sl + kVecOff + lane * 20;
                 auto V4 = [&](int comp) { return *reinterpret_cast<const float4*>(vb + 4 * comp); };
                 const float4 a = V4(0), b = V4(1), u1 = V4(2), u2 = V4(3), u3 = V4(4);
+                if (full) {
+                    // the common case, specialised: Picard sweep of a full group, BC vertex
+                    const float* kb = sl + lane * (3 * kRows * 4);
+                    const int sw = ((col >> 2) >> 1) & 3;  // kswz of a full group
+                    auto K = [&](int r, int pl) {
+                        return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
+                    };
+                    rows32_chunk<false>(R, K, kRows, 0, true, 0, a, b, u1, u2, u3, a, a, a, a, a);
+                } else {
+                const float* kb = sl + lane * 3 * nr * 4;
                 const int sw = kswz(nr, col >> 2);
                 auto K = [&](int r, int pl) {
                     return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
@@ -1335,6 +1345,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                     rows32_chunk<true>(R, K, nr, 0, bc, 0, a, b, u1, u2, u3, ea, eb, e1, e2, e3);
                 } else {
                     rows32_chunk<false>(R, K, nr, 0, bc, 0, a, b, u1, u2, u3, a, a, a, a, a);
+                }
                 }
             }
             __syncwarp();
