@@ -559,14 +559,16 @@ __device__ __forceinline__ void tick_group(const GroupDesc& d, int phase, int la
     }
 }
 
-// Copy every instance's parameters into its row groups' descriptors (after each upload).
-__global__ void k_group_params(const DevInst* __restrict__ inst, Grid g, int ngroups) {
+// Copy every instance's parameters into its row groups' descriptors (after each upload): the
+// FP32 sweep's scale kappa D and mass m.
+__global__ void k_group_params(const DevInst* __restrict__ inst, Grid g, int ngroups,
+                               double kappa) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ngroups) return;
     const DevInst I = inst[g.gdesc[t].b];
     g.gdesc[t].mode = I.mode;
-    g.gdesc[t].D = I.D;
-    g.gdesc[t].m = I.m;
+    g.gdesc[t].sc32 = (float)(kappa * I.D);
+    g.gdesc[t].m32 = (float)I.m;
 }
 
 // Narrow every group's column range to the union of its rows' nonzero bands.
@@ -751,6 +753,18 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
     int next = s.phase;
     bool done = false;
     int status = s.status;
+    if (s.phase == PH_PICARD32) {
+        // the grid constants the next sweep's node vectors need, into L1 while the change is
+        // computed (one 128-byte line per thread)
+        const int t = T.tid(), nl = (I.n + 31) / 32, nl3 = (3 * I.n + 31) / 32;
+        const void* pf = nullptr;
+        if (t < nl) pf = g.wt32 + o + 32 * t;
+        else if (t < 2 * nl) pf = g.sq32 + o + 32 * (t - nl);
+        else if (t < 3 * nl) pf = g.W32 + o + 32 * (t - 2 * nl);
+        else if (t < 4 * nl) pf = g.sta + o + 32 * (t - 3 * nl);
+        else if (t < 4 * nl + nl3) pf = g.stc32 + 3 * (size_t)o + 32 * (t - 4 * nl);
+        if (pf) asm volatile("prefetch.global.L1 [%0];" ::"l"(pf));
+    }
 
     if (s.phase == PH_PICARD32) {
         // relaxed FP32 Picard step and its R7 relative change, in FP32 like the iterate
@@ -1159,7 +1173,6 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     };
     int nmine = 1 << 30;  // groups this warp claimed: known once a claim fails
     const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
-    const double kappa = ctl->kappa;
     const uint64_t pol = lane == 0 ? evict_first_policy() : evict_last_policy();
 
     // prologue: claim groups 0 .. 3 and fetch their list ids, then the descriptors and phases of
@@ -1370,9 +1383,9 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                                : (-y1 * qB - x1 * eqB - Pl * (y2 * qA + x2 * eqA)) * KTd;
                 }
             }
-            const float sc = (float)(kappa * d.D);
+            const float sc = d.sc32;
             if (!isB) w.xn32[o + rr] = tan ? __fdividef(sc * tot, Pl) : 1.f + __fdividef(sc * tot, Pl);
-            else w.xn32[ntot + o + rr] = tan ? sc * tot : (float)d.m + sc * tot;
+            else w.xn32[ntot + o + rr] = tan ? sc * tot : d.m32 + sc * tot;
         }
     }
     cp_wait(0);  // no small copy may land after the block has released its shared memory
@@ -1535,8 +1548,8 @@ cudaError_t launch_group_bands(qdse_ctx* c) {
 
 cudaError_t launch_group_params(qdse_ctx* c) {
     if (c->n_groups <= 0) return cudaSuccess;
-    k_group_params<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(c->d_inst, c->grid,
-                                                                      c->n_groups);
+    k_group_params<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(
+        c->d_inst, c->grid, c->n_groups, c->opt.cf / (8.0 * kPi * kPi * kPi));
     c->launches++;
     return cudaGetLastError();
 }

@@ -53,8 +53,10 @@ struct GroupDesc {        // one row group (kRows consecutive external points of
     int b, i0, nr, jlo;   // instance, first row, rows in the group, band union start
     int jhi, v_off, x_off, ld;  // band union end, node-vector base, point base, kernel columns
     long long kbase;      // kernel-pool offset of the group's block (see kpos)
-    int mode, pad;        // grid mode of the instance
-    double D, m;          // instance parameters (refreshed with every parameter upload)
+    int mode;             // grid mode of the instance
+    float sc32, m32;      // kappa D and m of the instance in FP32 (refreshed with every
+                          // parameter upload)
+    int pad[3];
 };
 
 struct DevState {         // per-instance solver state, updated by the update kernel
