@@ -121,6 +121,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
+PROFILE = os.path.join(ROOT, "profiles", "k_tick_ring_scan256.md")
+
+
+def traffic_ratio():
+    """DRAM bytes per algorithmic byte of the FP32 sweep kernel, from the ncu capture summarised in
+    profiles/ (a 256-instance tick of the same scan; traffic grows in proportion to the kernel
+    entries a launch reads, so it scales to any launch by the algorithmic bytes)."""
+    try:
+        with open(PROFILE) as f:
+            for line in f:
+                if line.startswith("traffic_per_algorithmic_byte:"):
+                    return float(line.split(":", 1)[1])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 # ------------------------------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -259,6 +276,8 @@ def run_ours(args):
         hbm, kind = peaks()
         sweep_ms, sweep_n = prof["sweep"]
         achieved = work["sweep_bytes"] / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+        ratio = traffic_ratio()
+        traffic = ratio * work["sweep_bytes"] / max(sweep_n, 1) if ratio else None
         shares = {k: v[0] for k, v in prof.items()}
         tot = sum(shares.values()) or 1.0
         line = {
@@ -275,11 +294,13 @@ def run_ours(args):
             "kernel_evals_per_s": work["kernel_evals"] / (ms / 1e3),
             "sweeps": {"fp32_instance_sweeps": sweeps32, "fp64_instance_sweeps": sweeps64},
             "e2e": e2e, "gpu_launches": launches, "accuracy": acc,
-            "roofline": {"kernel": "k_tick (batched sweep rows)", "bound": "hbm",
+            "roofline": {"kernel": "k_tick_ring (batched FP32 sweep)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                         "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                         "traffic_unit": "bytes per launch (ncu ratio x algorithmic bytes)",
                          "peak_kind": kind, "launches": sweep_n,
-                         "avg_launch_ms": sweep_ms / max(sweep_n, 1)},
+                         "avg_launch_ms": sweep_ms / max(sweep_n, 1),
+                         "alg_bytes_per_launch": work["sweep_bytes"] / max(sweep_n, 1)},
             "device_time_share": {k: v / tot for k, v in shares.items()},
             "clocks": clk.summary(),
         }
