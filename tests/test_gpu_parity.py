@@ -99,6 +99,32 @@ def test_fp32_sweeps_track_oracle():
     assert rel(host(A), Ao) < 2e-5 and rel(host(B), Bo) < 2e-5
 
 
+RAGGED32 = [inputs.Instance(37, 16, 0.93, 0.5, 0.005), inputs.Instance(64, 32, 0.7, 0.45, 0.05),
+            inputs.Instance(130, 24, 1.1, 0.6, 0.1), inputs.Instance(300, 32, 0.6, 0.4, 0.0)]
+
+
+@pytest.mark.parametrize("kind", ["ring", "groups"])
+def test_fp32_sweep_kernels_track_oracle_on_ragged_batch(kind, monkeypatch):
+    """Both FP32 sweep kernels (the shared-memory ring, the default, and the register-only row
+    groups) on one ragged batch: last groups of 1, 2 and 4 rows, bands from a few columns to a
+    few hundred (tiles split at 128 columns), three sweeps each against the oracle's FP64 sweeps."""
+    if kind == "groups":
+        monkeypatch.setenv("QDSE_SWEEP", "groups")
+    else:
+        monkeypatch.delenv("QDSE_SWEEP", raising=False)
+    ctx = Q.Context([grid(i) for i in RAGGED32], precision=Q.QDSE_FP32)
+    x_off = ctx.layout()
+    A = dev(np.ones(ctx.n_total)); B = dev(np.full(ctx.n_total, 0.3))
+    ctx.qdse_iterate([[i.D, i.omega, i.m, 0.0] for i in RAGGED32], A, B, 3)
+    Ah, Bh = host(A), host(B)
+    for b, inst in enumerate(RAGGED32):
+        Ao, Bo = np.ones(inst.n_p), np.full(inst.n_p, 0.3)
+        for _ in range(3):
+            Ao, Bo = O.sweep(problem(inst), Ao, Bo)
+        sl = slice(x_off[b], x_off[b + 1])
+        assert rel(Ah[sl], Ao) < 2e-5 and rel(Bh[sl], Bo) < 2e-5, (kind, b)
+
+
 def test_jvp_matches_complex_step_jacobian():
     inst = TINY
     rng = np.random.default_rng(9)
