@@ -366,14 +366,26 @@ __device__ __forceinline__ float4 ld4(const float* p) {
 }
 
 // One (i, j) pair of the FP32 BC sweep (T^A_ij, T^B_ij of the header comment).
-__device__ __forceinline__ void pair32(float a, float b, float u1, float u2, float u3, float K0,
-                                       float KT, float K3, float Ai, float Bi, float Pi,
-                                       float& sA, float& sB) {
+// h1 = 3/2 u1, h2 = 1/2 u2, h3 = 1/2 u3 are column factors, formed once per column by the caller.
+__device__ __forceinline__ void pair32(float a, float b, float u1, float u2, float h1, float h2,
+                                       float h3, float K0, float KT, float K3, float Ai, float Bi,
+                                       float Pi, float& sA, float& sB) {
     const float da = a - Ai, db = b - Bi, sa = Ai + a;
-    const float cT = fmaf(-u1, db, -0.5f * fmaf(Pi, u2, u3) * da);
-    sA = fmaf(cT, KT, fmaf(0.5f * u2 * sa, K3, sA));
-    sB = fmaf(fmaf(u1, da, -u2 * db), KT, fmaf(1.5f * u1 * sa, K0, sB));
+    const float T = fmaf(Pi, h2, h3);                // (P_i u2 + u3) / 2
+    const float cT = fmaf(-T, da, -u1 * db);
+    sA = fmaf(cT, KT, fmaf(h2 * sa, K3, sA));
+    sB = fmaf(fmaf(u1, da, -u2 * db), KT, fmaf(h1 * sa, K0, sB));
 }
+
+// The column factors of a lane's 4 columns.
+struct Cols4 {
+    float4 h1, h2, h3;
+    __device__ Cols4(const float4& u1, const float4& u2, const float4& u3) {
+        h1 = make_float4(1.5f * u1.x, 1.5f * u1.y, 1.5f * u1.z, 1.5f * u1.w);
+        h2 = make_float4(0.5f * u2.x, 0.5f * u2.y, 0.5f * u2.z, 0.5f * u2.w);
+        h3 = make_float4(0.5f * u3.x, 0.5f * u3.y, 0.5f * u3.z, 0.5f * u3.w);
+    }
+};
 
 // Its tangent in direction (ea, eb, e1, e2, e3 at q_j; dAi, dBi at p_i).
 __device__ __forceinline__ void tpair32(float a, float b, float u1, float u2, float u3, float ea,
@@ -431,6 +443,7 @@ __device__ __forceinline__ void rows32_chunk(Rows32& R, const KLoad& K, int nr, 
                                              const float4& u3, const float4& ea,
                                              const float4& eb, const float4& e1,
                                              const float4& e2, const float4& e3) {
+    const Cols4 H(u1, u2, u3);
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         if (r < nr) {
@@ -438,10 +451,10 @@ __device__ __forceinline__ void rows32_chunk(Rows32& R, const KLoad& K, int nr, 
             if (bc) {
                 const float4 KT = K(r, 1);
                 if (!TAN) {
-                    pair32(a.x, b.x, u1.x, u2.x, u3.x, K0.x, KT.x, K3.x, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
-                    pair32(a.y, b.y, u1.y, u2.y, u3.y, K0.y, KT.y, K3.y, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
-                    pair32(a.z, b.z, u1.z, u2.z, u3.z, K0.z, KT.z, K3.z, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
-                    pair32(a.w, b.w, u1.w, u2.w, u3.w, K0.w, KT.w, K3.w, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.x, b.x, u1.x, u2.x, H.h1.x, H.h2.x, H.h3.x, K0.x, KT.x, K3.x, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.y, b.y, u1.y, u2.y, H.h1.y, H.h2.y, H.h3.y, K0.y, KT.y, K3.y, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.z, b.z, u1.z, u2.z, H.h1.z, H.h2.z, H.h3.z, K0.z, KT.z, K3.z, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
+                    pair32(a.w, b.w, u1.w, u2.w, H.h1.w, H.h2.w, H.h3.w, K0.w, KT.w, K3.w, R.Ai[r], R.Bi[r], R.Pi[r], R.sA[r], R.sB[r]);
                 } else {
                     tpair32(a.x, b.x, u1.x, u2.x, u3.x, ea.x, eb.x, e1.x, e2.x, e3.x, K0.x, KT.x, K3.x, R.Ai[r], R.Bi[r], R.dAi[r], R.dBi[r], R.Pi[r], R.sA[r], R.sB[r]);
                     tpair32(a.y, b.y, u1.y, u2.y, u3.y, ea.y, eb.y, e1.y, e2.y, e3.y, K0.y, KT.y, K3.y, R.Ai[r], R.Bi[r], R.dAi[r], R.dBi[r], R.Pi[r], R.sA[r], R.sB[r]);
@@ -1134,6 +1147,58 @@ __device__ __forceinline__ void cp_wait(int n) {
     else asm volatile("cp.async.wait_group 2;" ::: "memory");
 }
 
+// A narrow tile (at most 32 * 4 / SPLIT columns, typically the last of a band) of a full group's
+// BC Picard sweep: the warp's lanes split the group's rows instead of leaving 32 - 32 / SPLIT lanes
+// idle.  Lane l takes the 4-column block l % (32 / SPLIT) for rows (l / (32 / SPLIT)) * (4 /
+// SPLIT) and on; its sums go back to those rows' accumulators by selects, so the warp totals at
+// the end of the group are formed as for full tiles.
+__device__ __forceinline__ float pick_row(const float* v, int r) {
+    float x = v[0];
+#pragma unroll
+    for (int k = 1; k < kRows; ++k) x = (r == k) ? v[k] : x;
+    return x;
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void narrow_tile32(Rows32& R, const float* sl, int c, int jhi, int lane) {
+    constexpr int RPL = kRows / SPLIT, NB = 32 / SPLIT;
+    const int rg = lane / NB, cb = lane % NB;
+    const int col = c + 4 * cb;
+    float tA[RPL], tB[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) tA[k] = tB[k] = 0.f;
+    if (col < jhi) {
+        const float* kb = sl + cb * (3 * kRows * 4);
+        const float* vb = sl + kVecOff + cb * 20;
+        auto V4 = [&](int comp) { return *reinterpret_cast<const float4*>(vb + 4 * comp); };
+        const float4 a = V4(0), b = V4(1), u1 = V4(2), u2 = V4(3), u3 = V4(4);
+        const int sw = ((col >> 2) >> 1) & 3;
+        const Cols4 H(u1, u2, u3);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+            const int r = rg * RPL + k;
+            const float Ai = pick_row(R.Ai, r), Bi = pick_row(R.Bi, r), Pi = pick_row(R.Pi, r);
+            auto K = [&](int pl) {
+                return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
+            };
+            const float4 K0 = K(0), KT = K(1), K3 = K(2);
+            pair32(a.x, b.x, u1.x, u2.x, H.h1.x, H.h2.x, H.h3.x, K0.x, KT.x, K3.x, Ai, Bi, Pi, tA[k], tB[k]);
+            pair32(a.y, b.y, u1.y, u2.y, H.h1.y, H.h2.y, H.h3.y, K0.y, KT.y, K3.y, Ai, Bi, Pi, tA[k], tB[k]);
+            pair32(a.z, b.z, u1.z, u2.z, H.h1.z, H.h2.z, H.h3.z, K0.z, KT.z, K3.z, Ai, Bi, Pi, tA[k], tB[k]);
+            pair32(a.w, b.w, u1.w, u2.w, H.h1.w, H.h2.w, H.h3.w, K0.w, KT.w, K3.w, Ai, Bi, Pi, tA[k], tB[k]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+            const bool mine = (rg * RPL + k == r);
+            R.sA[r] += mine ? tA[k] : 0.f;
+            R.sB[r] += mine ? tB[k] : 0.f;
+        }
+    }
+}
+
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     k_tick_ring(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g, Work w,
@@ -1332,7 +1397,12 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
                 break;
             }
             const int col = c + 4 * lane;
-            if (col < jhi) {
+            const int wc = min(kTileCols, jhi - c);  // columns in this tile
+            if (full && wc <= kTileCols / 4) {
+                narrow_tile32<4>(R, ring + slot * kTileFloats, c, jhi, lane);
+            } else if (full && wc <= kTileCols / 2) {
+                narrow_tile32<2>(R, ring + slot * kTileFloats, c, jhi, lane);
+            } else if (col < jhi) {
                 const float* sl = ring + slot * kTileFloats;
                 const float* vb = sl + kVecOff + lane * 20;
                 auto V4 = [&](int comp) { return *reinterpret_cast<const float4*>(vb + 4 * comp); };
