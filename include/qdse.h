@@ -107,7 +107,10 @@ qdse_options qdse_default_options(void);
 /* Create a context for n_inst instances that share one grid (*g).  Builds the radial and angular
  * nodes on the host in FP64, uploads them and allocates the kernel-matrix pool (6 n_p^2 floats
  * per instance) and workspaces on the current device.  *out receives the context (NULL on
- * failure).  Errors: QDSE_ERR_ARG (bad sizes/options), QDSE_ERR_OOM, QDSE_ERR_CUDA. */
+ * failure).  Errors: QDSE_ERR_ARG (bad sizes/options), QDSE_ERR_OOM, QDSE_ERR_CUDA.
+ * The FP32 sweeps of the batched solve use the shared-memory ring kernel; the environment
+ * variable QDSE_SWEEP=groups, read here, selects the register-only kernel instead (the same sums
+ * in another order). */
 qdse_status qdse_create(const qdse_grid* g, int n_inst, const qdse_options* o, qdse_ctx** out);
 
 /* As qdse_create with one grid per instance: g points to n_inst host structs (ragged batch). */

@@ -14,8 +14,13 @@
 //   diag^A_i = (-u1_i dB_i - P_i u2_i dA_i) K_T,ii,   diag^B_i = (u1_i dA_i - u2_i dB_i) K_T,ii.
 // The bare (rainbow) vertex keeps only u2 K3 and 3 u1 K0.
 //
-// A sweep is one warp per external point: lanes stride over j, read the three kernel rows
-// (coalesced) and the per-node vectors, accumulate in registers and reduce by warp shuffles.
+// FP64 sweeps (residuals, FP64 Picard, tangents and the row maps of the C interface) take one
+// warp per external point: lanes stride over j, read the three kernel entries and the per-node
+// vectors, accumulate in registers and reduce by warp shuffles.  The FP32 sweeps of the batched
+// solve take one warp per group of kRows consecutive points: the ring kernel (k_tick_ring, the
+// default) streams a group's kernel block and node vectors through shared memory by bulk copies,
+// the register kernel (k_tick) loads them straight from global memory; lanes own 4-column blocks
+// and the group's row sums are reduced by one butterfly at the end of the group.
 // The vectors (a, b, u1, u2, u3) are formed once per sweep per instance (O(N)) by the update
 // kernel, which also owns the convergence test (Eq. jifenab2, relative form) and the phase
 // transitions of the mixed-precision solve.
@@ -1468,8 +1473,8 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     }
 }
 
-// Advance every instance on the current active list after a tick (persistent blocks; used after
-// the on-the-fly FP64 sweep and the work-list sweep, which do not update instances themselves).
+// Advance every instance on the current active list after a tick's sweep (one block per instance,
+// blocks persistent over the list).
 __global__ void __launch_bounds__(128) k_update(const DevInst* __restrict__ inst, DevState* state,
                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
                                                 double* A, double* B, int ntot, int* count,

@@ -281,7 +281,7 @@ struct qdse_ctx {
     int g_path = -1;
     long long g_launches = 0;  // kernels per replay
     int n_tiles = 0;
-    long long tick = 0;       // sweeps issued since the last init (selects the work-list buffer)
+    long long tick = 0;       // ticks issued since the last init (selects the active-list buffers)
     qdse::DevInst* h_inst_pinned = nullptr;
 
     std::string err;
