@@ -140,6 +140,22 @@ def traffic_ratio():
     return None
 
 
+def job_rate(ms_local, ok_local, steps, world, device):
+    """Whole-job figures over all ranks (weak scaling: every rank solves its own batch): the
+    slowest rank's time, the converged solves summed over ranks, and their rate.  Returns
+    (ms, total_ok, solves_per_s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(ok_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    total = float(n.item())
+    return ms, total, total * steps / (ms / 1e3)
+
+
 # ------------------------------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -203,17 +219,10 @@ def run_ours(args):
         torch.cuda.synchronize()
     ctx.qdse_set_profiling(False)
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
     st = status.cpu().numpy()
     it = iters.cpu().numpy()
     ok = int((st == 0).sum())
-    n_ok = torch.tensor([ok], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(n_ok)
-    solves_per_s = float(n_ok.item()) * args.steps / (ms / 1e3)
+    ms, _, solves_per_s = job_rate(ms, ok, args.steps, world, dev)
 
     # end to end through the host-buffer entry point (copies in the timed region)
     Ah = np.ones(nt)
