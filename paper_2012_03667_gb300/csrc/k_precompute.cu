@@ -54,11 +54,13 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
     double* sz = sy + I.nt;
     double* ss = sz + I.nt;
     double* sw = ss + I.nt;
+    double* sz2 = sw + I.nt;
     for (int k = threadIdx.x; k < I.nt; k += blockDim.x) {
         sy[k] = g.y[I.t_off + k];
         sz[k] = g.z[I.t_off + k];
         ss[k] = g.s2[I.t_off + k];
         sw[k] = g.wz[I.t_off + k];
+        sz2[k] = sz[k] * sz[k];
     }
     __syncthreads();
     const int i0 = t.y * kTile, j0 = t.z * kTile;
@@ -87,23 +89,38 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
             if (dd * iw2 < kSkipExponent) {
                 const double c2 = 2.0 * rP * rQ, x0 = rP * rQ, PQ = P * Q, PpQ = P + Q;
                 const double ex_last = (dd + c2 * sy[0]) * iw2 + kAngularCut;
+                // g_T and g_3 are polynomials in z over k^2 with pair-constant coefficients
+                // (x = sqrt(PQ) z): accumulate F = E/k^2 against 1 - z^2, 1, z, z^2 and form
+                // K_T = 2PQ sum(F (1 - z^2)), K_3 = 3 x0 (P+Q) sum(F z) - 4 x0^2 sum(F z^2)
+                // - 2PQ sum(F) once per pair (likewise for the w-derivatives, G = F f)
+                double Fs = 0.0, F1 = 0.0, Fz = 0.0, Fzz = 0.0;
+                double Gs = 0.0, G1 = 0.0, Gz = 0.0, Gzz = 0.0;
                 for (int k = 0; k < I.nt; ++k) {
                     const double k2 = dd + c2 * sy[k];
-                    if (k2 * iw2 > ex_last) break;
-                    const double E = sw[k] * exp(-k2 * iw2);
-                    const double rk = 1.0 / k2;
-                    const double x = x0 * sz[k];
-                    const double gT = 2.0 * PQ * ss[k] * rk;
-                    const double g3 = (3.0 * x * PpQ - 4.0 * x * x - 2.0 * PQ) * rk;
+                    const double ex = k2 * iw2;
+                    if (ex > ex_last) break;
+                    const double E = sw[k] * exp(-ex);
+                    const double F = E / k2;
                     K0 += E;
-                    KT += E * gT;
-                    K3 += E * g3;
+                    F1 += F;
+                    Fs = fma(F, ss[k], Fs);
+                    Fz = fma(F, sz[k], Fz);
+                    Fzz = fma(F, sz2[k], Fzz);
                     if (WITH_W) {
                         const double f = fw0 + fw1 * k2;
-                        W0 += E * f;
-                        WT += E * f * gT;
-                        W3 += E * f * g3;
+                        const double G = F * f;
+                        W0 = fma(E, f, W0);
+                        G1 += G;
+                        Gs = fma(G, ss[k], Gs);
+                        Gz = fma(G, sz[k], Gz);
+                        Gzz = fma(G, sz2[k], Gzz);
                     }
+                }
+                KT = 2.0 * PQ * Fs;
+                K3 = 3.0 * x0 * PpQ * Fz - 4.0 * x0 * x0 * Fzz - 2.0 * PQ * F1;
+                if (WITH_W) {
+                    WT = 2.0 * PQ * Gs;
+                    W3 = 3.0 * x0 * PpQ * Gz - 4.0 * x0 * x0 * Gzz - 2.0 * PQ * G1;
                 }
                 const double dq = (coll && i == j) ? 1.0 : 1.0 / (Q - P);
                 K0 *= pref;
@@ -219,7 +236,7 @@ cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
                                     c->stream);
     if (e != cudaSuccess) return e;
     const size_t smem =
-        ((with_w ? 2 : 1) * 3 * kTile * (kTile + 1) + 4 * (size_t)c->max_nt) * sizeof(double);
+        ((with_w ? 2 : 1) * 3 * kTile * (kTile + 1) + 5 * (size_t)c->max_nt) * sizeof(double);
     prof_begin(c, PK_PRECOMPUTE);
     if (with_w) {
         k_precompute_tiles<true><<<c->n_tiles, 256, smem, c->stream>>>(
@@ -240,7 +257,7 @@ cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
 }
 
 cudaError_t configure_precompute(int max_nt) {
-    const size_t smem = (2 * 3 * kTile * (kTile + 1) + 4 * (size_t)max_nt) * sizeof(double);
+    const size_t smem = (2 * 3 * kTile * (kTile + 1) + 5 * (size_t)max_nt) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_precompute_tiles<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
