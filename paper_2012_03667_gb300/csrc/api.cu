@@ -184,6 +184,7 @@ Ctl make_ctl(const qdse_ctx* c) {
     t.precision = c->opt.precision;
     t.final_phase = (c->opt.precision == QDSE_FP32) ? PH_PICARD32 : PH_PICARD64;
     t.never_converge = 0;
+    t.stall_copies = c->stall_copies;
     return t;
 }
 
@@ -570,6 +571,9 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         cudaGetLastError();
         c->sweep_kind = ring_ok ? 1 : 0;
         if (k && std::string(k) == "groups") c->sweep_kind = 0;
+        // test of the sweep's bounded waits (tests only): every tile wait runs out
+        const char* st = std::getenv("QDSE_TEST_STALL");
+        c->stall_copies = (st && std::string(st) == "1") ? 1 : 0;
     }
     // zero the padding of the node vectors once; descriptors get their layout now and their
     // parameters on every call
@@ -717,11 +721,15 @@ qdse_status qdse_solve(qdse_ctx* c, const qdse_params* p, double* A, double* B, 
     QCHECK(c, launch_init_state(c, ctl, A, B, phase0), "init");
     bool timed_out = false;
     s = run_ticks(c, A, B, -1, timed_out);
-    if (s != QDSE_OK) return s;
+    if (s != QDSE_OK && !timed_out) return s;
     if (timed_out) {
+        // a bounded device wait ran out (s) or the host time limit was reached
+        const std::string why = (s == QDSE_ERR_TIMEOUT)
+                                    ? c->err
+                                    : std::string("time limit reached before every instance finished");
         QCHECK(c, launch_finish_timeout(c, A, B, nullptr, iters, inst_status), "finish");
         QCHECK(c, cudaStreamSynchronize(c->stream), "sync");
-        return fail(c, QDSE_ERR_TIMEOUT, "time limit reached before every instance finished");
+        return fail(c, QDSE_ERR_TIMEOUT, why);
     }
     QCHECK(c, launch_finish(c, A, B, nullptr, iters, inst_status), "finish");
     QCHECK(c, cudaStreamSynchronize(c->stream), "sync");

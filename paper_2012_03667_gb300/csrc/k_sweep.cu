@@ -1242,7 +1242,10 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         return c < cnt ? c * G : -1;
     };
     int nmine = 1 << 30;  // groups this warp claimed: known once a claim fails
+    // a bounded wait of an earlier launch of this solve ran out: leave the state as it is
+    if (*reinterpret_cast<volatile const int*>(err)) return;
     const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
+    const int stall = ctl->stall_copies ? 16 : 0;
     const uint64_t pol = lane == 0 ? evict_first_policy() : evict_last_policy();
 
     // prologue: claim groups 0 .. 3 and fetch their list ids, then the descriptors and phases of
@@ -1341,7 +1344,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (lane == 0)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                         "r"((uint32_t)(cols * (3 * pnr + 5) * 4))
+                         "r"((uint32_t)(cols * (3 * pnr + 5) * 4 + stall))
                          : "memory");
         __syncwarp();
         if (lane < 2) {
@@ -1478,7 +1481,10 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
 __global__ void __launch_bounds__(128) k_update(const DevInst* __restrict__ inst, DevState* state,
                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
                                                 double* A, double* B, int ntot, int* count,
-                                                unsigned long long* ctr, int list) {
+                                                unsigned long long* ctr, int list,
+                                                const int* err) {
+    // a bounded wait of this tick's sweep ran out: its outputs are incomplete, the solve stops
+    if (*reinterpret_cast<volatile const int*>(err)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int clr = (list + 2) % 3;  // lists of two ticks ahead start empty
         w.lcount[clr] = 0;
@@ -1664,7 +1670,7 @@ cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
     const int blocks = std::min(c->n_inst, 16 * (c->n_sms > 0 ? c->n_sms : 152));
     k_update<<<blocks, 128, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid, c->work,
                                             A, B, c->n_total, c->d_count, c->d_sweeps,
-                                            (int)(c->tick % 3));
+                                            (int)(c->tick % 3), c->d_err);
     c->tick++;
     c->launches++;
     prof_end(c);

@@ -83,6 +83,8 @@ struct Ctl {              // solver controls shared by every instance of a call
     int precision;
     int final_phase;      // PH_PICARD64 for FP64 modes, PH_PICARD32 for FP32-only
     int never_converge;   // 1 for qdse_iterate (run exactly max_iter sweeps)
+    int stall_copies;     // test of the bounded waits: the ring sweep expects 16 bytes more than
+                          // it copies per tile, so each tile wait runs out (QDSE_TEST_STALL=1)
 };
 
 // Work arrays (device).  Component counts in brackets, each of length n_total.
@@ -288,6 +290,7 @@ struct qdse_ctx {
     long long launches = 0, sweeps32 = 0, sweeps64 = 0, polls = 0;
     // optional CUDA-event timing of every launch, by kind (see qdse::ProfKind)
     int profiling = 0;
+    int stall_copies = 0;     // QDSE_TEST_STALL=1 at creation (see Ctl::stall_copies)
     struct ProfRec { int kind; cudaEvent_t a, b; };
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;

@@ -349,6 +349,32 @@ def test_status_not_converged_nonfinite_and_timeout():
     assert int(st.item()) == Q.QDSE_ERR_TIMEOUT
 
 
+def test_bounded_sweep_wait_runs_out_and_reports_timeout(monkeypatch):
+    """The sweep's waits are bounded: with the test switch QDSE_TEST_STALL=1 every tile expects
+    16 bytes more than its copies deliver, so each wait runs out after its clock budget (about a
+    second).  The kernel flags it and returns, later launches of the solve stop at once, the call
+    returns QDSE_ERR_TIMEOUT with per-instance TIMEOUT status, and the GPU stays usable: a fresh
+    context then solves normally."""
+    monkeypatch.delenv("QDSE_SWEEP", raising=False)
+    monkeypatch.setenv("QDSE_TEST_STALL", "1")
+    inst = PAPER
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(Q.QdseError) as e:
+        ctx.qdse_solve(prm(inst), A, B, None, st)
+    assert e.value.status == Q.QDSE_ERR_TIMEOUT
+    assert int(st.item()) == Q.QDSE_ERR_TIMEOUT
+    ctx.close()
+    monkeypatch.delenv("QDSE_TEST_STALL")
+    ctx2 = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED, tol=1e-13, max_iter=40000)
+    A = dev(np.ones(inst.n_p)); B = dev(np.full(inst.n_p, 0.3))
+    ctx2.qdse_solve(prm(inst), A, B, None, st)
+    assert int(st.item()) == Q.QDSE_OK
+    Ar, Br, _ = oracle_fixed_point(inst)
+    assert rel(host(A), Ar) < 1e-8 and rel(host(B), Br) < 1e-8
+
+
 def test_bad_parameters_rejected():
     ctx = Q.Context(grid(SMALL), 1)
     A = dev(np.ones(SMALL.n_p)); B = dev(np.full(SMALL.n_p, 0.3))
