@@ -1,0 +1,179 @@
+"""Pins of the finite-mu FP64 oracle (``oracle/qdse_oracle_mu.cpp``) against what the mathematics
+fixes (no GPU needed).
+
+The paper announces the finite chemical potential extension (Sec. V) without its equations; the
+oracle takes readings M1-M5 (its header).  These tests pin it to things other than itself:
+  * the Dirac algebra of its gamma matrices;
+  * the Ward-Takahashi identity that defines the Ball-Chiu construction (M3), at complex momenta;
+  * the chiral limit (B stays exactly zero) and the p_4 -> -p_4 conjugation symmetry;
+  * the mu = 0 limit against the vacuum oracle, which is pinned on its own;
+  * the contour-shift invariance at mu > 0: with inputs analytic in q~^2 and no propagator pole
+    between Im q_4 = 0 and mu, the q_4 integral can be moved back to the real axis, so A, C, B
+    depend on (|p_vec|, p_4, mu) only through p~^2 = p_vec^2 + (p_4 + i mu)^2, and C = A.
+A slip in the mu terms (projecting C on p_4 instead of p~_4, dropping i mu from the vertex, the
+wrong sign of mu) breaks the last one by at least 0.2, against a quadrature spread of 4e-4.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import oracle_mu as OM
+
+D, OMEGA, M = 0.93, 0.5, 0.005
+
+
+def _gl(n):
+    return np.polynomial.legendre.leggauss(n)
+
+
+def _grid(nr, n4, a=0.5, R=60.0):
+    """Internal points (|q_vec|, q_4) on a sinh-mapped Gauss-Legendre product rule covering
+    |q_vec| in [0, R] and q_4 in [-R, R]; weights include |q_vec|^2 d|q_vec| dq_4.  The q_4 nodes
+    are symmetric about 0."""
+    U = np.arcsinh(R / a)
+    t, w = _gl(nr)
+    ur, wr = 0.5 * U * (t + 1), 0.5 * U * w
+    qr = a * np.sinh(ur)
+    jr = a * np.cosh(ur) * wr * qr ** 2
+    t, w = _gl(n4)
+    q4 = a * np.sinh(U * t)
+    j4 = a * np.cosh(U * t) * U * w
+    QR, Q4 = np.meshgrid(qr, q4, indexing="ij")
+    WR, W4 = np.meshgrid(jr, j4, indexing="ij")
+    return QR.ravel(), Q4.ravel(), (WR * W4).ravel()
+
+
+def _af(s):
+    return 1 + 0.6 / (1 + s / 0.5)
+
+
+def _bf(s):
+    return 0.5 / (1 + s / 0.8) + M
+
+
+def _inputs(qv, q4, mu):
+    s = qv ** 2 + (q4 + 1j * mu) ** 2
+    return _af(s), _af(s), _bf(s)
+
+
+def _rand_momenta(rng, mu):
+    q, p = rng.normal(size=3), rng.normal(size=3)
+    return q, complex(rng.normal(), mu), p, complex(rng.normal(), mu)
+
+
+# --------------------------------------------------------------------------------------------
+def test_gamma_matrices_are_hermitian_and_satisfy_the_clifford_algebra():
+    rng = np.random.default_rng(1)
+    q, q4, p, p4 = _rand_momenta(rng, 0.3)
+    g, _, _ = OM.vertex(q, q4, p, p4, (1, 1, 0.3), (1, 1, 0.3), vertex=OM.RL)
+    for a in range(4):
+        np.testing.assert_allclose(g[a], g[a].conj().T, atol=0)
+        for b in range(4):
+            np.testing.assert_allclose(g[a] @ g[b] + g[b] @ g[a], 2.0 * (a == b) * np.eye(4),
+                                       atol=1e-15)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.25, 0.6])
+def test_bc_vertex_satisfies_the_ward_takahashi_identity_at_complex_momenta(mu):
+    """M3: i (q~ - p~)_nu Gamma_nu = S^-1(q~) - S^-1(p~), with complex A, C, B, C != A."""
+    rng = np.random.default_rng(int(10 * mu) + 2)
+    for _ in range(5):
+        q, q4, p, p4 = _rand_momenta(rng, mu)
+        fq = rng.normal(size=3) + 1j * rng.normal(size=3)
+        fp = rng.normal(size=3) + 1j * rng.normal(size=3)
+        g, sq, sp = OM.vertex(q, q4, p, p4, fq, fp)
+        d = np.array([q[0] - p[0], q[1] - p[1], q[2] - p[2], q4 - p4])
+        lhs = 1j * np.einsum("n,nab->ab", d, g)
+        np.testing.assert_allclose(lhs, sq - sp, rtol=0, atol=1e-12 * np.abs(sq - sp).max())
+        # the projections of M4 give back A, C, B from S^-1 of M1
+        G = OM.vertex(q, q4, p, p4, fq, fp, vertex=OM.RL)[0]
+        gq = np.einsum("k,kab->ab", q, G[:3])
+        assert abs(np.trace(gq @ sq) / (4j * (q @ q)) - fq[0]) < 1e-13
+        assert abs(np.trace(G[3] @ sq) / (4j * q4) - fq[1]) < 1e-13
+        assert abs(np.trace(sq) / 4 - fq[2]) < 1e-13
+
+
+def test_chiral_limit_keeps_B_exactly_zero():
+    """m = 0 and B = 0 at every point: tr of an odd number of gamma matrices vanishes, so B stays 0
+    (chiral symmetry) while A and C do not."""
+    qv, q4, wq = _grid(16, 32)
+    z, wz = _gl(12)
+    mu = 0.2
+    pv, p4 = np.array([0.3, 1.1]), np.array([0.2, -0.7])
+    Aq, Cq, _ = _inputs(qv, q4, mu)
+    Ap, Cp, _ = _inputs(pv, p4, mu)
+    A, C, B = OM.sweep(pv, p4, qv, q4, wq, z, wz, D, OMEGA, 0.0, mu, Ap, Cp, 0 * Ap, Aq, Cq, 0 * Aq)
+    assert np.all(np.abs(B) < 1e-15)
+    assert np.all(np.abs(A - 1) > 1e-2) and np.all(np.abs(C - 1) > 1e-2)
+
+
+@pytest.mark.parametrize("vertex", [OM.BC, OM.RL])
+def test_reflecting_p4_conjugates_the_result(vertex):
+    """With inputs F(q~^2) real-analytic and a q_4 rule symmetric about 0, p_4 -> -p_4 maps p~^2
+    to its conjugate and the sweep output to its conjugate (to rounding)."""
+    qv, q4, wq = _grid(16, 32)
+    z, wz = _gl(12)
+    mu = 0.3
+    pv = np.array([0.4, 0.4, 1.3, 1.3])
+    p4 = np.array([0.5, -0.5, 0.9, -0.9])
+    Aq, Cq, Bq = _inputs(qv, q4, mu)
+    Ap, Cp, Bp = _inputs(pv, p4, mu)
+    out = OM.sweep(pv, p4, qv, q4, wq, z, wz, D, OMEGA, M, mu, Ap, Cp, Bp, Aq, Cq, Bq,
+                   vertex=vertex)
+    for F in out:
+        assert np.abs(F.imag[0::2]).min() > 1e-4  # mu > 0 really makes the result complex
+        np.testing.assert_allclose(F[1::2], F[0::2].conj(), rtol=1e-12, atol=0)
+
+
+def test_mu_zero_reduces_to_the_vacuum_oracle():
+    """At mu = 0 with C = A, real inputs: A = C and B agree with the vacuum sweep of the pinned
+    vacuum oracle at its collocation nodes p^2 ~ 0.1 and 1 (point put off the 4-axis at angle 0.3),
+    to the two quadratures' difference (below 2e-4 relative to A - 1 and B - m here)."""
+    pr = O.Problem(n=128, n_theta=64, D=D, omega=OMEGA, m=M)
+    sp, sq, _, _ = O.radial_grid(128)
+    FA, FB = O.sweep(pr, _af(sq), _bf(sq), nthreads=O.max_threads())
+    idx = [int(np.argmin(abs(sp - P))) for P in (0.1, 1.0)]
+    P = sp[idx]
+    pv, p4 = np.sqrt(P) * np.cos(0.3), np.sqrt(P) * np.sin(0.3)
+    qv, q4, wq = _grid(48, 96)
+    z, wz = _gl(24)
+    Aq, Cq, Bq = _inputs(qv, q4, 0.0)
+    A, C, B = OM.sweep(pv, p4, qv, q4, wq, z, wz, D, OMEGA, M, 0.0, _af(P), _af(P), _bf(P),
+                       Aq, Cq, Bq, nthreads=O.max_threads())
+    for F in (A, C, B):
+        assert np.abs(F.imag).max() < 1e-14
+    tol = 2e-3
+    assert np.all(np.abs(A.real - FA[idx]) < tol * np.abs(FA[idx] - 1))
+    assert np.all(np.abs(C.real - FA[idx]) < tol * np.abs(FA[idx] - 1))
+    assert np.all(np.abs(B.real - FB[idx]) < tol * np.abs(FB[idx] - M))
+
+
+@pytest.mark.parametrize("vertex", [OM.BC, OM.RL])
+def test_result_depends_on_mu_only_through_p_tilde_squared(vertex):
+    """Contour shift: three points (|p_vec|, p_4, mu) with mu = 0.05, 0.1, 0.2 and the same
+    p~^2 = 0.73 + 0.04 i give the same A, C, B, and C = A.  The inputs' propagator pole sits at
+    q~^2 = -0.109 (mass 0.33 > mu) and their own poles at q~^2 = -0.5 and -0.8, so the shift crosses
+    none.  The spread is quadrature error: 2.3e-3, 3.4e-4, 1.1e-4 at 16, 24, 32 cosine nodes."""
+    s = np.linspace(-0.49, -1e-6, 4000)
+    disc = s * _af(s) ** 2 + _bf(s) ** 2
+    s_pole = s[np.argmin(np.abs(disc))]
+    assert -0.12 < s_pole < -0.10
+    qv, q4, wq = _grid(48, 96)
+    z, wz = _gl(24)
+    c, d = 0.04, 0.73  # 2 p_4 mu = c, |p_vec|^2 + p_4^2 - mu^2 = d
+    res = []
+    for mu in (0.05, 0.1, 0.2):
+        assert mu ** 2 < -s_pole
+        p4 = c / (2 * mu)
+        pv = np.sqrt(d - p4 ** 2 + mu ** 2)
+        Ap, Cp, Bp = _inputs(np.array([pv]), np.array([p4]), mu)
+        Aq, Cq, Bq = _inputs(qv, q4, mu)
+        A, C, B = OM.sweep([pv], [p4], qv, q4, wq, z, wz, D, OMEGA, M, mu, Ap, Cp, Bp, Aq, Cq, Bq,
+                           vertex=vertex, nthreads=O.max_threads())
+        res.append((A[0], C[0], B[0]))
+    res = np.array(res)
+    assert abs(res[0, 0].imag) > 5e-3  # genuinely complex
+    tol = 1e-3
+    assert np.abs(res[:, 0] - res[0, 0]).max() < tol
+    assert np.abs(res[:, 1] - res[:, 0]).max() < tol
+    assert np.abs(res[:, 2] - res[0, 2]).max() < tol
