@@ -35,7 +35,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scan", choices=["scan", "large", "small", "adjoint"],
+    ap.add_argument("--workload", default="scan",
+                    choices=["scan", "large", "small", "adjoint", "mu", "mu-small"],
                     help="adjoint: 1024 scan instances at N_q = 256, N_theta = 64; one step = "
                          "forward solve + condensate gradient w.r.t. (m, D, w, mu) by the adjoint")
     ap.add_argument("--n-inst", type=int, default=4096)
@@ -449,11 +450,127 @@ def run_adjoint(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------------------------------------
+# Finite chemical potential: FP32 operations of one (pair, mu) evaluation of the Ball-Chiu sweep
+# (csrc/mu_pair.cuh: 118 additions + 159 multiplications + 1 reciprocal in mu_pair_add) and of one
+# pair's real combinations, shared by a tile of 8 chemical potentials (12 + 24 + 1 in
+# mu_pair_real), counted by instantiating the templates with an operation-counting scalar.
+MU_FLOPS_PAIR_MU = 278
+MU_FLOPS_PAIR = 37
+MU_TILE = 8
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_mu(args):
+    """One step = one batched FP32 sweep of the finite-mu gap equation (Ball-Chiu vertex) for all
+    chemical potentials: propagator prep + sweep over the precomputed angular-moment table.  The
+    table precompute (once per omega and grid) is timed separately.  Single GPU; other ranks
+    idle."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_03667_gb300 import inputs
+    from paper_2012_03667_gb300 import qdse_mu as QM
+    if args.workload == "mu":
+        w = inputs.mu_workload()
+        name = ("finite mu: 256 mu ~ U[0, 0.4] GeV, |p| 128 x p4 128 external (staggered), "
+                "|q| 128 x q4 256 internal, log-mapped GL on [1e-2, 1e2] GeV, 64 GL angles, "
+                "D = 0.93, omega = 0.5, m = 0.005, BC vertex, FP32 sweep")
+    else:
+        w = inputs.mu_workload(n_r=64, n_4=48, n_z=64, n_mu=32)
+        name = "finite mu (small): 32 mu, |p| 64 x p4 48, |q| 64 x q4 96, 64 angles, FP32 sweep"
+    QR, Q4 = np.meshgrid(w.q_abs, w.q4, indexing="ij")
+    qv, q4 = QR.ravel(), Q4.ravel()
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, 3)
+    t_pre = time.perf_counter() - t0
+    info = g.info()
+    n_mu = len(w.mu)
+    Fe_h = np.stack([inputs.mu_iterate(w.p_abs, w.p4, mu, w.m) for mu in w.mu])
+    Fi_h = np.stack([inputs.mu_iterate(qv, q4, mu, w.m) for mu in w.mu])
+    Fe = torch.from_numpy(Fe_h).to(dev)
+    Fi = torch.from_numpy(Fi_h).to(dev)
+    out = torch.empty_like(Fe)
+    mu = list(w.mu)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.sweep(mu, w.D, w.m, Fe, Fi, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.profile()
+    g.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = g.profile()
+    g.set_profiling(False)
+    ok = bool(torch.isfinite(torch.view_as_real(out)).all().item())
+    # end to end through the same call: pinned host inputs in, the result out, every step
+    Fe_p = torch.from_numpy(Fe_h).pin_memory()
+    Fi_p = torch.from_numpy(Fi_h).pin_memory()
+    out_p = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        Fe.copy_(Fe_p, non_blocking=True)
+        Fi.copy_(Fi_p, non_blocking=True)
+        step()
+        out_p.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if rank != 0:
+        return
+    evals = info["n_pairs"] * n_mu
+    sweep_ms = prof["sweep"]["ms"] / max(prof["sweep"]["launches"], 1)
+    flops = evals * MU_FLOPS_PAIR_MU + info["n_pairs"] * -(-n_mu // MU_TILE) * MU_FLOPS_PAIR
+    achieved = flops / (sweep_ms / 1e3) / 1e12
+    line = {"metric": "finite-mu sweep: (pair, mu) evaluations per second",
+            "value": evals * args.steps / (ms / 1e3), "unit": "pair-mu evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": name, "n_mu": n_mu, "n_ext": len(w.p_abs),
+                       "n_int": len(qv), "pairs_kept": info["n_pairs"],
+                       "table_bytes": info["table_bytes"],
+                       "l2": "inputs larger than L2: the moment table is re-read each step"},
+            "precompute_s": t_pre,
+            "kernel_ms": {"prep": prof["prep"]["ms"] / max(prof["prep"]["launches"], 1),
+                          "sweep": sweep_ms},
+            "roofline": {"bound": "alu", "kernel": "k_mu_sweep<float, 8>",
+                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "flops_per_launch": flops,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "e2e": {"value": evals * args.steps / (ms_e2e / 1e3), "unit": "pair-mu evals/s",
+                    "h2d_bytes_per_step": Fe_h.nbytes + Fi_h.nbytes,
+                    "d2h_bytes_per_step": out_p.numel() * out_p.element_size()},
+            "gpu_launches": 2 * args.steps, "outputs_finite": ok, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "adjoint":
         run_adjoint(a)
+    elif a.workload.startswith("mu"):
+        run_mu(a)
     else:
         run_ours(a)

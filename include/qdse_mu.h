@@ -1,0 +1,91 @@
+/*
+ * qdse_mu.h -- C interface of libqdse for one sweep of the quark gap equation at finite quark
+ * chemical potential mu, batched over many mu (Huang, Duan, Hu, Chen, arXiv:2012.03667, the
+ * extension announced in Sec. V; the paper gives no equations for it).
+ *
+ * Equation solved (readings taken where the paper is silent):
+ *   S^-1(p~) = i g_vec.p_vec A + i g_4 p~_4 C + B,  p~ = (p_vec, p_4 + i mu),  A, C, B complex
+ *   functions of (|p_vec|, p_4);
+ *   the gap equation of Sec. II (Eq. gendse) with p -> p~ in the propagator and the vertex, the
+ *   gluon momentum k = p - q real, the interaction 8 pi^2 D/w^4 exp(-k^2/w^2) times the Landau
+ *   projector (Eqs. KernelAnsatz, IRGsQC), colour factor cf;
+ *   the Ball-Chiu vertex built from the Ward-Takahashi identity for this S^-1,
+ *     Gamma_nu = Sigma_nu g_nu + t_nu (g_vec.t_vec dA/2 + g_4 t_4 dC/2 - i dB),  t = q~ + p~,
+ *     Sigma_nu = (A_q + A_p)/2 for nu = 1..3, (C_q + C_p)/2 for nu = 4,
+ *     dF = (F_q - F_p)/(q~^2 - p~^2)   (at mu = 0 with C = A: Eq. bcvtxmu with Eq. 2),
+ *   or the bare vertex g_nu (QDSE_VERTEX_RL);
+ *   projections A = tr[g_vec.p_vec S^-1]/(4 i p_vec^2), C = tr[g_4 S^-1]/(4 i p~_4),
+ *   B = tr[S^-1]/4;  measure d^4q/(2 pi)^4 = 2 pi/(2 pi)^4 dq_4 |q_vec|^2 d|q_vec| dz.
+ * One sweep maps the values at the external points and at the internal (quadrature) points to new
+ * values at the external points.
+ *
+ * Conventions: as in qdse.h (GeV units; "device" pointers are device memory of the current CUDA
+ * device, "host" pointers ordinary host memory; the caller owns every array passed in; work is
+ * enqueued on the given stream, NULL = legacy default stream; the return value reports argument
+ * and CUDA errors, qdse_mu_last_error() describes the last one; a grid is not thread-safe).
+ * Complex arrays are interleaved (re, im) doubles, the layout of C99 double complex and of a
+ * torch.complex128 tensor.
+ */
+#ifndef QDSE_MU_H
+#define QDSE_MU_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qdse_mu_grid qdse_mu_grid; /* opaque: angular-moment table and workspaces */
+
+/* Builds the grid and its angular-moment table on the device (enqueued on stream).
+ * External points: n_ext pairs (p_abs[e] > 0, p4[e]), host double[n_ext] each.
+ * Internal points: the product of n_r radial nodes q_abs (host double[n_r], > 0, strictly
+ * increasing) and n_4 fourth components q4 (host double[n_4], strictly increasing); internal point
+ * j = r * n_4 + f has |q_vec| = q_abs[r], q_4 = q4[f] and weight w_q[j] (host double[n_r * n_4]),
+ * which must include |q_vec|^2 d|q_vec| dq_4.  Angular rule: n_z nodes z (host double[n_z], in
+ * (-1, 1)) with weights w_z.  omega > 0: the interaction width (the table depends on it, on the
+ * points and on the rule, not on D, m, mu or the colour factor).
+ * precision: QDSE_FP64 (0) or QDSE_FP32 (3) -- the arithmetic of the sweeps; the moments are
+ * always formed in FP64.
+ * Pairs whose Gaussian exp(-((|p|-|q|)^2 + (p_4-q_4)^2)/omega^2) is below exp(-70) at every angle
+ * are left out (a relative effect below 1e-30).
+ * Returns QDSE_OK, QDSE_ERR_ARG (sizes < 1, non-finite or unordered nodes, omega <= 0,
+ * precision), QDSE_ERR_OOM or QDSE_ERR_CUDA; *out is NULL unless QDSE_OK. */
+int qdse_mu_grid_create(int n_ext, const double* p_abs, const double* p4, int n_r,
+                        const double* q_abs, int n_4, const double* q4, const double* w_q, int n_z,
+                        const double* z, const double* w_z, double omega, int precision,
+                        void* stream, qdse_mu_grid** out);
+
+/* Sizes: the pairs kept in the table and its device bytes (either pointer may be NULL). */
+int qdse_mu_grid_info(const qdse_mu_grid* g, long long* n_pairs, long long* table_bytes);
+
+/* One sweep for n_mu chemical potentials at once.
+ * mu: host double[n_mu] (>= 0).  D, m, cf: interaction strength, current-quark mass, colour factor.
+ * vertex: QDSE_VERTEX_BC or QDSE_VERTEX_RL.
+ * F_ext: device complex[n_mu][3][n_ext] -- A, C, B at the external points for each mu (used in
+ *        the vertex); F_int: device complex[n_mu][3][n_r * n_4] -- A, C, B at the internal points;
+ * F_out: device complex[n_mu][3][n_ext] -- the new A, C, B; must not overlap the inputs.
+ * An internal point with q~^2 = p~^2 (it coincides with an external point, or mu = 0 and equal
+ * 4-radii) or a singular propagator gives non-finite output; no error is returned for it.
+ * n_mu = 0 returns QDSE_OK without work.  The first call with a larger n_mu grows the grid's
+ * workspace (a device allocation). */
+int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double m, double cf,
+                  int vertex, const double* F_ext, const double* F_int, double* F_out,
+                  void* stream);
+
+/* Kernel timing.  With profiling on, every qdse_mu_sweep records CUDA events around its two
+ * launches (the propagator prep and the sweep) on its stream, without synchronising.
+ * qdse_mu_profile waits for the last recorded event, adds the elapsed times since the previous
+ * read into ms[2] (prep, sweep; host double[2]) and the launch counts into launches[2] (host
+ * long long[2]), and clears them.  Either output may be NULL. */
+int qdse_mu_set_profiling(qdse_mu_grid* g, int on);
+int qdse_mu_profile(qdse_mu_grid* g, double* ms, long long* launches);
+
+void qdse_mu_grid_destroy(qdse_mu_grid* g);
+
+/* One-line description of the last error of a qdse_mu_* call on this thread. */
+const char* qdse_mu_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDSE_MU_H */

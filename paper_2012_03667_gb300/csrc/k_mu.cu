@@ -1,0 +1,479 @@
+// k_mu.cu -- finite chemical potential: the angular-moment table, the propagator prep and the
+// batched sweep (include/qdse_mu.h), for sm_103a.
+//
+// The sweep of the gap equation at finite mu (Sec. V extension of Sec. II) is, per external point
+// p and chemical potential mu, a sum over internal points q of complex structures built from
+// A, C, B at p and q, times four real angular moments of the Gaussian interaction (mu_pair.cuh).
+// The moments do not depend on mu, so they are formed once per (omega, grid) in FP64 and stored;
+// every sweep of every mu reads them.  Layout in HBM:
+//   table  T[9 * n_pairs]: external point e owns pairs [off_e, off_e + len_e); its internal points
+//          are a window r in [r_lo, r_lo + nr_e) x f in [f_lo, f_lo + nf_e) of the product grid
+//          (the rest are below exp(-70)); plane c of e is the contiguous run
+//          table[9 off_e + c len_e + jj], jj = (r - r_lo) nf_e + (f - f_lo), so that consecutive
+//          threads read consecutive words of every plane.
+//   vec    T[n_mu][12][n_int]: A, C, B, sv, s4 q~_4, ss at each internal point for each mu
+//          (re, im planes), written by k_mu_prep once per sweep.
+// k_mu_sweep runs one block per (external point, tile of TB chemical potentials): each thread
+// takes pairs jj = tid, tid + blockDim, ...; loads the pair's 9 planes once and applies them to
+// the TB chemical potentials of the tile, so the table is read n_mu/TB times per sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/qdse.h"
+#include "../../include/qdse_mu.h"
+#include "mu_pair.cuh"
+
+namespace {
+
+thread_local std::string g_mu_err;
+
+int mu_fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_mu_err = buf;
+    return status;
+}
+
+int mu_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return QDSE_OK;
+    return mu_fail(e == cudaErrorMemoryAllocation ? QDSE_ERR_OOM : QDSE_ERR_CUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
+}
+
+struct MuRow {
+    long long off;     // first pair of this external point
+    int len;           // pairs kept: nr * nf
+    int r_lo, f_lo;    // window origin in the product grid
+    int nf;            // window width in f (>= 1)
+    double P, p4;      // |p_vec|, p_4
+};
+
+constexpr int kSweepThreads = 256;
+constexpr int kMomentThreads = 256;
+constexpr int kTileF32 = 8;  // chemical potentials per block, FP32 sweep
+constexpr int kTileF64 = 4;  // chemical potentials per block, FP64 sweep
+constexpr int kMaxZ = 1024;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// ---- the moment table ------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kMomentThreads)
+k_mu_moments(const MuRow* __restrict__ rows, const double* __restrict__ qr,
+             const double* __restrict__ q4, const double* __restrict__ wq, int n_4, int nz,
+             const double* __restrict__ z_g, const double* __restrict__ wz_g, double omega,
+             double scale, T* __restrict__ table) {
+    extern __shared__ double zs[];  // z[nz], wz[nz]
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        zs[k] = z_g[k];
+        zs[nz + k] = wz_g[k];
+    }
+    __syncthreads();
+    const MuRow row = rows[blockIdx.x];
+    T* base = table + 9 * row.off;
+    for (int jj = threadIdx.x; jj < row.len; jj += blockDim.x) {
+        const int r = row.r_lo + jj / row.nf, f = row.f_lo + jj % row.nf;
+        const double Q = qr[r], h = row.p4 - q4[f];
+        double m0, m1, n0, n1, v[qmu::kPlanes];
+        qmu::mu_moments(row.P, Q, h, omega, nz, zs, zs + nz, &m0, &m1, &n0, &n1);
+        qmu::mu_planes(row.P, Q, h, m0, m1, n0, n1, scale * wq[(size_t)r * n_4 + f], v);
+#pragma unroll
+        for (int c = 0; c < qmu::kPlanes; ++c) base[(size_t)c * row.len + jj] = T(v[c]);
+    }
+}
+
+// ---- per (mu, internal point): the propagator parts --------------------------------------------
+template <class T>
+__global__ void k_mu_prep(int n_mu, const double* __restrict__ mu, int n_int, int n_4,
+                          const double* __restrict__ qr, const double* __restrict__ q4,
+                          const double* __restrict__ F_int, T* __restrict__ vec) {
+    using C = qmu::cx<double>;
+    const size_t total = (size_t)n_mu * n_int;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / n_int), j = (int)(t % n_int);
+        const int r = j / n_4, f = j % n_4;
+        const double* Fb = F_int + (size_t)b * 6 * n_int;  // [3][n_int] complex
+        const C A{Fb[2 * j], Fb[2 * j + 1]};
+        const C Cc{Fb[2 * n_int + 2 * j], Fb[2 * n_int + 2 * j + 1]};
+        const C B{Fb[4 * n_int + 2 * j], Fb[4 * n_int + 2 * j + 1]};
+        C sv, s4q, ss;
+        qmu::mu_propagator<double>(qr[r], C{q4[f], mu[b]}, A, Cc, B, &sv, &s4q, &ss);
+        const double vals[12] = {A.re, A.im, Cc.re, Cc.im, B.re, B.im,
+                                 sv.re, sv.im, s4q.re, s4q.im, ss.re, ss.im};
+        T* vb = vec + (size_t)b * 12 * n_int + j;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) vb[(size_t)c * n_int] = T(vals[c]);
+    }
+}
+
+// ---- the sweep ------------------------------------------------------------------------------------
+template <class T, int TB>
+__global__ void __launch_bounds__(kSweepThreads)
+k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
+           const double* __restrict__ q4, const T* __restrict__ table, const T* __restrict__ vec,
+           int n_int, int n_4, int n_mu, const double* __restrict__ mu,
+           const double* __restrict__ F_ext, int n_ext, double kappa, double m_cur, int bc,
+           double* __restrict__ F_out) {
+    using C = qmu::cx<T>;
+    const int e = blockIdx.x, b0 = blockIdx.y * TB;
+    const int nb = min(TB, n_mu - b0);
+    const MuRow row = rows[e];
+    const T P = T(row.P);
+    C Ai[TB], Ci[TB], Bi[TB], SA[TB], SC[TB], SB[TB];
+    T mut[TB];
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+        const int b = b0 + (t < nb ? t : 0);
+        const double* Fb = F_ext + (size_t)b * 6 * n_ext;
+        Ai[t] = C{T(Fb[2 * e]), T(Fb[2 * e + 1])};
+        Ci[t] = C{T(Fb[2 * n_ext + 2 * e]), T(Fb[2 * n_ext + 2 * e + 1])};
+        Bi[t] = C{T(Fb[4 * n_ext + 2 * e]), T(Fb[4 * n_ext + 2 * e + 1])};
+        mut[t] = T(mu[b]);
+        SA[t] = SC[t] = SB[t] = C{T(0), T(0)};
+    }
+    const T* base = table + 9 * row.off;
+    for (int jj = threadIdx.x; jj < row.len; jj += blockDim.x) {
+        const int r = row.r_lo + jj / row.nf, f = row.f_lo + jj % row.nf;
+        const int j = r * n_4 + f;
+        T v[qmu::kPlanes];
+#pragma unroll
+        for (int c = 0; c < qmu::kPlanes; ++c) v[c] = base[(size_t)c * row.len + jj];
+        const double q4f = q4[f];
+        const qmu::PairReal<T> pr = qmu::mu_pair_real<T>(v, P, T(qr[r]), T(row.p4 - q4f));
+        const T s = T(row.p4 + q4f);
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+            if (t < nb) {
+                const T* vb = vec + (size_t)(b0 + t) * 12 * n_int + j;
+                const C Aj{vb[0], vb[(size_t)n_int]};
+                const C Cj{vb[2 * (size_t)n_int], vb[3 * (size_t)n_int]};
+                const C Bj{vb[4 * (size_t)n_int], vb[5 * (size_t)n_int]};
+                const C sv{vb[6 * (size_t)n_int], vb[7 * (size_t)n_int]};
+                const C s4q{vb[8 * (size_t)n_int], vb[9 * (size_t)n_int]};
+                const C ss{vb[10 * (size_t)n_int], vb[11 * (size_t)n_int]};
+                qmu::mu_pair_add<T>(pr, s, mut[t], bc != 0, Ai[t], Ci[t], Bi[t], Aj, Cj, Bj, sv,
+                                    s4q, ss, SA[t], SC[t], SB[t]);
+            }
+        }
+    }
+    // block reduction of the 6 TB partial sums
+    constexpr int kW = kSweepThreads / 32;
+    __shared__ T red[kW][6 * TB];
+    __shared__ T tot[6 * TB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+        T x[6] = {SA[t].re, SA[t].im, SC[t].re, SC[t].im, SB[t].re, SB[t].im};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            T y = x[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+            if (lane == 0) red[warp][6 * t + c] = y;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6 * TB) {
+        T y = 0;
+#pragma unroll
+        for (int w = 0; w < kW; ++w) y += red[w][threadIdx.x];
+        tot[threadIdx.x] = y;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+        const int t = threadIdx.x, b = b0 + t;
+        const double sa_re = kappa * (double)tot[6 * t], sa_im = kappa * (double)tot[6 * t + 1];
+        const double sc_re = kappa * (double)tot[6 * t + 2], sc_im = kappa * (double)tot[6 * t + 3];
+        const double sb_re = kappa * (double)tot[6 * t + 4], sb_im = kappa * (double)tot[6 * t + 5];
+        // C = 1 + S_C / p~_4
+        const double pr = row.p4, pi = mu[b], d = 1.0 / (pr * pr + pi * pi);
+        const double c_re = (sc_re * pr + sc_im * pi) * d, c_im = (sc_im * pr - sc_re * pi) * d;
+        double* Fo = F_out + (size_t)b * 6 * n_ext;
+        Fo[2 * e] = 1.0 + sa_re;
+        Fo[2 * e + 1] = sa_im;
+        Fo[2 * n_ext + 2 * e] = 1.0 + c_re;
+        Fo[2 * n_ext + 2 * e + 1] = c_im;
+        Fo[4 * n_ext + 2 * e] = m_cur + sb_re;
+        Fo[4 * n_ext + 2 * e + 1] = sb_im;
+    }
+}
+
+bool finite_all(const double* x, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+bool increasing(const double* x, int n) {
+    for (int i = 1; i < n; ++i)
+        if (!(x[i] > x[i - 1])) return false;
+    return true;
+}
+
+}  // namespace
+
+struct qdse_mu_grid {
+    int n_ext = 0, n_r = 0, n_4 = 0, n_int = 0, nz = 0, precision = QDSE_FP64;
+    double omega = 0;
+    long long n_pairs = 0;
+    size_t elem = 8;
+    MuRow* rows = nullptr;
+    double *qr = nullptr, *q4 = nullptr, *wq = nullptr, *z = nullptr, *wz = nullptr;
+    void* table = nullptr;
+    void* vec = nullptr;
+    double* mu = nullptr;
+    int mu_cap = 0;
+    // profiling: event triples (before prep, between, after sweep) of unread calls
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    int n_rec = 0;
+};
+
+extern "C" {
+
+const char* qdse_mu_last_error(void) { return g_mu_err.c_str(); }
+
+void qdse_mu_grid_destroy(qdse_mu_grid* g) {
+    if (!g) return;
+    for (void* p : {(void*)g->rows, (void*)g->qr, (void*)g->q4, (void*)g->wq, (void*)g->z,
+                    (void*)g->wz, g->table, g->vec, (void*)g->mu})
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+    delete g;
+}
+
+int qdse_mu_grid_create(int n_ext, const double* p_abs, const double* p4, int n_r,
+                        const double* q_abs, int n_4, const double* q4, const double* w_q, int n_z,
+                        const double* z, const double* w_z, double omega, int precision,
+                        void* stream, qdse_mu_grid** out) {
+    if (!out) return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: out is NULL");
+    *out = nullptr;
+    if (n_ext < 1 || n_r < 1 || n_4 < 1 || n_z < 1)
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: n_ext, n_r, n_4, n_z must be >= 1");
+    if (n_z > kMaxZ) return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: n_z above %d", kMaxZ);
+    if ((long long)n_r * n_4 > (1LL << 28))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: n_r * n_4 above 2^28");
+    if (!p_abs || !p4 || !q_abs || !q4 || !w_q || !z || !w_z)
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: NULL array");
+    if (!(omega > 0) || !std::isfinite(omega))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: omega must be finite and > 0");
+    if (precision != QDSE_FP64 && precision != QDSE_FP32)
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: precision must be QDSE_FP64 or QDSE_FP32");
+    const int n_int = n_r * n_4;
+    if (!finite_all(p_abs, n_ext) || !finite_all(p4, n_ext) || !finite_all(q_abs, n_r) ||
+        !finite_all(q4, n_4) || !finite_all(w_q, n_int) || !finite_all(z, n_z) ||
+        !finite_all(w_z, n_z))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: non-finite node or weight");
+    for (int e = 0; e < n_ext; ++e)
+        if (!(p_abs[e] > 0)) return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: p_abs must be > 0");
+    if (!(q_abs[0] > 0) || !increasing(q_abs, n_r) || !increasing(q4, n_4))
+        return mu_fail(QDSE_ERR_ARG,
+                       "qdse_mu_grid_create: q_abs (> 0) and q4 must be strictly increasing");
+    for (int k = 0; k < n_z; ++k)
+        if (!(z[k] > -1.0 && z[k] < 1.0))
+            return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create: z nodes must lie in (-1, 1)");
+
+    // windows: |P - Q| <= L and |p_4 - q_4| <= L, L^2 = 70 omega^2 (outside, every angle's
+    // Gaussian factor is below exp(-70))
+    const double L = std::sqrt(qmu::kSkipExponent) * omega;
+    std::vector<MuRow> rows(n_ext);
+    long long off = 0;
+    for (int e = 0; e < n_ext; ++e) {
+        MuRow& w = rows[e];
+        const int r_lo = (int)(std::lower_bound(q_abs, q_abs + n_r, p_abs[e] - L) - q_abs);
+        const int r_hi = (int)(std::upper_bound(q_abs, q_abs + n_r, p_abs[e] + L) - q_abs);
+        const int f_lo = (int)(std::lower_bound(q4, q4 + n_4, p4[e] - L) - q4);
+        const int f_hi = (int)(std::upper_bound(q4, q4 + n_4, p4[e] + L) - q4);
+        const int nr = std::max(0, r_hi - r_lo), nf = std::max(0, f_hi - f_lo);
+        w.off = off;
+        w.len = nr * nf;
+        w.r_lo = std::min(r_lo, n_r - 1);
+        w.f_lo = std::min(f_lo, n_4 - 1);
+        w.nf = std::max(nf, 1);
+        w.P = p_abs[e];
+        w.p4 = p4[e];
+        off += w.len;
+    }
+
+    qdse_mu_grid* g = new qdse_mu_grid;
+    g->n_ext = n_ext;
+    g->n_r = n_r;
+    g->n_4 = n_4;
+    g->n_int = n_int;
+    g->nz = n_z;
+    g->precision = precision;
+    g->omega = omega;
+    g->n_pairs = off;
+    g->elem = precision == QDSE_FP32 ? sizeof(float) : sizeof(double);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = QDSE_OK;
+    auto alloc = [&](void** p, size_t bytes, const char* what) {
+        if (rc == QDSE_OK) rc = mu_cuda(cudaMalloc(p, std::max<size_t>(bytes, 16)), what);
+    };
+    alloc((void**)&g->rows, sizeof(MuRow) * n_ext, "cudaMalloc(rows)");
+    alloc((void**)&g->qr, sizeof(double) * n_r, "cudaMalloc(q_abs)");
+    alloc((void**)&g->q4, sizeof(double) * n_4, "cudaMalloc(q4)");
+    alloc((void**)&g->wq, sizeof(double) * n_int, "cudaMalloc(w_q)");
+    alloc((void**)&g->z, sizeof(double) * n_z, "cudaMalloc(z)");
+    alloc((void**)&g->wz, sizeof(double) * n_z, "cudaMalloc(w_z)");
+    alloc(&g->table, g->elem * qmu::kPlanes * (size_t)off, "cudaMalloc(moment table)");
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (rc == QDSE_OK)
+            rc = mu_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st),
+                         "cudaMemcpyAsync(grid)");
+    };
+    put(g->rows, rows.data(), sizeof(MuRow) * n_ext);
+    put(g->qr, q_abs, sizeof(double) * n_r);
+    put(g->q4, q4, sizeof(double) * n_4);
+    put(g->wq, w_q, sizeof(double) * n_int);
+    put(g->z, z, sizeof(double) * n_z);
+    put(g->wz, w_z, sizeof(double) * n_z);
+    if (rc == QDSE_OK && off > 0) {
+        // constant part of measure x interaction: 2 pi/(2 pi)^4 x 8 pi^2/omega^4 = 1/(pi omega^4)
+        const double scale = 1.0 / (kPi * omega * omega * omega * omega);
+        const size_t smem = 2 * sizeof(double) * n_z;
+        if (precision == QDSE_FP32)
+            k_mu_moments<float><<<n_ext, kMomentThreads, smem, st>>>(
+                g->rows, g->qr, g->q4, g->wq, n_4, n_z, g->z, g->wz, omega, scale,
+                (float*)g->table);
+        else
+            k_mu_moments<double><<<n_ext, kMomentThreads, smem, st>>>(
+                g->rows, g->qr, g->q4, g->wq, n_4, n_z, g->z, g->wz, omega, scale,
+                (double*)g->table);
+        rc = mu_cuda(cudaGetLastError(), "k_mu_moments launch");
+    }
+    // the host rows vector is freed on return: wait for its copy
+    if (rc == QDSE_OK) rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_grid_create");
+    if (rc != QDSE_OK) {
+        qdse_mu_grid_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return QDSE_OK;
+}
+
+int qdse_mu_grid_info(const qdse_mu_grid* g, long long* n_pairs, long long* table_bytes) {
+    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_info: grid is NULL");
+    if (n_pairs) *n_pairs = g->n_pairs;
+    if (table_bytes) *table_bytes = (long long)(g->elem * qmu::kPlanes * g->n_pairs);
+    return QDSE_OK;
+}
+
+int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double m, double cf,
+                  int vertex, const double* F_ext, const double* F_int, double* F_out,
+                  void* stream) {
+    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: grid is NULL");
+    if (n_mu < 0) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_mu < 0");
+    if (n_mu == 0) return QDSE_OK;
+    if (n_mu > 65535 * kTileF64) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_mu too large");
+    if (!mu || !F_ext || !F_int || !F_out) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: NULL array");
+    if (vertex != QDSE_VERTEX_BC && vertex != QDSE_VERTEX_RL)
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: vertex must be BC or RL");
+    if (!std::isfinite(D) || !std::isfinite(m) || !std::isfinite(cf))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: D, m, cf must be finite");
+    if (!finite_all(mu, n_mu)) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: non-finite mu");
+    for (int b = 0; b < n_mu; ++b)
+        if (mu[b] < 0) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: mu must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_mu > g->mu_cap) {
+        // grow the workspace; the stream's earlier work may still read the old one
+        int rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_sweep (grow)");
+        if (rc != QDSE_OK) return rc;
+        if (g->vec) cudaFree(g->vec);
+        if (g->mu) cudaFree(g->mu);
+        g->vec = nullptr;
+        g->mu = nullptr;
+        g->mu_cap = 0;
+        rc = mu_cuda(cudaMalloc(&g->vec, g->elem * 12 * (size_t)g->n_int * n_mu),
+                     "cudaMalloc(mu workspace)");
+        if (rc == QDSE_OK) rc = mu_cuda(cudaMalloc((void**)&g->mu, sizeof(double) * n_mu),
+                                        "cudaMalloc(mu values)");
+        if (rc != QDSE_OK) return rc;
+        g->mu_cap = n_mu;
+    }
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    int rc = mu_cuda(cudaMemcpyAsync(g->mu, mu, sizeof(double) * n_mu, cudaMemcpyHostToDevice, st),
+                     "cudaMemcpyAsync(mu)");
+    if (rc != QDSE_OK) return rc;
+    const size_t total = (size_t)n_mu * g->n_int;
+    const int prep_blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    const double kappa = cf * D;
+    const int bc = vertex == QDSE_VERTEX_BC;
+    cudaEvent_t* evt = nullptr;
+    if (g->profiling) {
+        if ((size_t)(3 * g->n_rec + 3) > g->ev.size()) {
+            for (int k = 0; k < 3; ++k) {
+                cudaEvent_t e;
+                rc = mu_cuda(cudaEventCreate(&e), "cudaEventCreate");
+                if (rc != QDSE_OK) return rc;
+                g->ev.push_back(e);
+            }
+        }
+        evt = &g->ev[3 * g->n_rec];
+        g->n_rec++;
+    }
+    auto mark = [&](int k) {
+        if (evt) cudaEventRecord(evt[k], st);
+    };
+    mark(0);
+    if (g->precision == QDSE_FP32) {
+        k_mu_prep<float><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4,
+                                                      F_int, (float*)g->vec);
+        mark(1);
+        dim3 grid(g->n_ext, (n_mu + kTileF32 - 1) / kTileF32);
+        k_mu_sweep<float, kTileF32><<<grid, kSweepThreads, 0, st>>>(
+            g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int, g->n_4,
+            n_mu, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+    } else {
+        k_mu_prep<double><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
+                                                       g->q4, F_int, (double*)g->vec);
+        mark(1);
+        dim3 grid(g->n_ext, (n_mu + kTileF64 - 1) / kTileF64);
+        k_mu_sweep<double, kTileF64><<<grid, kSweepThreads, 0, st>>>(
+            g->rows, g->qr, g->q4, (const double*)g->table, (const double*)g->vec, g->n_int,
+            g->n_4, n_mu, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+    }
+    mark(2);
+    return mu_cuda(cudaGetLastError(), "qdse_mu_sweep launch");
+}
+
+int qdse_mu_set_profiling(qdse_mu_grid* g, int on) {
+    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_set_profiling: grid is NULL");
+    g->profiling = on != 0;
+    return QDSE_OK;
+}
+
+int qdse_mu_profile(qdse_mu_grid* g, double* ms, long long* launches) {
+    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_profile: grid is NULL");
+    double t[2] = {0, 0};
+    if (g->n_rec > 0) {
+        int rc = mu_cuda(cudaEventSynchronize(g->ev[3 * g->n_rec - 1]), "cudaEventSynchronize");
+        if (rc != QDSE_OK) return rc;
+        for (int c = 0; c < g->n_rec; ++c)
+            for (int k = 0; k < 2; ++k) {
+                float x = 0;
+                rc = mu_cuda(cudaEventElapsedTime(&x, g->ev[3 * c + k], g->ev[3 * c + k + 1]),
+                             "cudaEventElapsedTime");
+                if (rc != QDSE_OK) return rc;
+                t[k] += x;
+            }
+    }
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    if (launches) launches[0] = launches[1] = g->n_rec;
+    g->n_rec = 0;
+    return QDSE_OK;
+}
+
+}  // extern "C"

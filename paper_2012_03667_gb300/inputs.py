@@ -93,3 +93,62 @@ def subsample(batch: List[Instance], k: int, seed: int = SCAN_SEED) -> List[int]
 def params_array(batch: List[Instance]) -> np.ndarray:
     """(n, 4) array of (D, omega, m, mu = 0)."""
     return np.array([[b.D, b.omega, b.m, 0.0] for b in batch], dtype=np.float64)
+
+
+@dataclass
+class MuWorkload:
+    """A finite chemical potential sweep workload: external points (p_abs, p4) [n_ext], the product
+    grid of internal points (q_abs [n_r] x q4 [n_4], weights w_q [n_r * n_4] including
+    |q|^2 d|q| dq_4), the angular rule (z, w_z), the chemical potentials mu [n_mu] and the
+    interaction."""
+    p_abs: np.ndarray
+    p4: np.ndarray
+    q_abs: np.ndarray
+    q4: np.ndarray
+    w_q: np.ndarray
+    z: np.ndarray
+    w_z: np.ndarray
+    mu: np.ndarray
+    D: float
+    omega: float
+    m: float
+
+
+def _log_gl(n: int, lo: float, hi: float) -> Tuple[np.ndarray, np.ndarray]:
+    """n Gauss-Legendre nodes log-mapped onto [lo, hi] and the weights of dx there."""
+    t, v = np.polynomial.legendre.leggauss(n)
+    a, b = np.log(lo), np.log(hi)
+    x = np.exp(a + 0.5 * (t + 1.0) * (b - a))
+    return x, 0.5 * (b - a) * v * x
+
+
+def mu_workload(n_r: int = 128, n_4: int = 128, n_z: int = 64, n_mu: int = 256,
+                seed: int = SCAN_SEED, lo: float = 1e-2, hi: float = 1e2,
+                mu_range: Tuple[float, float] = (0.0, 0.4), D: float = 0.93, omega: float = 0.5,
+                m: float = 0.005) -> MuWorkload:
+    """The finite-mu workload: |q| on n_r Gauss-Legendre nodes log-mapped onto [lo, hi] GeV, q_4 on
+    n_4 such nodes and their mirror images (2 n_4 values, symmetric about 0), n_z Gauss-Legendre
+    cosine nodes.  External points are staggered between the internal ones: |p|_1 = lo and
+    ln |p|_i = (ln q_{i-1} + ln q_i)/2, likewise p_4 > 0 from the positive q_4 nodes, so
+    n_ext = n_r * n_4 and no external point is an internal one.  mu ~ U[mu_range] from
+    SplitMix64(seed ^ 0x6D75), in draw order."""
+    qr, wr = _log_gl(n_r, lo, hi)
+    q4p, w4p = _log_gl(n_4, lo, hi)
+    q4 = np.concatenate([-q4p[::-1], q4p])
+    w4 = np.concatenate([w4p[::-1], w4p])
+    w_q = np.outer(wr * qr ** 2, w4).ravel()
+    stag = lambda x: np.concatenate([[lo], np.sqrt(x[:-1] * x[1:])])
+    PR, P4 = np.meshgrid(stag(qr), stag(q4p), indexing="ij")
+    z, wz = np.polynomial.legendre.leggauss(n_z)
+    rng = SplitMix64(seed ^ 0x6D75)
+    mu = np.array([mu_range[0] + (mu_range[1] - mu_range[0]) * rng.uniform() for _ in range(n_mu)])
+    return MuWorkload(PR.ravel(), P4.ravel(), qr, q4, w_q, z, wz, mu, D, omega, m)
+
+
+def mu_iterate(v_abs: np.ndarray, v4: np.ndarray, mu: float, m: float = 0.005) -> np.ndarray:
+    """A smooth synthetic iterate (A, C, B) [3, n] at points (|v|, v_4) for chemical potential mu:
+    rational functions of s = |v|^2 + (v_4 + i mu)^2 shaped like a dressed propagator,
+    A = 1 + 0.6/(1 + s/0.5), C = A (1 + 0.1/(1 + |v|)), B = 0.5/(1 + s/0.8) + m."""
+    s = v_abs ** 2 + (v4 + 1j * mu) ** 2
+    A = 1.0 + 0.6 / (1.0 + s / 0.5)
+    return np.array([A, A * (1.0 + 0.1 / (1.0 + v_abs)), 0.5 / (1.0 + s / 0.8) + m])

@@ -1,0 +1,118 @@
+"""Python binding of the finite chemical potential sweep (include/qdse_mu.h): argument marshalling
+only.
+
+The arithmetic runs in the CUDA kernels of ``libqdse.so`` (``csrc/k_mu.cu``); PyTorch supplies
+device memory and the current stream.  There is no CPU fallback: without the built library or a
+CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+
+from . import qdse as Q
+
+EXPORTS = ("qdse_mu_grid_create", "qdse_mu_grid_info", "qdse_mu_sweep", "qdse_mu_set_profiling",
+           "qdse_mu_profile", "qdse_mu_grid_destroy", "qdse_mu_last_error")
+
+_lib = None
+
+
+def load_library() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = Q.load_library()
+    P = ctypes.POINTER
+    vp, ip, dp, llp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, P(ctypes.c_longlong)
+    sig = {
+        "qdse_mu_grid_create": (ip, [ip, vp, vp, ip, vp, ip, vp, vp, ip, vp, vp, dp, ip, vp,
+                                     P(vp)]),
+        "qdse_mu_grid_info": (ip, [vp, llp, llp]),
+        "qdse_mu_sweep": (ip, [vp, ip, vp, dp, dp, dp, ip, vp, vp, vp, vp]),
+        "qdse_mu_set_profiling": (ip, [vp, ip]),
+        "qdse_mu_profile": (ip, [vp, P(dp), P(ctypes.c_longlong)]),
+        "qdse_mu_grid_destroy": (None, [vp]),
+        "qdse_mu_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _host(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+class MuGrid:
+    """Owns a ``qdse_mu_grid``: external points (|p_vec|, p_4), the product grid of internal points
+    (q_abs x q4 with weights w_q, row-major [r][f]), the angular rule and omega."""
+
+    def __init__(self, p_abs, p4, q_abs, q4, w_q, z, w_z, omega: float,
+                 precision: int = Q.QDSE_FP64):
+        self.lib = load_library()
+        arrs = [_host(a) for a in (p_abs, p4, q_abs, q4, w_q, z, w_z)]
+        self._keep = arrs
+        p_abs, p4, q_abs, q4, w_q, z, w_z = arrs
+        self.n_ext, self.n_r, self.n_4 = len(p_abs), len(q_abs), len(q4)
+        self.n_int = self.n_r * self.n_4
+        assert len(p4) == self.n_ext and w_q.size == self.n_int and len(w_z) == len(z)
+        self.precision = precision
+        self.ptr = ctypes.c_void_p()
+        st = self.lib.qdse_mu_grid_create(self.n_ext, p_abs.ctypes.data, p4.ctypes.data, self.n_r,
+                                          q_abs.ctypes.data, self.n_4, q4.ctypes.data,
+                                          w_q.ctypes.data, len(z), z.ctypes.data, w_z.ctypes.data,
+                                          float(omega), precision, Q._current_stream(),
+                                          ctypes.byref(self.ptr))
+        if st != Q.QDSE_OK:
+            raise Q.QdseError(st, self.lib.qdse_mu_last_error().decode())
+
+    def info(self) -> dict:
+        n, b = ctypes.c_longlong(), ctypes.c_longlong()
+        self._raise(self.lib.qdse_mu_grid_info(self.ptr, ctypes.byref(n), ctypes.byref(b)))
+        return {"n_pairs": n.value, "table_bytes": b.value}
+
+    def sweep(self, mu: Sequence[float], D: float, m: float, F_ext, F_int, F_out,
+              vertex: int = Q.QDSE_VERTEX_BC, cf: float = 4.0 / 3.0):
+        """F_ext, F_out: torch.complex128 CUDA tensors [n_mu, 3, n_ext] (A, C, B); F_int:
+        [n_mu, 3, n_r * n_4]."""
+        import torch
+        mu = _host(mu)
+        n_mu = len(mu)
+        for t, n in ((F_ext, self.n_ext), (F_int, self.n_int), (F_out, self.n_ext)):
+            assert t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()
+            assert tuple(t.shape) == (n_mu, 3, n), f"expected {(n_mu, 3, n)}, got {tuple(t.shape)}"
+        self._raise(self.lib.qdse_mu_sweep(self.ptr, n_mu, mu.ctypes.data, float(D), float(m),
+                                           float(cf), vertex, F_ext.data_ptr(), F_int.data_ptr(),
+                                           F_out.data_ptr(), Q._current_stream()))
+
+    def set_profiling(self, on: bool):
+        self._raise(self.lib.qdse_mu_set_profiling(self.ptr, int(bool(on))))
+
+    def profile(self) -> dict:
+        """Event-timed milliseconds and launches of the prep and sweep kernels since the last
+        read (waits for the last recorded sweep)."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_longlong * 2)()
+        self._raise(self.lib.qdse_mu_profile(self.ptr, ms, n))
+        return {k: {"ms": ms[i], "launches": n[i]} for i, k in enumerate(("prep", "sweep"))}
+
+    def _raise(self, st: int):
+        if st != Q.QDSE_OK:
+            raise Q.QdseError(st, self.lib.qdse_mu_last_error().decode())
+
+    def close(self):
+        if self.ptr:
+            self.lib.qdse_mu_grid_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,6 +8,7 @@ import pytest
 
 from paper_2012_03667_gb300 import build as B
 from paper_2012_03667_gb300 import qdse as Q
+from paper_2012_03667_gb300 import qdse_mu as QM
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -18,8 +19,8 @@ def lib():
     return Q.load_library()
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "qdse.h")).read()
+def declared_functions(header="qdse.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(qdse_[a-z_0-9]+)\s*\(", src)))
 
@@ -30,6 +31,48 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), f"{n} declared in include/qdse.h but not exported"
     assert set(names) == set(Q.EXPORTS)
+    mu_names = declared_functions("qdse_mu.h")
+    for n in mu_names:
+        assert hasattr(lib, n), f"{n} declared in include/qdse_mu.h but not exported"
+    assert set(mu_names) == set(QM.EXPORTS)
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["qdse.h", "qdse_mu.h"]
+
+
+def _mu_create(lib, n_ext=2, p_abs=(0.5, 1.0), p4=(0.3, 0.7), q_abs=(0.2, 0.4, 0.9),
+               q4=(-1.0, 0.1, 1.2), n_z=4, omega=0.5, precision=Q.QDSE_FP64):
+    dp = ctypes.c_double
+    arr = lambda xs: (dp * len(xs))(*xs)
+    w_q = arr([1.0] * (len(q_abs) * len(q4)))
+    z, wz = arr([-0.5, -0.1, 0.2, 0.6][:n_z] + [0.0] * max(0, n_z - 4)), arr([0.5] * n_z)
+    p = ctypes.c_void_p()
+    st = lib.qdse_mu_grid_create(n_ext, arr(p_abs), arr(p4), len(q_abs), arr(q_abs), len(q4),
+                                 arr(q4), w_q, n_z, z, wz, omega, precision, None, ctypes.byref(p))
+    return st, p
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(n_ext=0), "n_ext"),
+    (dict(p_abs=(0.0, 1.0)), "p_abs"),
+    (dict(q_abs=(0.4, 0.2, 0.9)), "increasing"),
+    (dict(q4=(0.1, -1.0, 1.2)), "increasing"),
+    (dict(q_abs=(0.0, 0.4, 0.9)), "increasing"),
+    (dict(p4=(0.3, float("nan"))), "non-finite"),
+    (dict(omega=0.0), "omega"),
+    (dict(precision=Q.QDSE_MIXED), "precision"),
+    (dict(n_z=2000), "n_z"),
+])
+def test_mu_grid_create_rejects_bad_arguments_on_the_host(lib, kw, msg):
+    QM.load_library()
+    st, p = _mu_create(lib, **kw)
+    assert st == Q.QDSE_ERR_ARG and not p
+    assert msg in lib.qdse_mu_last_error().decode()
+
+
+def test_mu_sweep_rejects_a_null_grid(lib):
+    QM.load_library()
+    assert lib.qdse_mu_sweep(None, 1, None, 1.0, 0.0, 1.0, 0, None, None, None, None) == Q.QDSE_ERR_ARG
+    assert lib.qdse_mu_grid_info(None, None, None) == Q.QDSE_ERR_ARG
+    lib.qdse_mu_grid_destroy(None)  # accepted
 
 
 def test_default_options(lib):
