@@ -11,11 +11,16 @@
 //          (the rest are below exp(-70)); plane c of e is the contiguous run
 //          table[9 off_e + c len_e + jj], jj = (r - r_lo) nf_e + (f - f_lo), so that consecutive
 //          threads read consecutive words of every plane.
-//   vec    T[n_mu][12][n_int]: A, C, B, sv, s4 q~_4, ss at each internal point for each mu
-//          (re, im planes), written by k_mu_prep once per sweep.
-// k_mu_sweep runs one block per (external point, tile of TB chemical potentials): each thread
-// takes pairs jj = tid, tid + blockDim, ...; loads the pair's 9 planes once and applies them to
-// the TB chemical potentials of the tile, so the table is read n_mu/TB times per sweep.
+//   vec    T[n_mu][n_int][12]: A, C, B, sv, s4 q~_4, ss at each internal point for each mu
+//          ((re, im) pairs; 48 B per point in FP32, read as three 16-byte loads), written by
+//          k_mu_prep once per sweep.
+// k_mu_sweep gives each warp one (external point, tile of TB chemical potentials): its lanes take
+// pairs jj = lane, lane + 32, ...; each lane loads a pair's 9 planes once and applies them to the
+// TB chemical potentials of the tile (the table is read n_mu/TB times per sweep), and the warp
+// reduces its sums with shuffles (no block barrier).  Consecutive warps take consecutive external
+// points of the same tile, so the tile's vectors stay in L2 while the table streams from HBM.
+// The tile's values at the external point sit in shared memory, which keeps the FP32 kernel at
+// 128 registers (4 blocks of 4 warps per SM).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,10 +62,10 @@ struct MuRow {
     double P, p4;      // |p_vec|, p_4
 };
 
-constexpr int kSweepThreads = 256;
+constexpr int kSweepThreads = 128;  // 4 independent warps per block
 constexpr int kMomentThreads = 256;
-constexpr int kTileF32 = 8;  // chemical potentials per block, FP32 sweep
-constexpr int kTileF64 = 4;  // chemical potentials per block, FP64 sweep
+constexpr int kTileF32 = 8;  // chemical potentials per warp, FP32 sweep
+constexpr int kTileF64 = 4;  // chemical potentials per warp, FP64 sweep
 constexpr int kMaxZ = 1024;
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
@@ -109,39 +114,68 @@ __global__ void k_mu_prep(int n_mu, const double* __restrict__ mu, int n_int, in
         qmu::mu_propagator<double>(qr[r], C{q4[f], mu[b]}, A, Cc, B, &sv, &s4q, &ss);
         const double vals[12] = {A.re, A.im, Cc.re, Cc.im, B.re, B.im,
                                  sv.re, sv.im, s4q.re, s4q.im, ss.re, ss.im};
-        T* vb = vec + (size_t)b * 12 * n_int + j;
+        T* vb = vec + t * 12;
 #pragma unroll
-        for (int c = 0; c < 12; ++c) vb[(size_t)c * n_int] = T(vals[c]);
+        for (int c = 0; c < 12; ++c) vb[c] = T(vals[c]);
     }
 }
 
 // ---- the sweep ------------------------------------------------------------------------------------
-template <class T, int TB>
-__global__ void __launch_bounds__(kSweepThreads)
+// The 12 values of one (mu, internal point): three 16-byte loads in FP32, six in FP64.
+template <class T>
+__device__ __forceinline__ void load_point(const T* p, qmu::cx<T>* x);
+template <>
+__device__ __forceinline__ void load_point<float>(const float* p, qmu::cx<float>* x) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = q[0], b = q[1], c = q[2];
+    x[0] = {a.x, a.y}; x[1] = {a.z, a.w}; x[2] = {b.x, b.y};
+    x[3] = {b.z, b.w}; x[4] = {c.x, c.y}; x[5] = {c.z, c.w};
+}
+template <>
+__device__ __forceinline__ void load_point<double>(const double* p, qmu::cx<double>* x) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double2 v = q[k];
+        x[k] = {v.x, v.y};
+    }
+}
+
+template <class T, int TB, int MINB>
+__global__ void __launch_bounds__(kSweepThreads, MINB)
 k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
            const double* __restrict__ q4, const T* __restrict__ table, const T* __restrict__ vec,
-           int n_int, int n_4, int n_mu, const double* __restrict__ mu,
+           int n_int, int n_4, int n_mu, int n_tiles, const double* __restrict__ mu,
            const double* __restrict__ F_ext, int n_ext, double kappa, double m_cur, int bc,
            double* __restrict__ F_out) {
     using C = qmu::cx<T>;
-    const int e = blockIdx.x, b0 = blockIdx.y * TB;
+    constexpr int kW = kSweepThreads / 32;
+    __shared__ T ext[kW][TB][7];  // A, C, B at the external point and mu, per slot of the tile
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long item = (long long)blockIdx.x * kW + wib;
+    if (item >= (long long)n_ext * n_tiles) return;  // whole warps only; no block barrier below
+    const int e = (int)(item % n_ext), b0 = (int)(item / n_ext) * TB;
     const int nb = min(TB, n_mu - b0);
     const MuRow row = rows[e];
-    const T P = T(row.P);
-    C Ai[TB], Ci[TB], Bi[TB], SA[TB], SC[TB], SB[TB];
-    T mut[TB];
-#pragma unroll
-    for (int t = 0; t < TB; ++t) {
-        const int b = b0 + (t < nb ? t : 0);
+    if (lane < TB) {
+        const int b = b0 + (lane < nb ? lane : 0);
         const double* Fb = F_ext + (size_t)b * 6 * n_ext;
-        Ai[t] = C{T(Fb[2 * e]), T(Fb[2 * e + 1])};
-        Ci[t] = C{T(Fb[2 * n_ext + 2 * e]), T(Fb[2 * n_ext + 2 * e + 1])};
-        Bi[t] = C{T(Fb[4 * n_ext + 2 * e]), T(Fb[4 * n_ext + 2 * e + 1])};
-        mut[t] = T(mu[b]);
-        SA[t] = SC[t] = SB[t] = C{T(0), T(0)};
+        T* d = ext[wib][lane];
+        d[0] = T(Fb[2 * e]);
+        d[1] = T(Fb[2 * e + 1]);
+        d[2] = T(Fb[2 * n_ext + 2 * e]);
+        d[3] = T(Fb[2 * n_ext + 2 * e + 1]);
+        d[4] = T(Fb[4 * n_ext + 2 * e]);
+        d[5] = T(Fb[4 * n_ext + 2 * e + 1]);
+        d[6] = T(mu[b]);
     }
+    __syncwarp();
+    const T P = T(row.P);
+    C SA[TB], SC[TB], SB[TB];
+#pragma unroll
+    for (int t = 0; t < TB; ++t) SA[t] = SC[t] = SB[t] = C{T(0), T(0)};
     const T* base = table + 9 * row.off;
-    for (int jj = threadIdx.x; jj < row.len; jj += blockDim.x) {
+    for (int jj = lane; jj < row.len; jj += 32) {
         const int r = row.r_lo + jj / row.nf, f = row.f_lo + jj % row.nf;
         const int j = r * n_4 + f;
         T v[qmu::kPlanes];
@@ -153,57 +187,39 @@ k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
 #pragma unroll
         for (int t = 0; t < TB; ++t) {
             if (t < nb) {
-                const T* vb = vec + (size_t)(b0 + t) * 12 * n_int + j;
-                const C Aj{vb[0], vb[(size_t)n_int]};
-                const C Cj{vb[2 * (size_t)n_int], vb[3 * (size_t)n_int]};
-                const C Bj{vb[4 * (size_t)n_int], vb[5 * (size_t)n_int]};
-                const C sv{vb[6 * (size_t)n_int], vb[7 * (size_t)n_int]};
-                const C s4q{vb[8 * (size_t)n_int], vb[9 * (size_t)n_int]};
-                const C ss{vb[10 * (size_t)n_int], vb[11 * (size_t)n_int]};
-                qmu::mu_pair_add<T>(pr, s, mut[t], bc != 0, Ai[t], Ci[t], Bi[t], Aj, Cj, Bj, sv,
-                                    s4q, ss, SA[t], SC[t], SB[t]);
+                C x[6];  // A, C, B, sv, s4 q~_4, ss at the internal point
+                load_point<T>(vec + ((size_t)(b0 + t) * n_int + j) * 12, x);
+                const T* d = ext[wib][t];
+                qmu::mu_pair_add<T>(pr, s, d[6], bc != 0, C{d[0], d[1]}, C{d[2], d[3]},
+                                    C{d[4], d[5]}, x[0], x[1], x[2], x[3], x[4], x[5], SA[t],
+                                    SC[t], SB[t]);
             }
         }
     }
-    // block reduction of the 6 TB partial sums
-    constexpr int kW = kSweepThreads / 32;
-    __shared__ T red[kW][6 * TB];
-    __shared__ T tot[6 * TB];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp all-reduce of the 6 TB sums; lane t writes chemical potential b0 + t
 #pragma unroll
     for (int t = 0; t < TB; ++t) {
-        T x[6] = {SA[t].re, SA[t].im, SC[t].re, SC[t].im, SB[t].re, SB[t].im};
+        T y[6] = {SA[t].re, SA[t].im, SC[t].re, SC[t].im, SB[t].re, SB[t].im};
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            T y = x[c];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
-            if (lane == 0) red[warp][6 * t + c] = y;
+            for (int o = 16; o > 0; o >>= 1) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
         }
-    }
-    __syncthreads();
-    if (threadIdx.x < 6 * TB) {
-        T y = 0;
-#pragma unroll
-        for (int w = 0; w < kW; ++w) y += red[w][threadIdx.x];
-        tot[threadIdx.x] = y;
-    }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-        const int t = threadIdx.x, b = b0 + t;
-        const double sa_re = kappa * (double)tot[6 * t], sa_im = kappa * (double)tot[6 * t + 1];
-        const double sc_re = kappa * (double)tot[6 * t + 2], sc_im = kappa * (double)tot[6 * t + 3];
-        const double sb_re = kappa * (double)tot[6 * t + 4], sb_im = kappa * (double)tot[6 * t + 5];
-        // C = 1 + S_C / p~_4
-        const double pr = row.p4, pi = mu[b], d = 1.0 / (pr * pr + pi * pi);
-        const double c_re = (sc_re * pr + sc_im * pi) * d, c_im = (sc_im * pr - sc_re * pi) * d;
-        double* Fo = F_out + (size_t)b * 6 * n_ext;
-        Fo[2 * e] = 1.0 + sa_re;
-        Fo[2 * e + 1] = sa_im;
-        Fo[2 * n_ext + 2 * e] = 1.0 + c_re;
-        Fo[2 * n_ext + 2 * e + 1] = c_im;
-        Fo[4 * n_ext + 2 * e] = m_cur + sb_re;
-        Fo[4 * n_ext + 2 * e + 1] = sb_im;
+        if (lane == t && t < nb) {
+            const int b = b0 + t;
+            const double sa_re = kappa * (double)y[0], sa_im = kappa * (double)y[1];
+            const double sc_re = kappa * (double)y[2], sc_im = kappa * (double)y[3];
+            const double sb_re = kappa * (double)y[4], sb_im = kappa * (double)y[5];
+            // C = 1 + S_C / p~_4
+            const double pr_ = row.p4, pi_ = mu[b], dd = 1.0 / (pr_ * pr_ + pi_ * pi_);
+            double* Fo = F_out + (size_t)b * 6 * n_ext;
+            Fo[2 * e] = 1.0 + sa_re;
+            Fo[2 * e + 1] = sa_im;
+            Fo[2 * n_ext + 2 * e] = 1.0 + (sc_re * pr_ + sc_im * pi_) * dd;
+            Fo[2 * n_ext + 2 * e + 1] = (sc_im * pr_ - sc_re * pi_) * dd;
+            Fo[4 * n_ext + 2 * e] = m_cur + sb_re;
+            Fo[4 * n_ext + 2 * e + 1] = sb_im;
+        }
     }
 }
 
@@ -374,7 +390,8 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
     if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: grid is NULL");
     if (n_mu < 0) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_mu < 0");
     if (n_mu == 0) return QDSE_OK;
-    if (n_mu > 65535 * kTileF64) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_mu too large");
+    if ((long long)g->n_ext * ((n_mu + kTileF64 - 1) / kTileF64) > (1LL << 32))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_ext * n_mu too large for one launch");
     if (!mu || !F_ext || !F_int || !F_out) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: NULL array");
     if (vertex != QDSE_VERTEX_BC && vertex != QDSE_VERTEX_RL)
         return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: vertex must be BC or RL");
@@ -429,18 +446,20 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
         k_mu_prep<float><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4,
                                                       F_int, (float*)g->vec);
         mark(1);
-        dim3 grid(g->n_ext, (n_mu + kTileF32 - 1) / kTileF32);
-        k_mu_sweep<float, kTileF32><<<grid, kSweepThreads, 0, st>>>(
+        const int n_tiles = (n_mu + kTileF32 - 1) / kTileF32;
+        const long long warps = (long long)g->n_ext * n_tiles;
+        k_mu_sweep<float, kTileF32, 4><<<(unsigned)((warps + 3) / 4), kSweepThreads, 0, st>>>(
             g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int, g->n_4,
-            n_mu, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+            n_mu, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
     } else {
         k_mu_prep<double><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
                                                        g->q4, F_int, (double*)g->vec);
         mark(1);
-        dim3 grid(g->n_ext, (n_mu + kTileF64 - 1) / kTileF64);
-        k_mu_sweep<double, kTileF64><<<grid, kSweepThreads, 0, st>>>(
+        const int n_tiles = (n_mu + kTileF64 - 1) / kTileF64;
+        const long long warps = (long long)g->n_ext * n_tiles;
+        k_mu_sweep<double, kTileF64, 2><<<(unsigned)((warps + 3) / 4), kSweepThreads, 0, st>>>(
             g->rows, g->qr, g->q4, (const double*)g->table, (const double*)g->vec, g->n_int,
-            g->n_4, n_mu, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+            g->n_4, n_mu, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
     }
     mark(2);
     return mu_cuda(cudaGetLastError(), "qdse_mu_sweep launch");

@@ -81,7 +81,7 @@ def test_mu_sweep_matches_oracle(QM, precision, tol, vertex):
 
 def test_mu_batch_position_does_not_change_results(QM):
     """A mu gives bitwise the same output alone and in a later tile of a larger batch at the same
-    slot of the tile (8 chemical potentials per block in FP32): tiles, workspace growth and reuse
+    slot of the tile (8 chemical potentials per warp in FP32): tiles, workspace growth and reuse
     do not change the arithmetic.  n_mu = 0 is a no-op."""
     w = I.mu_workload(**SMALL)
     qv, q4 = _internal(w)
