@@ -54,6 +54,34 @@ int qdse_mu_grid_create(int n_ext, const double* p_abs, const double* p4, int n_
                         const double* z, const double* w_z, double omega, int precision,
                         void* stream, qdse_mu_grid** out);
 
+/* As qdse_mu_grid_create, with the external points the product grid p_axis x p4_axis (host
+ * double[n_pr], double[n_p4]; both > 0 and strictly increasing; external point e = i * n_p4 + k
+ * has |p_vec| = p_axis[i], p_4 = p4_axis[k]).  Such a grid also carries the interpolation that
+ * qdse_mu_solve uses to get A, C, B at the internal points (reading M6, the staggered-grid rule of
+ * Sec. III along each axis): linear in |p| and in p_4 between the bracketing external nodes, held
+ * at the first/last node outside them, and F(|q|, -q_4) = conj F(|q|, q_4) for q_4 < 0. */
+int qdse_mu_grid_create_product(int n_pr, const double* p_axis, int n_p4, const double* p4_axis,
+                                int n_r, const double* q_abs, int n_4, const double* q4,
+                                const double* w_q, int n_z, const double* z, const double* w_z,
+                                double omega, int precision, void* stream, qdse_mu_grid** out);
+
+/* Successive approximation (Eq. jifen14 scheme) of the finite-mu equation for n_mu chemical
+ * potentials at once: G = sweep(F, interpolate(F)); F <- G (alpha = 1) or (1 - alpha) F + alpha G.
+ * Convergence (reading M7, per mu): max over A, C, B of max|F_new - F_old| / max|F_new| over the
+ * grid (absolute where max|F_new| = 0) below tol; a converged mu is frozen while the others go on.
+ * g: a product grid.  refine: NULL, or a product grid on the same points (normally QDSE_FP64 with
+ * g QDSE_FP32): sweeps run on g until every mu's change is below max(tol, switch_tol), then on
+ * refine until tol.  mu: host double[n_mu] (>= 0).  alpha in (0, 1].  max_iter >= 1 counts
+ * sweeps of both phases.
+ * F: device complex[n_mu][3][n_ext] -- the start on entry, the last iterate on return.
+ * iters, status: host int[n_mu] or NULL -- sweeps to convergence (max_iter otherwise) and
+ * QDSE_OK / QDSE_ERR_NOT_CONVERGED / QDSE_ERR_NONFINITE per mu.
+ * Synchronises the stream once per sweep (to read the per-mu change).  Returns QDSE_OK unless an
+ * argument or CUDA error occurred. */
+int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double* mu, double D,
+                  double m, double cf, int vertex, double alpha, double tol, double switch_tol,
+                  int max_iter, double* F, int* iters, int* status, void* stream);
+
 /* Sizes: the pairs kept in the table and its device bytes (either pointer may be NULL). */
 int qdse_mu_grid_info(const qdse_mu_grid* g, long long* n_pairs, long long* table_bytes);
 

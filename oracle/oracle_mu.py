@@ -99,3 +99,61 @@ def sweep(pv, p4, qv, q4, wq, z, wz, D, omega, m, mu, Ap, Cp, Bp, Aq, Cq, Bq, cf
     if bad:
         raise ValueError("singular propagator or k^2 = 0 at some (p, q) pair")
     return tuple(o.view(np.complex128) for o in outs)
+
+
+def interpolate(p_axis, p4_axis, F, q_abs, q4):
+    """Values at the internal points of the product grid (q_abs x q4, row-major) from values F
+    [3, n_pr * n_p4] on the external product grid (p_axis x p4_axis, row-major, both ascending,
+    p4 > 0) -- reading M6: the staggered-grid rule of Sec. III applied along each axis in turn
+    (linear in |p| and in p_4 between the bracketing nodes, held constant beyond the last node),
+    and F(|q|, -q_4) = conj F(|q|, q_4) for q_4 < 0."""
+    F = np.asarray(F, dtype=np.complex128).reshape(3, len(p_axis), len(p4_axis))
+
+    def bracket(axis, x):
+        # (lower index, weight of the upper node); x below the first node is held at it
+        i = np.searchsorted(axis, x, side="right") - 1
+        if i < 0:
+            return 0, 0.0
+        if i >= len(axis) - 1:
+            return len(axis) - 1, 0.0
+        return i, (x - axis[i]) / (axis[i + 1] - axis[i])
+
+    out = np.empty((3, len(q_abs), len(q4)), dtype=np.complex128)
+    for r, Q in enumerate(q_abs):
+        i, a = bracket(p_axis, Q)
+        i1 = min(i + 1, len(p_axis) - 1)
+        for f, x4 in enumerate(q4):
+            k, b = bracket(p4_axis, abs(x4))
+            k1 = min(k + 1, len(p4_axis) - 1)
+            v = ((1 - a) * (1 - b) * F[:, i, k] + a * (1 - b) * F[:, i1, k]
+                 + (1 - a) * b * F[:, i, k1] + a * b * F[:, i1, k1])
+            out[:, r, f] = np.conj(v) if x4 < 0 else v
+    return out.reshape(3, -1)
+
+
+def solve(p_axis, p4_axis, q_abs, q4, w_q, z, wz, D, omega, m, mu, F0, tol=1e-10, max_iter=500,
+          cf=4.0 / 3.0, vertex=BC, alpha=1.0, nthreads=0):
+    """Successive approximation (the paper's Eq. jifen14 scheme) of the finite-mu equation on the
+    external product grid: G = sweep(F, interpolate(F)), F <- G (alpha = 1) or
+    F <- (1 - alpha) F + alpha G, until the relative change of reading M7 (per function,
+    max |F_new - F_old| over the grid divided by max |F_new|) is below tol; tol = 0 runs exactly
+    max_iter steps.  (The change of a function that is identically zero is taken absolute.)
+    Returns (F [3, n_ext], iterations, converged)."""
+    PR, P4 = np.meshgrid(p_axis, p4_axis, indexing="ij")
+    pv, p4 = PR.ravel(), P4.ravel()
+    QR, Q4 = np.meshgrid(q_abs, q4, indexing="ij")
+    qv, q4f = QR.ravel(), Q4.ravel()
+    F = np.asarray(F0, dtype=np.complex128).reshape(3, -1).copy()
+    for it in range(1, max_iter + 1):
+        Fi = interpolate(p_axis, p4_axis, F, q_abs, q4)
+        G = np.array(sweep(pv, p4, qv, q4f, w_q, z, wz, D, omega, m, mu, *F, *Fi, cf=cf,
+                           vertex=vertex, nthreads=nthreads))
+        new = G if alpha == 1.0 else (1.0 - alpha) * F + alpha * G
+        change = 0.0
+        for c in range(3):
+            d, mag = np.abs(new[c] - F[c]).max(), np.abs(new[c]).max()
+            change = max(change, d / mag if mag > 0 else d)
+        F = new
+        if change < tol:
+            return F, it, True
+    return F, max_iter, False

@@ -120,6 +120,112 @@ __global__ void k_mu_prep(int n_mu, const double* __restrict__ mu, int n_int, in
     }
 }
 
+// Reading M6 for one internal point: the four external corners (|p| lower/upper x p_4
+// lower/upper, flat indices i * n_p4 + k), the weights of the upper |p| node (a) and of the upper
+// p_4 node (b), and whether the point mirrors q_4 < 0 (value conjugated).
+struct MuInterp {
+    int e00, e10, e01, e11;
+    double a, b;
+    int conj, pad;
+};
+
+// Propagator parts of one (mu, internal point) from its A, C, B; stored as 12 values in T.
+template <class T>
+__device__ __forceinline__ void prep_store(qmu::cx<double> A, qmu::cx<double> Cc,
+                                           qmu::cx<double> B, double Q, double q4f, double mu_b,
+                                           T* vb) {
+    qmu::cx<double> sv, s4q, ss;
+    qmu::mu_propagator<double>(Q, qmu::cx<double>{q4f, mu_b}, A, Cc, B, &sv, &s4q, &ss);
+    const double vals[12] = {A.re, A.im, Cc.re, Cc.im, B.re, B.im,
+                             sv.re, sv.im, s4q.re, s4q.im, ss.re, ss.im};
+#pragma unroll
+    for (int c = 0; c < 12; ++c) vb[c] = T(vals[c]);
+}
+
+// As k_mu_prep, with A, C, B at the internal points interpolated from the external values.
+template <class T>
+__global__ void k_mu_prep_interp(int n_mu, const double* __restrict__ mu, int n_int, int n_4,
+                                 const double* __restrict__ qr, const double* __restrict__ q4,
+                                 const MuInterp* __restrict__ interp,
+                                 const double* __restrict__ F_ext, int n_ext, T* __restrict__ vec) {
+    using C = qmu::cx<double>;
+    const size_t total = (size_t)n_mu * n_int;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / n_int), j = (int)(t % n_int);
+        const MuInterp ip = interp[j];
+        const double w00 = (1.0 - ip.a) * (1.0 - ip.b), w10 = ip.a * (1.0 - ip.b);
+        const double w01 = (1.0 - ip.a) * ip.b, w11 = ip.a * ip.b;
+        C v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double* Fc = F_ext + ((size_t)b * 3 + c) * 2 * n_ext;
+            C x = C{Fc[2 * ip.e00], Fc[2 * ip.e00 + 1]} * w00 +
+                  C{Fc[2 * ip.e10], Fc[2 * ip.e10 + 1]} * w10;
+            x = x + C{Fc[2 * ip.e01], Fc[2 * ip.e01 + 1]} * w01;
+            x = x + C{Fc[2 * ip.e11], Fc[2 * ip.e11 + 1]} * w11;
+            if (ip.conj) x.im = -x.im;
+            v[c] = x;
+        }
+        prep_store<T>(v[0], v[1], v[2], qr[j / n_4], q4[j % n_4], mu[b], vec + t * 12);
+    }
+}
+
+// One relaxation step and the convergence measure of reading M7, one block per chemical
+// potential: F <- G (alpha = 1) or (1 - alpha) F + alpha G; change[b] = max over A, C, B of
+// max|F_new - F_old| / max|F_new| (absolute where max|F_new| = 0); bad[b] = non-finite value.
+// Chemical potentials with done[b] set are left as they are.
+constexpr int kRelaxThreads = 256;
+__global__ void __launch_bounds__(kRelaxThreads)
+k_mu_relax(int n_ext, double alpha, double* __restrict__ F, const double* __restrict__ G,
+           const int* __restrict__ done, double* __restrict__ change, int* __restrict__ bad) {
+    const int b = blockIdx.x;
+    if (done[b]) return;  // uniform over the block
+    double md[3] = {0, 0, 0}, mm[3] = {0, 0, 0};
+    int nonfinite = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double* Fc = F + ((size_t)b * 3 + c) * 2 * n_ext;
+        const double* Gc = G + ((size_t)b * 3 + c) * 2 * n_ext;
+        for (int e = threadIdx.x; e < n_ext; e += blockDim.x) {
+            const double fr = Fc[2 * e], fi = Fc[2 * e + 1];
+            double nr = Gc[2 * e], ni = Gc[2 * e + 1];
+            if (alpha != 1.0) {
+                nr = (1.0 - alpha) * fr + alpha * nr;
+                ni = (1.0 - alpha) * fi + alpha * ni;
+            }
+            if (!isfinite(nr) || !isfinite(ni)) nonfinite = 1;
+            md[c] = fmax(md[c], hypot(nr - fr, ni - fi));
+            mm[c] = fmax(mm[c], hypot(nr, ni));
+            Fc[2 * e] = nr;
+            Fc[2 * e + 1] = ni;
+        }
+    }
+    __shared__ double red[kRelaxThreads / 32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double x[6] = {md[0], md[1], md[2], mm[0], mm[1], mm[2]};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x[k] = fmax(x[k], __shfl_down_sync(0xffffffffu, x[k], o));
+        if (lane == 0) red[warp][k] = x[k];
+    }
+    const int any_bad = __syncthreads_or(nonfinite);
+    if (threadIdx.x == 0) {
+        double ch = 0;
+        for (int c = 0; c < 3; ++c) {
+            double d = 0, m = 0;
+            for (int w = 0; w < kRelaxThreads / 32; ++w) {
+                d = fmax(d, red[w][c]);
+                m = fmax(m, red[w][3 + c]);
+            }
+            ch = fmax(ch, m > 0 ? d / m : d);
+        }
+        change[b] = ch;
+        bad[b] = any_bad;
+    }
+}
+
 // ---- the sweep ------------------------------------------------------------------------------------
 // The 12 values of one (mu, internal point): three 16-byte loads in FP32, six in FP64.
 template <class T>
@@ -248,6 +354,15 @@ struct qdse_mu_grid {
     void* vec = nullptr;
     double* mu = nullptr;
     int mu_cap = 0;
+    // external product grid and interpolation onto the internal points (create_product only)
+    int n_pr = 0, n_p4 = 0;
+    MuInterp* interp = nullptr;
+    double fingerprint = 0;  // of every node and weight: grids with equal points match
+    // solve workspace: the new iterate, per-mu change, non-finite and done flags
+    double* G = nullptr;
+    double* change = nullptr;
+    int *bad = nullptr, *done = nullptr;
+    int solve_cap = 0;
     // profiling: event triples (before prep, between, after sweep) of unread calls
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
@@ -261,7 +376,8 @@ const char* qdse_mu_last_error(void) { return g_mu_err.c_str(); }
 void qdse_mu_grid_destroy(qdse_mu_grid* g) {
     if (!g) return;
     for (void* p : {(void*)g->rows, (void*)g->qr, (void*)g->q4, (void*)g->wq, (void*)g->z,
-                    (void*)g->wz, g->table, g->vec, (void*)g->mu})
+                    (void*)g->wz, g->table, g->vec, (void*)g->mu, (void*)g->interp, (void*)g->G,
+                    (void*)g->change, (void*)g->bad, (void*)g->done})
         if (p) cudaFree(p);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;
@@ -330,6 +446,20 @@ int qdse_mu_grid_create(int n_ext, const double* p_abs, const double* p4, int n_
     g->omega = omega;
     g->n_pairs = off;
     g->elem = precision == QDSE_FP32 ? sizeof(float) : sizeof(double);
+    {
+        double fp = omega;
+        auto mix = [&](const double* x, int n) {
+            for (int i = 0; i < n; ++i) fp += x[i] * (1.0 + 1e-3 * (i % 97));
+        };
+        mix(p_abs, n_ext);
+        mix(p4, n_ext);
+        mix(q_abs, n_r);
+        mix(q4, n_4);
+        mix(w_q, n_int);
+        mix(z, n_z);
+        mix(w_z, n_z);
+        g->fingerprint = fp;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     int rc = QDSE_OK;
     auto alloc = [&](void** p, size_t bytes, const char* what) {
@@ -384,26 +514,27 @@ int qdse_mu_grid_info(const qdse_mu_grid* g, long long* n_pairs, long long* tabl
     return QDSE_OK;
 }
 
-int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double m, double cf,
-                  int vertex, const double* F_ext, const double* F_int, double* F_out,
-                  void* stream) {
-    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: grid is NULL");
-    if (n_mu < 0) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_mu < 0");
-    if (n_mu == 0) return QDSE_OK;
-    if ((long long)g->n_ext * ((n_mu + kTileF64 - 1) / kTileF64) > (1LL << 32))
-        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_ext * n_mu too large for one launch");
-    if (!mu || !F_ext || !F_int || !F_out) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: NULL array");
+}  // extern "C"
+
+namespace {
+
+int check_physics(const char* who, int n_mu, const double* mu, double D, double m, double cf,
+                  int vertex) {
     if (vertex != QDSE_VERTEX_BC && vertex != QDSE_VERTEX_RL)
-        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: vertex must be BC or RL");
+        return mu_fail(QDSE_ERR_ARG, "%s: vertex must be BC or RL", who);
     if (!std::isfinite(D) || !std::isfinite(m) || !std::isfinite(cf))
-        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: D, m, cf must be finite");
-    if (!finite_all(mu, n_mu)) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: non-finite mu");
+        return mu_fail(QDSE_ERR_ARG, "%s: D, m, cf must be finite", who);
+    if (!finite_all(mu, n_mu)) return mu_fail(QDSE_ERR_ARG, "%s: non-finite mu", who);
     for (int b = 0; b < n_mu; ++b)
-        if (mu[b] < 0) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: mu must be >= 0");
-    cudaStream_t st = (cudaStream_t)stream;
+        if (mu[b] < 0) return mu_fail(QDSE_ERR_ARG, "%s: mu must be >= 0", who);
+    return QDSE_OK;
+}
+
+// Grows the per-mu workspace of g to n_mu and uploads the chemical potentials.
+int mu_workspace(qdse_mu_grid* g, int n_mu, const double* mu, cudaStream_t st) {
     if (n_mu > g->mu_cap) {
-        // grow the workspace; the stream's earlier work may still read the old one
-        int rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_sweep (grow)");
+        // the stream's earlier work may still read the old buffers
+        int rc = mu_cuda(cudaStreamSynchronize(st), "mu workspace (grow)");
         if (rc != QDSE_OK) return rc;
         if (g->vec) cudaFree(g->vec);
         if (g->mu) cudaFree(g->mu);
@@ -418,9 +549,13 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
         g->mu_cap = n_mu;
     }
     // pageable source: the copy is staged before cudaMemcpyAsync returns
-    int rc = mu_cuda(cudaMemcpyAsync(g->mu, mu, sizeof(double) * n_mu, cudaMemcpyHostToDevice, st),
-                     "cudaMemcpyAsync(mu)");
-    if (rc != QDSE_OK) return rc;
+    return mu_cuda(cudaMemcpyAsync(g->mu, mu, sizeof(double) * n_mu, cudaMemcpyHostToDevice, st),
+                   "cudaMemcpyAsync(mu)");
+}
+
+// prep (from F_int, or interpolated from F_ext when F_int is NULL) + sweep, on stream st.
+int mu_launch(qdse_mu_grid* g, int n_mu, double D, double m, double cf, int vertex,
+              const double* F_ext, const double* F_int, double* F_out, cudaStream_t st) {
     const size_t total = (size_t)n_mu * g->n_int;
     const int prep_blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     const double kappa = cf * D;
@@ -430,7 +565,7 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
         if ((size_t)(3 * g->n_rec + 3) > g->ev.size()) {
             for (int k = 0; k < 3; ++k) {
                 cudaEvent_t e;
-                rc = mu_cuda(cudaEventCreate(&e), "cudaEventCreate");
+                const int rc = mu_cuda(cudaEventCreate(&e), "cudaEventCreate");
                 if (rc != QDSE_OK) return rc;
                 g->ev.push_back(e);
             }
@@ -443,8 +578,13 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
     };
     mark(0);
     if (g->precision == QDSE_FP32) {
-        k_mu_prep<float><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4,
-                                                      F_int, (float*)g->vec);
+        if (F_int)
+            k_mu_prep<float><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
+                                                          g->q4, F_int, (float*)g->vec);
+        else
+            k_mu_prep_interp<float><<<prep_blocks, 256, 0, st>>>(
+                n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4, g->interp, F_ext, g->n_ext,
+                (float*)g->vec);
         mark(1);
         const int n_tiles = (n_mu + kTileF32 - 1) / kTileF32;
         const long long warps = (long long)g->n_ext * n_tiles;
@@ -452,8 +592,13 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
             g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int, g->n_4,
             n_mu, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
     } else {
-        k_mu_prep<double><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
-                                                       g->q4, F_int, (double*)g->vec);
+        if (F_int)
+            k_mu_prep<double><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
+                                                           g->q4, F_int, (double*)g->vec);
+        else
+            k_mu_prep_interp<double><<<prep_blocks, 256, 0, st>>>(
+                n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4, g->interp, F_ext, g->n_ext,
+                (double*)g->vec);
         mark(1);
         const int n_tiles = (n_mu + kTileF64 - 1) / kTileF64;
         const long long warps = (long long)g->n_ext * n_tiles;
@@ -462,7 +607,209 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
             g->n_4, n_mu, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
     }
     mark(2);
-    return mu_cuda(cudaGetLastError(), "qdse_mu_sweep launch");
+    return mu_cuda(cudaGetLastError(), "finite-mu sweep launch");
+}
+
+// Reading M6 on the host: (lower index, weight of the upper node) of x on an ascending axis;
+// held at the first/last node outside it.
+void bracket(const double* axis, int n, double x, int* i, double* w) {
+    const int k = (int)(std::upper_bound(axis, axis + n, x) - axis) - 1;
+    if (k < 0) {
+        *i = 0;
+        *w = 0.0;
+    } else if (k >= n - 1) {
+        *i = n - 1;
+        *w = 0.0;
+    } else {
+        *i = k;
+        *w = (x - axis[k]) / (axis[k + 1] - axis[k]);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double m, double cf,
+                  int vertex, const double* F_ext, const double* F_int, double* F_out,
+                  void* stream) {
+    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: grid is NULL");
+    if (n_mu < 0) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_mu < 0");
+    if (n_mu == 0) return QDSE_OK;
+    if ((long long)g->n_ext * ((n_mu + kTileF64 - 1) / kTileF64) > (1LL << 32))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: n_ext * n_mu too large for one launch");
+    if (!mu || !F_ext || !F_int || !F_out) return mu_fail(QDSE_ERR_ARG, "qdse_mu_sweep: NULL array");
+    int rc = check_physics("qdse_mu_sweep", n_mu, mu, D, m, cf, vertex);
+    if (rc != QDSE_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = mu_workspace(g, n_mu, mu, st);
+    if (rc != QDSE_OK) return rc;
+    return mu_launch(g, n_mu, D, m, cf, vertex, F_ext, F_int, F_out, st);
+}
+
+int qdse_mu_grid_create_product(int n_pr, const double* p_axis, int n_p4, const double* p4_axis,
+                                int n_r, const double* q_abs, int n_4, const double* q4,
+                                const double* w_q, int n_z, const double* z, const double* w_z,
+                                double omega, int precision, void* stream, qdse_mu_grid** out) {
+    if (!out) return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create_product: out is NULL");
+    *out = nullptr;
+    if (n_pr < 1 || n_p4 < 1 || !p_axis || !p4_axis)
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create_product: empty or NULL axis");
+    if ((long long)n_pr * n_p4 > (1LL << 28))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_grid_create_product: n_pr * n_p4 above 2^28");
+    if (!finite_all(p_axis, n_pr) || !finite_all(p4_axis, n_p4) || !(p_axis[0] > 0) ||
+        !(p4_axis[0] > 0) || !increasing(p_axis, n_pr) || !increasing(p4_axis, n_p4))
+        return mu_fail(QDSE_ERR_ARG,
+                       "qdse_mu_grid_create_product: axes must be finite, > 0 and strictly "
+                       "increasing");
+    const int n_ext = n_pr * n_p4;
+    std::vector<double> pa(n_ext), p4a(n_ext);
+    for (int i = 0; i < n_pr; ++i)
+        for (int k = 0; k < n_p4; ++k) {
+            pa[(size_t)i * n_p4 + k] = p_axis[i];
+            p4a[(size_t)i * n_p4 + k] = p4_axis[k];
+        }
+    qdse_mu_grid* g = nullptr;
+    int rc = qdse_mu_grid_create(n_ext, pa.data(), p4a.data(), n_r, q_abs, n_4, q4, w_q, n_z, z,
+                                 w_z, omega, precision, stream, &g);
+    if (rc != QDSE_OK) return rc;
+    std::vector<MuInterp> ip((size_t)n_r * n_4);
+    for (int r = 0; r < n_r; ++r)
+        for (int f = 0; f < n_4; ++f) {
+            int i, k;
+            double a, b;
+            bracket(p_axis, n_pr, q_abs[r], &i, &a);
+            bracket(p4_axis, n_p4, std::fabs(q4[f]), &k, &b);
+            const int i1 = std::min(i + 1, n_pr - 1), k1 = std::min(k + 1, n_p4 - 1);
+            MuInterp& e = ip[(size_t)r * n_4 + f];
+            e.e00 = i * n_p4 + k;
+            e.e10 = i1 * n_p4 + k;
+            e.e01 = i * n_p4 + k1;
+            e.e11 = i1 * n_p4 + k1;
+            e.a = a;
+            e.b = b;
+            e.conj = q4[f] < 0;
+            e.pad = 0;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = mu_cuda(cudaMalloc((void**)&g->interp, sizeof(MuInterp) * ip.size()),
+                 "cudaMalloc(interpolation)");
+    if (rc == QDSE_OK)
+        rc = mu_cuda(cudaMemcpyAsync(g->interp, ip.data(), sizeof(MuInterp) * ip.size(),
+                                     cudaMemcpyHostToDevice, st),
+                     "cudaMemcpyAsync(interpolation)");
+    if (rc == QDSE_OK) rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_grid_create_product");
+    if (rc != QDSE_OK) {
+        qdse_mu_grid_destroy(g);
+        return rc;
+    }
+    g->n_pr = n_pr;
+    g->n_p4 = n_p4;
+    *out = g;
+    return QDSE_OK;
+}
+
+int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double* mu, double D,
+                  double m, double cf, int vertex, double alpha, double tol, double switch_tol,
+                  int max_iter, double* F, int* iters, int* status, void* stream) {
+    const char* who = "qdse_mu_solve";
+    if (!g) return mu_fail(QDSE_ERR_ARG, "%s: grid is NULL", who);
+    if (!g->interp)
+        return mu_fail(QDSE_ERR_ARG, "%s: the grid was not made by qdse_mu_grid_create_product",
+                       who);
+    if (refine && (!refine->interp || refine->n_ext != g->n_ext || refine->n_int != g->n_int ||
+                   refine->fingerprint != g->fingerprint))
+        return mu_fail(QDSE_ERR_ARG, "%s: refine must be a product grid on the same points", who);
+    if (n_mu < 0) return mu_fail(QDSE_ERR_ARG, "%s: n_mu < 0", who);
+    if (n_mu == 0) return QDSE_OK;
+    if ((long long)g->n_ext * ((n_mu + kTileF64 - 1) / kTileF64) > (1LL << 32))
+        return mu_fail(QDSE_ERR_ARG, "%s: n_ext * n_mu too large for one launch", who);
+    if (!mu || !F) return mu_fail(QDSE_ERR_ARG, "%s: NULL array", who);
+    if (!(alpha > 0 && alpha <= 1)) return mu_fail(QDSE_ERR_ARG, "%s: alpha must be in (0, 1]", who);
+    if (!(tol >= 0) || !std::isfinite(tol) || !(switch_tol >= 0) || !std::isfinite(switch_tol))
+        return mu_fail(QDSE_ERR_ARG, "%s: tol and switch_tol must be finite and >= 0", who);
+    if (max_iter < 1) return mu_fail(QDSE_ERR_ARG, "%s: max_iter must be >= 1", who);
+    int rc = check_physics(who, n_mu, mu, D, m, cf, vertex);
+    if (rc != QDSE_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = mu_workspace(g, n_mu, mu, st);
+    if (rc == QDSE_OK && refine) rc = mu_workspace(refine, n_mu, mu, st);
+    if (rc != QDSE_OK) return rc;
+    if (n_mu > g->solve_cap) {
+        rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_solve (grow)");
+        if (rc != QDSE_OK) return rc;
+        for (void* p : {(void*)g->G, (void*)g->change, (void*)g->bad, (void*)g->done})
+            if (p) cudaFree(p);
+        g->G = nullptr;
+        g->change = nullptr;
+        g->bad = g->done = nullptr;
+        g->solve_cap = 0;
+        rc = mu_cuda(cudaMalloc((void**)&g->G, sizeof(double) * 6 * (size_t)g->n_ext * n_mu),
+                     "cudaMalloc(solve workspace)");
+        if (rc == QDSE_OK)
+            rc = mu_cuda(cudaMalloc((void**)&g->change, sizeof(double) * n_mu), "cudaMalloc");
+        if (rc == QDSE_OK) rc = mu_cuda(cudaMalloc((void**)&g->bad, sizeof(int) * n_mu), "cudaMalloc");
+        if (rc == QDSE_OK) rc = mu_cuda(cudaMalloc((void**)&g->done, sizeof(int) * n_mu), "cudaMalloc");
+        if (rc != QDSE_OK) return rc;
+        g->solve_cap = n_mu;
+    }
+    std::vector<int> done(n_mu, 0), bad(n_mu, 0), it_at(n_mu, 0);
+    std::vector<double> change(n_mu, 0.0);
+    // phase 0: sweeps on g (to switch_tol when refining, else to tol); phase 1: sweeps on refine
+    int phase = 0;
+    int it = 0;
+    while (it < max_iter) {
+        ++it;
+        qdse_mu_grid* s = phase == 0 ? g : refine;
+        rc = mu_cuda(cudaMemcpyAsync(g->done, done.data(), sizeof(int) * n_mu,
+                                     cudaMemcpyHostToDevice, st),
+                     "cudaMemcpyAsync(done)");
+        if (rc == QDSE_OK) rc = mu_launch(s, n_mu, D, m, cf, vertex, F, nullptr, g->G, st);
+        if (rc != QDSE_OK) return rc;
+        k_mu_relax<<<n_mu, kRelaxThreads, 0, st>>>(g->n_ext, alpha, F, g->G, g->done, g->change,
+                                                   g->bad);
+        rc = mu_cuda(cudaGetLastError(), "k_mu_relax launch");
+        if (rc == QDSE_OK)
+            rc = mu_cuda(cudaMemcpyAsync(change.data(), g->change, sizeof(double) * n_mu,
+                                         cudaMemcpyDeviceToHost, st),
+                         "cudaMemcpyAsync(change)");
+        std::vector<int> bad_now(n_mu, 0);
+        if (rc == QDSE_OK)
+            rc = mu_cuda(cudaMemcpyAsync(bad_now.data(), g->bad, sizeof(int) * n_mu,
+                                         cudaMemcpyDeviceToHost, st),
+                         "cudaMemcpyAsync(bad)");
+        if (rc == QDSE_OK) rc = mu_cuda(cudaStreamSynchronize(st), who);
+        if (rc != QDSE_OK) return rc;
+        const bool final_phase = refine == nullptr || phase == 1;
+        const double goal = final_phase ? tol : std::max(tol, switch_tol);
+        bool all_done = true, all_switch = true;
+        for (int b = 0; b < n_mu; ++b) {
+            if (done[b]) continue;
+            if (bad_now[b]) {
+                bad[b] = 1;
+                done[b] = 1;  // frozen from here on
+                continue;
+            }
+            if (change[b] < goal) {
+                if (final_phase) {
+                    done[b] = 1;
+                    it_at[b] = it;
+                    continue;
+                }
+            } else {
+                all_switch = false;
+            }
+            all_done = false;
+        }
+        if (all_done) break;
+        if (!final_phase && all_switch) phase = 1;
+    }
+    for (int b = 0; b < n_mu; ++b) {
+        if (iters) iters[b] = done[b] && !bad[b] ? it_at[b] : it;
+        if (status)
+            status[b] = bad[b] ? QDSE_ERR_NONFINITE : done[b] ? QDSE_OK : QDSE_ERR_NOT_CONVERGED;
+    }
+    return QDSE_OK;
 }
 
 int qdse_mu_set_profiling(qdse_mu_grid* g, int on) {

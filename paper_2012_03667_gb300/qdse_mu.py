@@ -14,8 +14,9 @@ import numpy as np
 
 from . import qdse as Q
 
-EXPORTS = ("qdse_mu_grid_create", "qdse_mu_grid_info", "qdse_mu_sweep", "qdse_mu_set_profiling",
-           "qdse_mu_profile", "qdse_mu_grid_destroy", "qdse_mu_last_error")
+EXPORTS = ("qdse_mu_grid_create", "qdse_mu_grid_create_product", "qdse_mu_solve",
+           "qdse_mu_grid_info", "qdse_mu_sweep", "qdse_mu_set_profiling", "qdse_mu_profile",
+           "qdse_mu_grid_destroy", "qdse_mu_last_error")
 
 _lib = None
 
@@ -30,6 +31,9 @@ def load_library() -> ctypes.CDLL:
     sig = {
         "qdse_mu_grid_create": (ip, [ip, vp, vp, ip, vp, ip, vp, vp, ip, vp, vp, dp, ip, vp,
                                      P(vp)]),
+        "qdse_mu_grid_create_product": (ip, [ip, vp, ip, vp, ip, vp, ip, vp, vp, ip, vp, vp, dp,
+                                             ip, vp, P(vp)]),
+        "qdse_mu_solve": (ip, [vp, vp, ip, vp, dp, dp, dp, ip, dp, dp, dp, ip, vp, vp, vp, vp]),
         "qdse_mu_grid_info": (ip, [vp, llp, llp]),
         "qdse_mu_sweep": (ip, [vp, ip, vp, dp, dp, dp, ip, vp, vp, vp, vp]),
         "qdse_mu_set_profiling": (ip, [vp, ip]),
@@ -54,23 +58,50 @@ class MuGrid:
     (q_abs x q4 with weights w_q, row-major [r][f]), the angular rule and omega."""
 
     def __init__(self, p_abs, p4, q_abs, q4, w_q, z, w_z, omega: float,
-                 precision: int = Q.QDSE_FP64):
+                 precision: int = Q.QDSE_FP64, product: bool = False):
+        """product=False: p_abs, p4 are the external points [n_ext] (qdse_mu_grid_create).
+        product=True: they are the axes [n_pr], [n_p4] of the external product grid
+        (qdse_mu_grid_create_product), which qdse_mu_solve needs."""
         self.lib = load_library()
         arrs = [_host(a) for a in (p_abs, p4, q_abs, q4, w_q, z, w_z)]
         self._keep = arrs
         p_abs, p4, q_abs, q4, w_q, z, w_z = arrs
-        self.n_ext, self.n_r, self.n_4 = len(p_abs), len(q_abs), len(q4)
+        self.n_r, self.n_4 = len(q_abs), len(q4)
         self.n_int = self.n_r * self.n_4
-        assert len(p4) == self.n_ext and w_q.size == self.n_int and len(w_z) == len(z)
+        self.n_ext = len(p_abs) * len(p4) if product else len(p_abs)
+        assert (product or len(p4) == self.n_ext) and w_q.size == self.n_int
+        assert len(w_z) == len(z)
         self.precision = precision
         self.ptr = ctypes.c_void_p()
-        st = self.lib.qdse_mu_grid_create(self.n_ext, p_abs.ctypes.data, p4.ctypes.data, self.n_r,
-                                          q_abs.ctypes.data, self.n_4, q4.ctypes.data,
-                                          w_q.ctypes.data, len(z), z.ctypes.data, w_z.ctypes.data,
-                                          float(omega), precision, Q._current_stream(),
-                                          ctypes.byref(self.ptr))
+        tail = (self.n_r, q_abs.ctypes.data, self.n_4, q4.ctypes.data, w_q.ctypes.data, len(z),
+                z.ctypes.data, w_z.ctypes.data, float(omega), precision, Q._current_stream(),
+                ctypes.byref(self.ptr))
+        if product:
+            st = self.lib.qdse_mu_grid_create_product(len(p_abs), p_abs.ctypes.data, len(p4),
+                                                      p4.ctypes.data, *tail)
+        else:
+            st = self.lib.qdse_mu_grid_create(self.n_ext, p_abs.ctypes.data, p4.ctypes.data, *tail)
         if st != Q.QDSE_OK:
             raise Q.QdseError(st, self.lib.qdse_mu_last_error().decode())
+
+    def solve(self, mu: Sequence[float], D: float, m: float, F, alpha: float = 1.0,
+              tol: float = 1e-10, max_iter: int = 500, vertex: int = Q.QDSE_VERTEX_BC,
+              cf: float = 4.0 / 3.0, refine: "MuGrid" = None, switch_tol: float = 1e-5):
+        """qdse_mu_solve: F (torch.complex128 CUDA [n_mu, 3, n_ext]) holds the start and receives
+        the result.  Returns (iters, status) as numpy int32 arrays."""
+        import torch
+        mu = _host(mu)
+        n_mu = len(mu)
+        assert F.is_cuda and F.dtype == torch.complex128 and F.is_contiguous()
+        assert tuple(F.shape) == (n_mu, 3, self.n_ext)
+        iters = np.zeros(n_mu, dtype=np.int32)
+        status = np.zeros(n_mu, dtype=np.int32)
+        self._raise(self.lib.qdse_mu_solve(self.ptr, refine.ptr if refine is not None else None,
+                                           n_mu, mu.ctypes.data, float(D), float(m), float(cf),
+                                           vertex, float(alpha), float(tol), float(switch_tol),
+                                           int(max_iter), F.data_ptr(), iters.ctypes.data,
+                                           status.ctypes.data, Q._current_stream()))
+        return iters, status
 
     def info(self) -> dict:
         n, b = ctypes.c_longlong(), ctypes.c_longlong()

@@ -128,3 +128,27 @@ def test_null_context_is_rejected(lib):
     assert lib.qdse_solve(None, None, None, None, None, None) == Q.QDSE_ERR_ARG
     assert lib.qdse_sizes(None, None, None) == Q.QDSE_ERR_ARG
     lib.qdse_destroy(None)  # accepted
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(p_axis=(0.5, 0.2)), "axes"),
+    (dict(p_axis=(0.0, 0.2)), "axes"),
+    (dict(p4_axis=(-0.1, 0.3)), "axes"),
+    (dict(n_pr=0), "axis"),
+])
+def test_mu_product_grid_and_solve_reject_bad_arguments_on_the_host(lib, kw, msg):
+    QM.load_library()
+    dp = ctypes.c_double
+    arr = lambda xs: (dp * len(xs))(*xs)
+    a = dict(n_pr=2, p_axis=(0.2, 0.5), p4_axis=(0.1, 0.4))
+    a.update(kw)
+    q_abs, q4 = arr([0.3, 0.6]), arr([-0.2, 0.2])
+    p = ctypes.c_void_p()
+    st = lib.qdse_mu_grid_create_product(a["n_pr"], arr(a["p_axis"]), len(a["p4_axis"]),
+                                         arr(a["p4_axis"]), 2, q_abs, 2, q4, arr([1.0] * 4), 2,
+                                         arr([-0.5, 0.5]), arr([1.0, 1.0]), 0.5, Q.QDSE_FP64,
+                                         None, ctypes.byref(p))
+    assert st == Q.QDSE_ERR_ARG and not p
+    assert msg in lib.qdse_mu_last_error().decode()
+    assert lib.qdse_mu_solve(None, None, 1, None, 1.0, 0.0, 1.0, 0, 1.0, 1e-10, 1e-5, 10, None,
+                             None, None, None) == Q.QDSE_ERR_ARG

@@ -121,3 +121,93 @@ def test_mu_full_size_sampled_against_oracle(QM, precision, tol):
         scale = np.abs(ref - x0).max(axis=1)
         err = (np.abs(got[b][:, idx] - ref).max(axis=1) / scale).max()
         assert err < tol, (b, err)
+
+
+# ---- the solve (interpolation + successive approximation) --------------------------------------
+SOLVE = dict(n_r=12, n_4=8, n_z=24, n_mu=3)
+
+
+def _solve_setup(QM, precision, D=None):
+    w = I.mu_workload(**SOLVE)
+    pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
+    g = QM.MuGrid(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, precision, product=True)
+    start = np.array([np.ones(len(w.p_abs)), np.ones(len(w.p_abs)),
+                      0.3 * np.ones(len(w.p_abs))], dtype=np.complex128)
+    return w, pa, p4a, g, start
+
+
+def _oracle_solve(w, pa, p4a, D, mu, start, **kw):
+    return OM.solve(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, D, w.omega, w.m, mu, start, **kw)
+
+
+def test_mu_solve_reaches_the_oracle_fixed_point_rainbow(QM):
+    """FP64 solve of three chemical potentials at once (rainbow vertex, D = 0.93) against the
+    oracle's solve: same fixed point to 1e-10 of max |F - x0|, same sweep count within one."""
+    w, pa, p4a, g, start = _solve_setup(QM, 0)
+    mu_list = [0.0, 0.1, 0.3]
+    F = torch.from_numpy(np.stack([start] * 3)).cuda()
+    iters, status = g.solve(mu_list, w.D, w.m, F, tol=1e-12, max_iter=200, vertex=1)
+    assert list(status) == [0, 0, 0]
+    got = F.cpu().numpy()
+    x0 = np.array([1.0, 1.0, w.m])[:, None]
+    for b, mu in enumerate(mu_list):
+        ref, it, ok = _oracle_solve(w, pa, p4a, w.D, mu, start, tol=1e-12, max_iter=200,
+                                    vertex=OM.RL)
+        assert ok and abs(int(iters[b]) - it) <= 1
+        err = (np.abs(got[b] - ref).max(axis=1) / np.abs(ref - x0).max(axis=1)).max()
+        assert err < 1e-10, (mu, err)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+def test_mu_solve_iterates_match_the_oracle_bc(QM, alpha):
+    """Ball-Chiu vertex (D = 0.5, where the iteration contracts), exactly 15 sweeps (tol = 0) of
+    two chemical potentials, damped and undamped: every element against the oracle to 1e-11."""
+    w, pa, p4a, g, start = _solve_setup(QM, 0)
+    D = 0.5
+    mu_list = [0.05, 0.25]
+    F = torch.from_numpy(np.stack([start] * 2)).cuda()
+    iters, status = g.solve(mu_list, D, w.m, F, alpha=alpha, tol=0.0, max_iter=15, vertex=0)
+    assert list(status) == [QM.Q.QDSE_ERR_NOT_CONVERGED] * 2 and list(iters) == [15, 15]
+    got = F.cpu().numpy()
+    x0 = np.array([1.0, 1.0, w.m])[:, None]
+    for b, mu in enumerate(mu_list):
+        ref, _, _ = _oracle_solve(w, pa, p4a, D, mu, start, tol=0.0, max_iter=15, vertex=OM.BC,
+                                  alpha=alpha)
+        err = (np.abs(got[b] - ref).max(axis=1) / np.abs(ref - x0).max(axis=1)).max()
+        assert err < 1e-11, (mu, err)
+
+
+def test_mu_mixed_solve_reaches_the_fp64_fixed_point(QM):
+    """FP32 sweeps to a change of 1e-5, then FP64 sweeps on a grid of the same points to 1e-12:
+    the result is the FP64 solve's fixed point to 1e-9."""
+    w, pa, p4a, g64, start = _solve_setup(QM, 0)
+    g32 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, 3, product=True)
+    mu_list = [0.1, 0.3]
+    F64 = torch.from_numpy(np.stack([start] * 2)).cuda()
+    it64, st64 = g64.solve(mu_list, 0.5, w.m, F64, tol=1e-12, max_iter=400, vertex=0)
+    Fm = torch.from_numpy(np.stack([start] * 2)).cuda()
+    itm, stm = g32.solve(mu_list, 0.5, w.m, Fm, tol=1e-12, max_iter=400, vertex=0, refine=g64,
+                         switch_tol=1e-5)
+    assert list(st64) == [0, 0] and list(stm) == [0, 0]
+    a, b = F64.cpu().numpy(), Fm.cpu().numpy()
+    x0 = np.array([1.0, 1.0, w.m])[None, :, None]
+    assert (np.abs(a - b).max(axis=2) / np.abs(a - x0).max(axis=2)).max() < 1e-9
+
+
+def test_mu_solve_reports_non_convergence_and_non_finite_values(QM):
+    """A start holding NaN at one chemical potential gives QDSE_ERR_NONFINITE there and leaves the
+    other one unaffected; a sweep budget too small gives QDSE_ERR_NOT_CONVERGED; a grid made
+    without the product form is refused."""
+    w, pa, p4a, g, start = _solve_setup(QM, 0)
+    bad = start.copy()
+    bad[0, 3] = np.nan
+    F = torch.from_numpy(np.stack([start, bad])).cuda()
+    iters, status = g.solve([0.1, 0.1], w.D, w.m, F, tol=1e-12, max_iter=200, vertex=1)
+    assert list(status) == [0, QM.Q.QDSE_ERR_NONFINITE]
+    assert np.isfinite(F[0].cpu().numpy()).all()
+    F = torch.from_numpy(np.stack([start])).cuda()
+    iters, status = g.solve([0.1], w.D, w.m, F, tol=1e-12, max_iter=3, vertex=1)
+    assert list(status) == [QM.Q.QDSE_ERR_NOT_CONVERGED] and list(iters) == [3]
+    flat = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, 0)
+    with pytest.raises(QM.Q.QdseError):
+        flat.solve([0.1], w.D, w.m, F)

@@ -177,3 +177,44 @@ def test_result_depends_on_mu_only_through_p_tilde_squared(vertex):
     assert np.abs(res[:, 0] - res[0, 0]).max() < tol
     assert np.abs(res[:, 1] - res[:, 0]).max() < tol
     assert np.abs(res[:, 2] - res[0, 2]).max() < tol
+
+
+def test_interpolation_is_exact_for_bilinear_functions_held_outside_and_mirrored():
+    """Reading M6: linear in |p| and in p_4 between bracketing external nodes (so any function
+    a + b|p| + c p_4 + d |p| p_4 is reproduced exactly inside the grid), held at the last node
+    beyond it, and conjugated for q_4 < 0."""
+    pa = np.array([0.1, 0.5, 1.0, 2.0])
+    p4a = np.array([0.05, 0.4, 1.5])
+    PR, P4 = np.meshgrid(pa, p4a, indexing="ij")
+
+    def f(x, y):
+        return (1 + 2j) + (0.3 - 0.1j) * x + (0.2 + 0.5j) * y + 0.7j * x * y
+
+    F = np.array([f(PR, P4).ravel(), 2 * f(PR, P4).ravel(), -f(PR, P4).ravel()])
+    qa = np.array([0.1, 0.2, 0.7, 1.9, 3.0])
+    q4 = np.array([-1.0, -0.1, 0.05, 0.2, 1.2, 2.0])
+    out = OM.interpolate(pa, p4a, F, qa, q4).reshape(3, len(qa), len(q4))
+    for r, Q in enumerate(qa):
+        for k, x4 in enumerate(q4):
+            want = f(min(Q, 2.0), min(abs(x4), 1.5))
+            want = np.conj(want) if x4 < 0 else want
+            np.testing.assert_allclose(out[:, r, k], [want, 2 * want, -want], rtol=0, atol=1e-14)
+
+
+def test_solve_reaches_a_fixed_point_of_the_sweep():
+    """The solve (rainbow vertex, mu = 0.1, a coarse staggered grid) stops at a point where one
+    more sweep moves every function by less than its tolerance, in the same number of steps from
+    a damped iteration's limit; tol = 0 runs exactly max_iter steps."""
+    from paper_2012_03667_gb300 import inputs as I
+    w = I.mu_workload(n_r=12, n_4=8, n_z=24, n_mu=1)
+    pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
+    F0 = np.array([np.ones(len(w.p_abs)), np.ones(len(w.p_abs)), 0.3 * np.ones(len(w.p_abs))])
+    args = (pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.D, w.omega, w.m, 0.1)
+    F, it, ok = OM.solve(*args, F0, tol=1e-11, max_iter=200, vertex=OM.RL)
+    assert ok and 10 < it < 100
+    G, _, _ = OM.solve(*args, F, tol=0.0, max_iter=1, vertex=OM.RL)
+    for c in range(3):
+        assert np.abs(G[c] - F[c]).max() < 1e-10 * np.abs(F[c]).max()
+    Fd, itd, okd = OM.solve(*args, F0, tol=1e-11, max_iter=400, vertex=OM.RL, alpha=0.7)
+    assert okd and np.abs(Fd - F).max() < 1e-9 * np.abs(F).max()
+    assert abs(F[0][0].imag) > 1e-4  # mu > 0: genuinely complex
