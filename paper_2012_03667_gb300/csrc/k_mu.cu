@@ -143,16 +143,20 @@ __device__ __forceinline__ void prep_store(qmu::cx<double> A, qmu::cx<double> Cc
 }
 
 // As k_mu_prep, with A, C, B at the internal points interpolated from the external values.
+// list: NULL, or the chemical potentials to prepare (compact slot cb holds list[cb]); vec is
+// indexed by slot.
 template <class T>
-__global__ void k_mu_prep_interp(int n_mu, const double* __restrict__ mu, int n_int, int n_4,
+__global__ void k_mu_prep_interp(int n_act, const int* __restrict__ list,
+                                 const double* __restrict__ mu, int n_int, int n_4,
                                  const double* __restrict__ qr, const double* __restrict__ q4,
                                  const MuInterp* __restrict__ interp,
                                  const double* __restrict__ F_ext, int n_ext, T* __restrict__ vec) {
     using C = qmu::cx<double>;
-    const size_t total = (size_t)n_mu * n_int;
+    const size_t total = (size_t)n_act * n_int;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(t / n_int), j = (int)(t % n_int);
+        const int cb = (int)(t / n_int), j = (int)(t % n_int);
+        const int b = list ? list[cb] : cb;
         const MuInterp ip = interp[j];
         const double w00 = (1.0 - ip.a) * (1.0 - ip.b), w10 = ip.a * (1.0 - ip.b);
         const double w01 = (1.0 - ip.a) * ip.b, w11 = ip.a * ip.b;
@@ -251,9 +255,11 @@ template <class T, int TB, int MINB>
 __global__ void __launch_bounds__(kSweepThreads, MINB)
 k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
            const double* __restrict__ q4, const T* __restrict__ table, const T* __restrict__ vec,
-           int n_int, int n_4, int n_mu, int n_tiles, const double* __restrict__ mu,
-           const double* __restrict__ F_ext, int n_ext, double kappa, double m_cur, int bc,
-           double* __restrict__ F_out) {
+           int n_int, int n_4, int n_mu, const int* __restrict__ list, int n_tiles,
+           const double* __restrict__ mu, const double* __restrict__ F_ext, int n_ext,
+           double kappa, double m_cur, int bc, double* __restrict__ F_out) {
+    // n_mu slots; slot cb is chemical potential list[cb] (cb itself when list is NULL): F_ext,
+    // F_out and mu are indexed by the chemical potential, vec by the slot.
     using C = qmu::cx<T>;
     constexpr int kW = kSweepThreads / 32;
     __shared__ T ext[kW][TB][7];  // A, C, B at the external point and mu, per slot of the tile
@@ -264,7 +270,8 @@ k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
     const int nb = min(TB, n_mu - b0);
     const MuRow row = rows[e];
     if (lane < TB) {
-        const int b = b0 + (lane < nb ? lane : 0);
+        const int cb = b0 + (lane < nb ? lane : 0);
+        const int b = list ? list[cb] : cb;
         const double* Fb = F_ext + (size_t)b * 6 * n_ext;
         T* d = ext[wib][lane];
         d[0] = T(Fb[2 * e]);
@@ -312,7 +319,7 @@ k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
             for (int o = 16; o > 0; o >>= 1) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
         }
         if (lane == t && t < nb) {
-            const int b = b0 + t;
+            const int b = list ? list[b0 + t] : b0 + t;
             const double sa_re = kappa * (double)y[0], sa_im = kappa * (double)y[1];
             const double sc_re = kappa * (double)y[2], sc_im = kappa * (double)y[3];
             const double sb_re = kappa * (double)y[4], sb_im = kappa * (double)y[5];
@@ -362,7 +369,9 @@ struct qdse_mu_grid {
     double* G = nullptr;
     double* change = nullptr;
     int *bad = nullptr, *done = nullptr;
-    int solve_cap = 0;
+    int solve_cap = 0;     // capacity (chemical potentials) of G, change, bad, done
+    int* list = nullptr;  // chemical potentials this grid sweeps in the current step
+    int list_cap = 0;
     // profiling: event triples (before prep, between, after sweep) of unread calls
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
@@ -377,7 +386,7 @@ void qdse_mu_grid_destroy(qdse_mu_grid* g) {
     if (!g) return;
     for (void* p : {(void*)g->rows, (void*)g->qr, (void*)g->q4, (void*)g->wq, (void*)g->z,
                     (void*)g->wz, g->table, g->vec, (void*)g->mu, (void*)g->interp, (void*)g->G,
-                    (void*)g->change, (void*)g->bad, (void*)g->done})
+                    (void*)g->change, (void*)g->bad, (void*)g->done, (void*)g->list})
         if (p) cudaFree(p);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;
@@ -554,8 +563,10 @@ int mu_workspace(qdse_mu_grid* g, int n_mu, const double* mu, cudaStream_t st) {
 }
 
 // prep (from F_int, or interpolated from F_ext when F_int is NULL) + sweep, on stream st.
-int mu_launch(qdse_mu_grid* g, int n_mu, double D, double m, double cf, int vertex,
-              const double* F_ext, const double* F_int, double* F_out, cudaStream_t st) {
+// list: NULL (chemical potentials 0 .. n_mu-1) or device int[n_mu] (interpolated prep only).
+int mu_launch(qdse_mu_grid* g, int n_mu, const int* list, double D, double m, double cf,
+              int vertex, const double* F_ext, const double* F_int, double* F_out,
+              cudaStream_t st) {
     const size_t total = (size_t)n_mu * g->n_int;
     const int prep_blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     const double kappa = cf * D;
@@ -583,28 +594,28 @@ int mu_launch(qdse_mu_grid* g, int n_mu, double D, double m, double cf, int vert
                                                           g->q4, F_int, (float*)g->vec);
         else
             k_mu_prep_interp<float><<<prep_blocks, 256, 0, st>>>(
-                n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4, g->interp, F_ext, g->n_ext,
+                n_mu, list, g->mu, g->n_int, g->n_4, g->qr, g->q4, g->interp, F_ext, g->n_ext,
                 (float*)g->vec);
         mark(1);
         const int n_tiles = (n_mu + kTileF32 - 1) / kTileF32;
         const long long warps = (long long)g->n_ext * n_tiles;
         k_mu_sweep<float, kTileF32, 4><<<(unsigned)((warps + 3) / 4), kSweepThreads, 0, st>>>(
             g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int, g->n_4,
-            n_mu, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+            n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
     } else {
         if (F_int)
             k_mu_prep<double><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
                                                            g->q4, F_int, (double*)g->vec);
         else
             k_mu_prep_interp<double><<<prep_blocks, 256, 0, st>>>(
-                n_mu, g->mu, g->n_int, g->n_4, g->qr, g->q4, g->interp, F_ext, g->n_ext,
+                n_mu, list, g->mu, g->n_int, g->n_4, g->qr, g->q4, g->interp, F_ext, g->n_ext,
                 (double*)g->vec);
         mark(1);
         const int n_tiles = (n_mu + kTileF64 - 1) / kTileF64;
         const long long warps = (long long)g->n_ext * n_tiles;
         k_mu_sweep<double, kTileF64, 2><<<(unsigned)((warps + 3) / 4), kSweepThreads, 0, st>>>(
             g->rows, g->qr, g->q4, (const double*)g->table, (const double*)g->vec, g->n_int,
-            g->n_4, n_mu, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+            g->n_4, n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
     }
     mark(2);
     return mu_cuda(cudaGetLastError(), "finite-mu sweep launch");
@@ -644,7 +655,7 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
     cudaStream_t st = (cudaStream_t)stream;
     rc = mu_workspace(g, n_mu, mu, st);
     if (rc != QDSE_OK) return rc;
-    return mu_launch(g, n_mu, D, m, cf, vertex, F_ext, F_int, F_out, st);
+    return mu_launch(g, n_mu, nullptr, D, m, cf, vertex, F_ext, F_int, F_out, st);
 }
 
 int qdse_mu_grid_create_product(int n_pr, const double* p_axis, int n_p4, const double* p4_axis,
@@ -735,6 +746,21 @@ int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double*
     rc = mu_workspace(g, n_mu, mu, st);
     if (rc == QDSE_OK && refine) rc = mu_workspace(refine, n_mu, mu, st);
     if (rc != QDSE_OK) return rc;
+    // the stream's earlier work may still read the buffers about to be replaced
+    auto grow_list = [&](qdse_mu_grid* x) -> int {
+        if (n_mu <= x->list_cap) return QDSE_OK;
+        int r = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_solve (grow)");
+        if (r != QDSE_OK) return r;
+        if (x->list) cudaFree(x->list);
+        x->list = nullptr;
+        x->list_cap = 0;
+        r = mu_cuda(cudaMalloc((void**)&x->list, sizeof(int) * n_mu), "cudaMalloc(list)");
+        if (r == QDSE_OK) x->list_cap = n_mu;
+        return r;
+    };
+    rc = grow_list(g);
+    if (rc == QDSE_OK && refine) rc = grow_list(refine);
+    if (rc != QDSE_OK) return rc;
     if (n_mu > g->solve_cap) {
         rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_solve (grow)");
         if (rc != QDSE_OK) return rc;
@@ -753,18 +779,38 @@ int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double*
         if (rc != QDSE_OK) return rc;
         g->solve_cap = n_mu;
     }
-    std::vector<int> done(n_mu, 0), bad(n_mu, 0), it_at(n_mu, 0);
+    std::vector<int> done(n_mu, 0), bad(n_mu, 0), it_at(n_mu, 0), phase(n_mu, 0);
+    std::vector<int> bad_now(n_mu, 0), list0, list1;
     std::vector<double> change(n_mu, 0.0);
-    // phase 0: sweeps on g (to switch_tol when refining, else to tol); phase 1: sweeps on refine
-    int phase = 0;
+    // per chemical potential: phase 0 sweeps on g (to switch_tol when refining, else to tol),
+    // phase 1 sweeps on refine (to tol); converged or non-finite ones are no longer swept
     int it = 0;
     while (it < max_iter) {
         ++it;
-        qdse_mu_grid* s = phase == 0 ? g : refine;
+        list0.clear();
+        list1.clear();
+        for (int b = 0; b < n_mu; ++b)
+            if (!done[b]) (phase[b] == 0 ? list0 : list1).push_back(b);
+        if (list0.empty() && list1.empty()) break;
         rc = mu_cuda(cudaMemcpyAsync(g->done, done.data(), sizeof(int) * n_mu,
                                      cudaMemcpyHostToDevice, st),
                      "cudaMemcpyAsync(done)");
-        if (rc == QDSE_OK) rc = mu_launch(s, n_mu, D, m, cf, vertex, F, nullptr, g->G, st);
+        if (rc == QDSE_OK && !list0.empty()) {
+            rc = mu_cuda(cudaMemcpyAsync(g->list, list0.data(), sizeof(int) * list0.size(),
+                                         cudaMemcpyHostToDevice, st),
+                         "cudaMemcpyAsync(list)");
+            if (rc == QDSE_OK)
+                rc = mu_launch(g, (int)list0.size(), g->list, D, m, cf, vertex, F, nullptr, g->G,
+                               st);
+        }
+        if (rc == QDSE_OK && !list1.empty()) {
+            rc = mu_cuda(cudaMemcpyAsync(refine->list, list1.data(), sizeof(int) * list1.size(),
+                                         cudaMemcpyHostToDevice, st),
+                         "cudaMemcpyAsync(list)");
+            if (rc == QDSE_OK)
+                rc = mu_launch(refine, (int)list1.size(), refine->list, D, m, cf, vertex, F,
+                               nullptr, g->G, st);
+        }
         if (rc != QDSE_OK) return rc;
         k_mu_relax<<<n_mu, kRelaxThreads, 0, st>>>(g->n_ext, alpha, F, g->G, g->done, g->change,
                                                    g->bad);
@@ -773,36 +819,24 @@ int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double*
             rc = mu_cuda(cudaMemcpyAsync(change.data(), g->change, sizeof(double) * n_mu,
                                          cudaMemcpyDeviceToHost, st),
                          "cudaMemcpyAsync(change)");
-        std::vector<int> bad_now(n_mu, 0);
         if (rc == QDSE_OK)
             rc = mu_cuda(cudaMemcpyAsync(bad_now.data(), g->bad, sizeof(int) * n_mu,
                                          cudaMemcpyDeviceToHost, st),
                          "cudaMemcpyAsync(bad)");
         if (rc == QDSE_OK) rc = mu_cuda(cudaStreamSynchronize(st), who);
         if (rc != QDSE_OK) return rc;
-        const bool final_phase = refine == nullptr || phase == 1;
-        const double goal = final_phase ? tol : std::max(tol, switch_tol);
-        bool all_done = true, all_switch = true;
         for (int b = 0; b < n_mu; ++b) {
             if (done[b]) continue;
             if (bad_now[b]) {
                 bad[b] = 1;
                 done[b] = 1;  // frozen from here on
-                continue;
+            } else if (refine && phase[b] == 0) {
+                if (change[b] < std::max(tol, switch_tol)) phase[b] = 1;
+            } else if (change[b] < tol) {
+                done[b] = 1;
+                it_at[b] = it;
             }
-            if (change[b] < goal) {
-                if (final_phase) {
-                    done[b] = 1;
-                    it_at[b] = it;
-                    continue;
-                }
-            } else {
-                all_switch = false;
-            }
-            all_done = false;
         }
-        if (all_done) break;
-        if (!final_phase && all_switch) phase = 1;
     }
     for (int b = 0; b < n_mu; ++b) {
         if (iters) iters[b] = done[b] && !bad[b] ? it_at[b] : it;
