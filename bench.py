@@ -36,7 +36,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scan",
-                    choices=["scan", "large", "small", "adjoint", "mu", "mu-small", "mu-solve"],
+                    choices=["scan", "large", "small", "adjoint", "mu", "mu-small", "mu-solve",
+                             "table1"],
                     help="adjoint: 1024 scan instances at N_q = 256, N_theta = 64; one step = "
                          "forward solve + condensate gradient w.r.t. (m, D, w, mu) by the adjoint")
     ap.add_argument("--n-inst", type=int, default=4096)
@@ -388,6 +389,100 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------------
+# Table 1 of Sec. IV: N = 150 radial points, M = 100 angular nodes, xi = 0.005, the paper's
+# interaction D = 0.55, omega = 0.678 (Intel Core i7 at 1.00 GHz, GCC 9.3.0, 11 iterations).
+TABLE1 = dict(n=150, n_theta=100, tol=0.005, D=0.55, omega=0.678, m=0.005)
+TABLE1_PAPER = {"1 traditional, serial": {"cpu_s": 65, "cpu_pct": 100.0},
+                "2 modified, serial": {"cpu_s": 6, "cpu_pct": 100.0},
+                "3 traditional, parallel": {"cpu_s": 9, "cpu_pct": 782.0},
+                "4 modified, parallel": {"cpu_s": 1, "cpu_pct": 792.0}}
+
+
+def run_table1(args):
+    """Table 1 of Sec. IV on this machine.  --impl reference: the paper's four CPU algorithms
+    (traditional or modified interpolation, serial or OpenMP over the external index on every
+    host core) by the FP64 oracle on the staggered grid, to the relative change xi = 0.005 (R7);
+    the value is algorithm 4's time.  --impl ours: the GPU solver on the same problem, plain FP64
+    sweeps to the same xi and mixed precision to 1e-10 (times from CUDA events)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t = TABLE1
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if args.impl == "reference":
+        from oracle import oracle as O
+        O.build()
+        algs = {}
+        for name, mode, nt in (("1 traditional, serial", O.STAGGERED_TRADITIONAL, 1),
+                               ("2 modified, serial", O.STAGGERED, 1),
+                               ("3 traditional, parallel", O.STAGGERED_TRADITIONAL, cores),
+                               ("4 modified, parallel", O.STAGGERED, cores)):
+            pr = O.Problem(n=t["n"], n_theta=t["n_theta"], grid_mode=mode, D=t["D"],
+                           omega=t["omega"], m=t["m"])
+            w0, c0 = time.perf_counter(), time.process_time()
+            A, B, it, ch, st = O.solve(pr, tol=t["tol"], max_iter=1000, nthreads=nt)
+            wall, cpu = time.perf_counter() - w0, time.process_time() - c0
+            algs[name] = {"wall_s": wall, "cpu_pct": 100.0 * cpu / wall, "threads": nt,
+                          "iterations": it, "status": st, "A0": A[0], "M0": B[0] / A[0]}
+        v = algs["4 modified, parallel"]["wall_s"]
+        line = {"metric": "Table 1 solve time (Sec. IV)", "value": v, "unit": "s",
+                "n_gpus": 0, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * v,
+                "higher_is_better": False, "scaling": "none", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": "Table 1: N = 150, M = 100 (Gauss-Chebyshev), xi = 0.005 "
+                                       "relative change, D = 0.55, omega = 0.678, m = 0.005, "
+                                       "staggered grid on [1e-4, 1e4] GeV^2"},
+                "algorithms": algs, "cores": cores, "paper": TABLE1_PAPER,
+                "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                                 "sample": "the whole Table 1 problem, algorithm 4"},
+                "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_03667_gb300 import qdse as Q
+    grid = Q.Grid(t["n"], t["n_theta"], 1e-4, 1e4, Q.QDSE_STAGGERED)
+    prm = [[t["D"], t["omega"], t["m"], 0.0]]
+    out = {}
+    for name, prec, tol in (("fp64 sweeps to xi", Q.QDSE_FP64, t["tol"]),
+                            ("mixed to 1e-10", Q.QDSE_MIXED, 1e-10)):
+        ctx = Q.Context(grid, 1, precision=prec, tol=tol)
+        A = torch.ones(t["n"], dtype=torch.float64, device="cuda")
+        B = torch.full((t["n"],), 0.3, dtype=torch.float64, device="cuda")
+        it = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        times = []
+        for rep in range(args.warmup + args.steps):
+            A.fill_(1.0)
+            B.fill_(0.3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            ctx.qdse_solve(prm, A, B, it, st)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        out[name] = {"s": float(np.median(times)), "iterations": int(it.item()),
+                     "status": int(st.item()), "A0": float(A[0].item()),
+                     "M0": float((B[0] / A[0]).item())}
+        ctx.close()
+    v = out["fp64 sweeps to xi"]["s"]
+    line = {"metric": "Table 1 solve time (Sec. IV)", "value": v, "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v,
+            "higher_is_better": False, "scaling": "none", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "Table 1: N = 150, M = 100 (Gauss-Chebyshev), xi = 0.005 "
+                                   "relative change, D = 0.55, omega = 0.678, m = 0.005, "
+                                   "staggered grid on [1e-4, 1e4] GeV^2"},
+            "gpu": out, "paper": TABLE1_PAPER}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------------
 def run_adjoint(args):
     """Gradients of the chiral condensate -<qq> of every instance with respect to (m, D, w, mu):
     one step = forward mixed-precision solve to 1e-12 (kernel precompute included) + condensate
@@ -633,7 +728,9 @@ def run_mu_solve(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.workload == "table1":
+        run_table1(a)
+    elif a.impl == "reference":
         run_reference(a)
     elif a.workload == "adjoint":
         run_adjoint(a)

@@ -84,6 +84,10 @@ def _f64(a) -> np.ndarray:
 
 
 COLLOCATED, STAGGERED = 0, 1
+# The staggered grid with the paper's traditional interpolation (Table 1, algorithms 1 and 3):
+# the bracket of each internal node is searched for at every integrand evaluation.  Same values
+# as STAGGERED, more work; for timing the paper's comparison only.
+STAGGERED_TRADITIONAL = 2
 BC, RL = 0, 1
 STATUS = {0: "converged", 1: "bad argument", 4: "not converged", 5: "non-finite"}
 

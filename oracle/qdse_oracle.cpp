@@ -35,6 +35,9 @@
  *       3-point Lagrange polynomial in u = ln s (one-sided at the ends).
  *   R9  modified interpolation is linear in |p|; F(q_N) = F(p_N).
  *   R10 angular rule: Gauss-Chebyshev of the second kind (weight sin^2 theta).
+ *   R15 the traditional interpolation of Table 1 (algorithms 1, 3) searches the external grid
+ *       linearly for q's bracket at every integrand evaluation, then applies Eq. chazhiresult0;
+ *       grid_mode 2 selects it (timing only: the values equal those of grid_mode 1).
  *
  * After the Dirac traces the per-point integrand reduces to three angular kernels
  *   g_T = 2 P Q (1 - z^2) / k^2,   g_3 = [3 x (P+Q) - 4 x^2 - 2 P Q] / k^2,   g_0 = 1
@@ -69,6 +72,7 @@ struct Cfg {
     int n_theta;    /* angular nodes                                         */
     double s_min, s_max; /* GeV^2                                            */
     int grid_mode;  /* 0 collocated, 1 staggered (modified interpolation)    */
+    int traditional; /* staggered, bracket found at every evaluation (R15)   */
     int vertex;     /* 0 Ball-Chiu, 1 rainbow (bare vertex)                  */
     double cf;      /* colour factor                                         */
 };
@@ -241,6 +245,30 @@ T at_q(const Cfg& c, const Grid& g, const T* F, int j) {
     return F[b] + (q - pb) * (F[b + 1] - F[b]) / (pb1 - pb);     /* Eq. chazhiresult */
 }
 
+/* Reading R15, the paper's traditional interpolation (Sec. III; Table 1, algorithms 1 and 3):
+ * no bracket is kept between evaluations; each one scans the external grid for
+ * p[b] <= q < p[b+1] (the finding step before Eq. chazhiresult0) and interpolates there.  The
+ * values equal at_q's exactly; only the work differs.  noipa keeps the compiler from proving the
+ * call loop-invariant and hoisting the search out of the angular loop. */
+__attribute__((noipa)) double at_q_traditional(const Cfg& c, const Grid& g, const double* F,
+                                                int j) {
+    const double q2 = g.sq[j];
+    int b = 0;
+    while (b + 1 < c.n && g.sp[b + 1] <= q2) ++b;
+    if (b >= c.n - 1) return F[c.n - 1];
+    const double pb = std::sqrt(g.sp[b]), pb1 = std::sqrt(g.sp[b + 1]), q = std::sqrt(q2);
+    return F[b] + (q - pb) * (F[b + 1] - F[b]) / (pb1 - pb);
+}
+
+template <class T>
+void traditional_values(const Cfg&, const Grid&, const T*, const T*, int, T*, T*) {}
+template <>
+void traditional_values<double>(const Cfg& c, const Grid& g, const double* A, const double* B,
+                                int j, double* Aq, double* Bq) {
+    *Aq = at_q_traditional(c, g, A, j);
+    *Bq = at_q_traditional(c, g, B, j);
+}
+
 /* One Jacobi sweep  x_{n+1} = F(x_n)  for external rows [i0, i1).  Plain triple loop. */
 template <class T>
 void sweep_rows(const Cfg& c, const Grid& g, T D, T omega, T m, const T* A, const T* B,
@@ -253,7 +281,7 @@ void sweep_rows(const Cfg& c, const Grid& g, T D, T omega, T m, const T* A, cons
         T SA = T(0.0), SB = T(0.0);
         for (int j = 0; j < n; ++j) {
             const double Q = g.sq[j];
-            const T Aq = at_q(c, g, A, j), Bq = at_q(c, g, B, j);
+            T Aq = at_q(c, g, A, j), Bq = at_q(c, g, B, j);
             T DA, DB;
             if (Q == P) {  /* collocated diagonal: removable limit (reading R8) */
                 DA = diag_quotient(g.sp.data(), n, A, i);
@@ -264,6 +292,11 @@ void sweep_rows(const Cfg& c, const Grid& g, T D, T omega, T m, const T* A, cons
             }
             const double sP = std::sqrt(P), sQ = std::sqrt(Q);
             for (int k = 0; k < c.n_theta; ++k) {
+                if (c.traditional) {  /* R15: interpolate again at every evaluation */
+                    traditional_values<T>(c, g, A, B, j, &Aq, &Bq);
+                    DA = (Aq - A[i]) / (Q - P);
+                    DB = (Bq - B[i]) / (Q - P);
+                }
                 const double k2 = (sP - sQ) * (sP - sQ) + 2.0 * sP * sQ * g.y[k];
                 const T Dk = pref * std::exp(-k2 / (omega * omega));
                 T IA, IB;
@@ -345,7 +378,8 @@ int lu_solve(int n, std::vector<double>& M, double* b) {
 Cfg make_cfg(int n, int n_theta, double s_min, double s_max, int grid_mode, int vertex, double cf) {
     Cfg c;
     c.n = n; c.n_theta = n_theta; c.s_min = s_min; c.s_max = s_max;
-    c.grid_mode = grid_mode; c.vertex = vertex; c.cf = cf;
+    c.grid_mode = grid_mode == 2 ? 1 : grid_mode; c.vertex = vertex; c.cf = cf;
+    c.traditional = grid_mode == 2;
     return c;
 }
 

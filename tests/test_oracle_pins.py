@@ -428,3 +428,22 @@ def test_solution_is_a_fixed_point():
     Fa, Fb = O.sweep(pr, A, B)
     assert np.abs(Fa - A).max() < 1e-11 * np.abs(A).max()
     assert np.abs(Fb - B).max() < 1e-11 * np.abs(B).max()
+
+
+def test_table_1_algorithms_reach_the_same_solution_in_the_same_iterations():
+    """Sec. IV, Table 1: traditional and modified interpolation, each serial and with OpenMP over
+    the external index, lead to the same solution with the same number of iterations (the
+    paper's check that the algorithms change only the speed).  Here: bitwise, at the paper's
+    interaction D = 0.55, omega = 0.678, on the staggered grid; the Nambu solution."""
+    base = dict(n=40, n_theta=24, D=0.55, omega=0.678, m=0.005)
+    runs = []
+    for mode in (O.STAGGERED_TRADITIONAL, O.STAGGERED):
+        for nt in (1, 4):
+            A, B, it, ch, st = O.solve(O.Problem(grid_mode=mode, **base), tol=1e-8, nthreads=nt)
+            assert st == 0
+            runs.append((A, B, it))
+    for A, B, it in runs[1:]:
+        assert np.array_equal(A, runs[0][0]) and np.array_equal(B, runs[0][1])
+        assert it == runs[0][2]
+    A, B = runs[0][0], runs[0][1]
+    assert 1.1 < A[0] < 1.3 and 0.25 < B[0] / A[0] < 0.35  # A(0) ~ 1.18, M(0) ~ 0.30 GeV
