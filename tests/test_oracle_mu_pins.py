@@ -225,8 +225,8 @@ def test_mu_zero_solve_approaches_the_vacuum_solution_as_the_grid_is_refined():
     vertex, against the pinned vacuum oracle's solve on its own 1-D grid: the 2-D solution is
     real, and its distance to the vacuum B(p^2) and the O(4) breaking |C - A| both shrink as the
     (|p|, p_4) grid is refined (observed: B 0.79 -> 0.19 of max|B|, |C - A| 1.05 -> 0.53, and
-    0.055, 0.17 on a 24 x 16 grid).  A slip in the interpolation weights or axes stops the
-    convergence."""
+    0.055, 0.17 on a 24 x 16 grid).  It checks the pieces together, not each formula: a swap of
+    the two interpolation weights still passes here and is caught by the exactness pin above."""
     from paper_2012_03667_gb300 import inputs as I
     pr = O.Problem(n=128, n_theta=64, D=D, omega=OMEGA, m=M, vertex=O.RL)
     A, B, it, ch, st = O.solve(pr, tol=1e-12, nthreads=O.max_threads())
