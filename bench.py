@@ -559,6 +559,39 @@ MU_TILE = 8
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def mu_cpu_baseline(w, seconds=15.0):
+    """The finite-mu FP64 oracle (explicit 4x4 Dirac matrices, OpenMP over external points) on a
+    bounded sample of the workload: all internal points and angles for a growing set of external
+    points at two chemical potentials, until about `seconds` of CPU work; (pair, mu) evaluations
+    per second, pairs counted as all internal points (the oracle keeps no windows)."""
+    from oracle import oracle_mu as OM
+    from paper_2012_03667_gb300 import inputs
+    OM.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    QR, Q4 = np.meshgrid(w.q_abs, w.q4, indexing="ij")
+    qv, q4 = QR.ravel(), Q4.ravel()
+    evals, t_total, n_pts = 0, 0.0, 0
+    n = max(1, cores)
+    stride = max(1, len(w.p_abs) // 97)
+    for b in (0, len(w.mu) - 1):
+        mu = float(w.mu[b])
+        Fq = inputs.mu_iterate(qv, q4, mu, w.m)
+        idx = np.arange(0, len(w.p_abs), stride)[:n]
+        Fp = inputs.mu_iterate(w.p_abs[idx], w.p4[idx], mu, w.m)
+        t0 = time.perf_counter()
+        OM.sweep(w.p_abs[idx], w.p4[idx], qv, q4, w.w_q, w.z, w.w_z, w.D, w.omega, w.m, mu,
+                 *Fp, *Fq, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        evals += len(idx) * len(qv)
+        n_pts += len(idx)
+        if t_total > seconds:
+            break
+    return {"value": evals / t_total, "unit": "pair-mu evals/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n_pts} external points x all {len(qv)} internal points x "
+                      f"{len(w.z)} angles at 2 chemical potentials, FP64, {t_total:.1f} s"}
+
+
 def run_mu(args):
     """One step = one batched FP32 sweep of the finite-mu gap equation (Ball-Chiu vertex) for all
     chemical potentials: propagator prep + sweep over the precomputed angular-moment table.  The
@@ -658,6 +691,27 @@ def run_mu(args):
                     "h2d_bytes_per_step": Fe_h.nbytes + Fi_h.nbytes,
                     "d2h_bytes_per_step": out_p.numel() * out_p.element_size()},
             "gpu_launches": 2 * args.steps, "outputs_finite": ok, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = mu_cpu_baseline(w, args.cpu_seconds)
+    print(json.dumps(line))
+
+
+def run_mu_reference(args):
+    """--impl reference --workload mu: the finite-mu oracle timed on the host cores (rank 0)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from paper_2012_03667_gb300 import inputs
+    w = inputs.mu_workload()
+    cb = mu_cpu_baseline(w, args.cpu_seconds)
+    v = cb["value"]
+    line = {"metric": "finite-mu sweep: (pair, mu) evaluations per second", "value": v,
+            "unit": "pair-mu evals/s", "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "finite mu: the full grid of --workload mu, sampled"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "pair-mu evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -730,6 +784,8 @@ if __name__ == "__main__":
     a = parse()
     if a.workload == "table1":
         run_table1(a)
+    elif a.impl == "reference" and a.workload == "mu":
+        run_mu_reference(a)
     elif a.impl == "reference":
         run_reference(a)
     elif a.workload == "adjoint":
