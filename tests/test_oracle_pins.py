@@ -531,3 +531,39 @@ def test_table_1_iteration_count():
                 break
         assert abs(it - t["iterations"]) <= 1, (mode, it)
         assert 0.25 < B[0] / A[0] < 0.35  # sanity: the Nambu branch (the paper prints no M(0))
+
+
+@pytest.mark.parametrize("vertex", [O.BC, O.RL])
+def test_paper_i_terms_equal_the_reduced_integrand(vertex):
+    """The six I-terms of Eq. dsesys2 as printed (dot products of the 4-vectors p, q, k = p - q,
+    t = p + q), with readings R1 (the internal propagator's q^2 A_q^2 + B_q^2 in the denominator)
+    and R3 (I_A1 carries one 1/p^2, not two; the A projection one 1/p^2 overall), against the
+    oracle's reduced integrand (g_T, g_3), at random momenta: the second path of the oracle."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        P, Q = np.exp(rng.uniform(-3, 3, 2))
+        z = rng.uniform(-0.99, 0.99)
+        p = np.array([0.0, 0.0, 0.0, math.sqrt(P)])
+        q = math.sqrt(Q) * np.array([math.sqrt(1 - z * z), 0.0, 0.0, z])
+        k, t = p - q, p + q
+        Ap, Aq = rng.uniform(1.0, 2.5, 2)
+        Bp, Bq = rng.uniform(0.01, 0.8, 2)
+        if vertex == O.BC:
+            SA = 0.5 * (Aq + Ap)
+            DA, DB = (Aq - Ap) / (Q - P), (Bq - Bp) / (Q - P)
+        else:  # bare vertex: Sigma_A = 1, no difference quotients
+            SA, DA, DB = 1.0, 0.0, 0.0
+        k2, pp = k @ k, p @ p
+        IA1 = -(Bq / pp) * (k2 * (p @ t) - (k @ p) * (k @ t)) / (k2 * pp) * DB
+        IA2 = -(Aq / (2 * pp)) * (pp * (q @ t) * k2 + (q @ q) * (p @ t) * k2
+                                  - (q @ q) * (p @ k) * (t @ k) - pp * (q @ k) * (t @ k)) / k2 * DA
+        IA3 = (Aq / pp) * (k2 * (p @ q) + 2 * (k @ q) * (k @ p)) / k2 * SA
+        IB1 = -Aq * ((q @ t) * k2 - (q @ k) * (t @ k)) / k2 * DB
+        IB2 = 3 * Bq * SA
+        IB3 = Bq * (k2 * (t @ t) - (k @ t) ** 2) / (2 * k2) * DA
+        dq = Q * Aq ** 2 + Bq ** 2                      # R1
+        want_A = (pp * IA1 + IA2 + IA3) / dq             # R3: one 1/p^2 in I_A1
+        want_B = (IB1 + IB2 + IB3) / dq
+        ia, ib = O.point_integrand(P, Q, z, Ap, Bp, Aq, Bq, DA, DB, vertex)
+        assert abs(ia - want_A) <= 1e-12 * max(1.0, abs(want_A)), (P, Q, z)
+        assert abs(ib - want_B) <= 1e-12 * max(1.0, abs(want_B)), (P, Q, z)
