@@ -152,3 +152,22 @@ def test_mu_product_grid_and_solve_reject_bad_arguments_on_the_host(lib, kw, msg
     assert msg in lib.qdse_mu_last_error().decode()
     assert lib.qdse_mu_solve(None, None, 1, None, 1.0, 0.0, 1.0, 0, 1.0, 1e-10, 1e-5, 10, None,
                              None, None, None) == Q.QDSE_ERR_ARG
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_public_headers_compile_as_plain_c_and_cxx(tmp_path, lang, std):
+    """include/*.h is a C ABI: both headers compile on their own and together as C99 (no C++
+    types, no torch types) and as C++, with every warning an error."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use.c" if lang == "c" else "use.cpp")
+    src.write_text('#include "qdse.h"\n#include "qdse_mu.h"\n#include "qdse.h"\n'
+                   "int main(void) { qdse_mu_grid* g = 0; qdse_ctx* c = 0; (void)g; (void)c;\n"
+                   "  return QDSE_OK + QDSE_VERTEX_BC + QDSE_FP32; }\n")
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
