@@ -53,6 +53,11 @@ def _load():
                                               ctypes.c_int, _dp, _dp] + [ctypes.c_double] * 5
                                              + [ctypes.c_int] + [_dp] * 9 + [ctypes.c_int])
             lib.oracle_mu_sweep.restype = ctypes.c_int
+            lib.oracle_mu_sweep_dq.argtypes = ([ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp,
+                                                 _dp, ctypes.c_int, _dp, _dp]
+                                                + [ctypes.c_double] * 5 + [ctypes.c_int]
+                                                + [_dp] * 10 + [ctypes.c_int])
+            lib.oracle_mu_sweep_dq.restype = ctypes.c_int
             _lib = lib
         return _lib
 
@@ -85,17 +90,26 @@ def vertex(q, q4, p, p4, fq, fp, vertex=BC):
 
 
 def sweep(pv, p4, qv, q4, wq, z, wz, D, omega, m, mu, Ap, Cp, Bp, Aq, Cq, Bq, cf=4.0 / 3.0,
-          vertex=BC, nthreads=0):
+          vertex=BC, nthreads=0, Fd=None):
     """One finite-mu sweep (readings M1-M5): new (A, C, B) at the external points (|p_vec|, p_4)
     from the inputs there and at the internal points (|q_vec|, q_4) with weights wq (including
-    |q|^2 d|q| dq_4) and cosine nodes z, wz."""
+    |q|^2 d|q| dq_4) and cosine nodes z, wz.  Fd (reading M8): None, or complex [3, n_ext * n_int]
+    -- per pair, the values subtracted in the vertex's difference numerators in place of the
+    external point's own."""
     lib = _load()
     pv, p4, qv, q4, wq, z, wz = map(_f64, (pv, p4, qv, q4, wq, z, wz))
     ins = [_c(x) for x in (Ap, Cp, Bp, Aq, Cq, Bq)]
     outs = [np.zeros(2 * len(pv)) for _ in range(3)]
-    bad = lib.oracle_mu_sweep(len(pv), _p(pv), _p(p4), len(qv), _p(qv), _p(q4), _p(wq), len(z),
-                              _p(z), _p(wz), D, omega, m, mu, cf, vertex, *[_p(x) for x in ins],
-                              *[_p(x) for x in outs], nthreads)
+    if Fd is None:
+        bad = lib.oracle_mu_sweep(len(pv), _p(pv), _p(p4), len(qv), _p(qv), _p(q4), _p(wq),
+                                  len(z), _p(z), _p(wz), D, omega, m, mu, cf, vertex,
+                                  *[_p(x) for x in ins], *[_p(x) for x in outs], nthreads)
+    else:
+        fd = _c(np.asarray(Fd).reshape(3, len(pv) * len(qv)))
+        bad = lib.oracle_mu_sweep_dq(len(pv), _p(pv), _p(p4), len(qv), _p(qv), _p(q4), _p(wq),
+                                     len(z), _p(z), _p(wz), D, omega, m, mu, cf, vertex,
+                                     *[_p(x) for x in ins], _p(fd), *[_p(x) for x in outs],
+                                     nthreads)
     if bad:
         raise ValueError("singular propagator or k^2 = 0 at some (p, q) pair")
     return tuple(o.view(np.complex128) for o in outs)
@@ -131,23 +145,64 @@ def interpolate(p_axis, p4_axis, F, q_abs, q4):
     return out.reshape(3, -1)
 
 
+def interpolate_points(p_axis, p4_axis, F, x, y):
+    """Reading M6 at arbitrary points (|p| = x, p_4 = y; arrays of one shape), vectorised: the
+    same bracketing, weights, holding and conjugation (y < 0) as interpolate().  Returns
+    [3, *x.shape]."""
+    F = np.asarray(F, dtype=np.complex128).reshape(3, len(p_axis), len(p4_axis))
+    x = np.asarray(x, dtype=np.float64)
+    ya = np.abs(np.asarray(y, dtype=np.float64))
+
+    def bracket(axis, v):
+        i = np.searchsorted(axis, v, side="right") - 1
+        inside = (i >= 0) & (i < len(axis) - 1)
+        ic = np.clip(i, 0, len(axis) - 1)
+        i1 = np.minimum(ic + 1, len(axis) - 1)
+        span = np.where(inside, axis[i1] - axis[ic], 1.0)
+        w = np.where(inside, (v - axis[ic]) / span, 0.0)
+        return ic, i1, w
+
+    i, i1, a = bracket(np.asarray(p_axis), x)
+    k, k1, b = bracket(np.asarray(p4_axis), ya)
+    v = ((1 - a) * (1 - b) * F[:, i, k] + a * (1 - b) * F[:, i1, k]
+         + (1 - a) * b * F[:, i, k1] + a * b * F[:, i1, k1])
+    return np.where(np.asarray(y) < 0, np.conj(v), v)
+
+
 def solve(p_axis, p4_axis, q_abs, q4, w_q, z, wz, D, omega, m, mu, F0, tol=1e-10, max_iter=500,
-          cf=4.0 / 3.0, vertex=BC, alpha=1.0, nthreads=0):
+          cf=4.0 / 3.0, vertex=BC, alpha=1.0, nthreads=0, ray_eta=None):
     """Successive approximation (the paper's Eq. jifen14 scheme) of the finite-mu equation on the
     external product grid: G = sweep(F, interpolate(F)), F <- G (alpha = 1) or
     F <- (1 - alpha) F + alpha G, until the relative change of reading M7 (per function,
     max |F_new - F_old| over the grid divided by max |F_new|) is below tol; tol = 0 runs exactly
     max_iter steps.  (The change of a function that is identically zero is taken absolute.)
+
+    ray_eta (reading M8, off when None): the difference numerators F_q - F_p of the vertex take,
+    per pair, F_p + beta (F_ray - F_p) in place of F_p, where F_ray is F interpolated (M6) at the
+    point of q's ray with p's 4-radius, (|q|, q_4) sqrt(P^2 + p_4^2)/sqrt(Q^2 + q_4^2), and
+    beta = exp(-(2 mu |q_4 - p_4| / ray_eta)^2).  At mu = 0 the numerator then vanishes on the
+    4-sphere q^2 = p^2 for any grid function, so the discrete principal-value sum of
+    1/(q~^2 - p~^2) no longer couples F_p to itself; where 2 mu |q_4 - p_4| >> ray_eta it is the
+    exact quotient of M3.
     Returns (F [3, n_ext], iterations, converged)."""
     PR, P4 = np.meshgrid(p_axis, p4_axis, indexing="ij")
     pv, p4 = PR.ravel(), P4.ravel()
     QR, Q4 = np.meshgrid(q_abs, q4, indexing="ij")
     qv, q4f = QR.ravel(), Q4.ravel()
     F = np.asarray(F0, dtype=np.complex128).reshape(3, -1).copy()
+    if ray_eta is not None:
+        lam = np.sqrt(pv ** 2 + p4 ** 2)[:, None] / np.sqrt(qv ** 2 + q4f ** 2)[None, :]
+        rx, ry = qv[None, :] * lam, q4f[None, :] * lam
+        beta = np.exp(-(2.0 * mu * np.abs(q4f[None, :] - p4[:, None]) / ray_eta) ** 2)
     for it in range(1, max_iter + 1):
         Fi = interpolate(p_axis, p4_axis, F, q_abs, q4)
+        Fd = None
+        if ray_eta is not None:
+            Fr = interpolate_points(p_axis, p4_axis, F, rx, ry)
+            Fp = F[:, :, None]
+            Fd = (Fp + beta[None] * (Fr - Fp)).reshape(3, -1)
         G = np.array(sweep(pv, p4, qv, q4f, w_q, z, wz, D, omega, m, mu, *F, *Fi, cf=cf,
-                           vertex=vertex, nthreads=nthreads))
+                           vertex=vertex, nthreads=nthreads, Fd=Fd))
         new = G if alpha == 1.0 else (1.0 - alpha) * F + alpha * G
         change = 0.0
         for c in range(3):

@@ -25,6 +25,10 @@
  *       B = tr[S^-1]/4, applied to S^-1(p~) = i g.p~ + m + Sigma(p~).
  *   M5  d^4q/(2 pi)^4 = 2 pi/(2 pi)^4 dq_4 |q|^2 d|q| dz, z the cosine between p_vec and q_vec:
  *       the projected traces are invariant under rotations about p_vec, so the azimuth gives 2 pi.
+ *   M8  (optional, off by default) the difference numerators F_q - F_p of M3 may take, per pair,
+ *       a caller-given value in place of F_p (oracle_mu_sweep_dq); the solve uses it for the
+ *       ray-blended quotient of oracle_mu.py, which removes the runaway of the discrete
+ *       principal-value sum at mu -> 0.
  * The quadrature (the internal points (|q|, q_4) with their weights, which include |q|^2, and the
  * z nodes and weights) is the caller's; the sweep is the plain sum over it.  Internal and
  * external points must differ (k^2 > 0): the removable point q~ = p~ is not treated here.
@@ -138,8 +142,9 @@ M4 sinv(const double* v, cd v4, cd A, cd C, cd B) {
 }
 
 // Gamma_nu(q~, p~) of reading M3 (vertex 0 = BC) or the bare g_nu (vertex 1 = rainbow).
+// ApD, CpD, BpD: the values subtracted in the difference numerators (normally Ap, Cp, Bp).
 void vertex(const double* q, cd q4, const double* p, cd p4, cd Aq, cd Cq, cd Bq, cd Ap, cd Cp,
-            cd Bp, int rainbow, M4 out[4]) {
+            cd Bp, cd ApD, cd CpD, cd BpD, int rainbow, M4 out[4]) {
     static const cd I(0.0, 1.0);
     if (rainbow) {
         for (int nu = 0; nu < 4; ++nu) out[nu] = G().g[nu];
@@ -149,7 +154,7 @@ void vertex(const double* q, cd q4, const double* p, cd p4, cd Aq, cd Cq, cd Bq,
     const cd q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q4 * q4;
     const cd p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] + p4 * p4;
     const cd den = q2 - p2;
-    const cd dA = (Aq - Ap) / den, dC = (Cq - Cp) / den, dB = (Bq - Bp) / den;
+    const cd dA = (Aq - ApD) / den, dC = (Cq - CpD) / den, dB = (Bq - BpD) / den;
     // the t-structure: g_vec.t_vec dA/2 + g_4 t_4 dC/2 - i dB
     M4 X = zero();
     for (int k = 0; k < 3; ++k) axpy(X, 0.5 * t[k] * dA, G().g[k]);
@@ -175,7 +180,7 @@ void oracle_mu_vertex(const double* q, double q4r, double q4i, const double* p, 
     const cd Aq(qf[0], qf[1]), Cq(qf[2], qf[3]), Bq(qf[4], qf[5]);
     const cd Ap(pf[0], pf[1]), Cp(pf[2], pf[3]), Bp(pf[4], pf[5]);
     M4 g[4];
-    vertex(q, q4, p, p4, Aq, Cq, Bq, Ap, Cp, Bp, rainbow, g);
+    vertex(q, q4, p, p4, Aq, Cq, Bq, Ap, Cp, Bp, Ap, Cp, Bp, rainbow, g);
     const M4 Sq = sinv(q, q4, Aq, Cq, Bq), Sp = sinv(p, p4, Ap, Cp, Bp);
     for (int nu = 0; nu < 4; ++nu)
         for (int i = 0; i < 4; ++i)
@@ -195,14 +200,15 @@ void oracle_mu_vertex(const double* q, double q4r, double q4i, const double* p, 
 // One sweep (readings M1-M5): for every external point i (|p_vec| = pv[i], p_4 = p4[i]) the new
 // A, C, B from the inputs at the external points (Ap, Cp, Bp, used in the vertex) and at the
 // internal points j (|q_vec| = qv[j], q_4 = q4[j], weight wq[j] for dq_4 |q|^2 d|q|), with nz
-// cosine nodes z (weights wz).  Complex arrays interleaved (re, im).  Returns 0, or 1 when a
-// propagator is singular or k^2 = 0 at some point.
-int oracle_mu_sweep(int np, const double* pv, const double* p4, int nq, const double* qv,
-                    const double* q4, const double* wq, int nz, const double* z,
-                    const double* wz, double D, double omega, double m, double mu, double cf,
-                    int rainbow, const double* Ap, const double* Cp, const double* Bp,
-                    const double* Aq, const double* Cq, const double* Bq, double* Ao, double* Co,
-                    double* Bo, int nthreads) {
+// cosine nodes z (weights wz).  Complex arrays interleaved (re, im).  Fd (M8): NULL, or complex
+// [3][np * nq] -- per pair (i, j), the A, C, B subtracted in the difference numerators in place
+// of Ap[i], Cp[i], Bp[i].  Returns 0, or 1 when a propagator is singular or k^2 = 0 at some point.
+int oracle_mu_sweep_dq(int np, const double* pv, const double* p4, int nq, const double* qv,
+                       const double* q4, const double* wq, int nz, const double* z,
+                       const double* wz, double D, double omega, double m, double mu, double cf,
+                       int rainbow, const double* Ap, const double* Cp, const double* Bp,
+                       const double* Aq, const double* Cq, const double* Bq, const double* Fd,
+                       double* Ao, double* Co, double* Bo, int nthreads) {
     static const cd I(0.0, 1.0);
     const double pref = cf * 8.0 * kPi * kPi * D / (omega * omega * omega * omega);
     const double measure = 2.0 * kPi / std::pow(2.0 * kPi, 4);
@@ -235,8 +241,15 @@ int oracle_mu_sweep(int np, const double* pv, const double* p4, int nq, const do
                     bad = 1;
                     continue;
                 }
+                cd AD = Api, CD = Cpi, BD = Bpi;
+                if (Fd) {
+                    const size_t o = (size_t)i * nq + j, npq = (size_t)np * nq;
+                    AD = cd(Fd[2 * o], Fd[2 * o + 1]);
+                    CD = cd(Fd[2 * (npq + o)], Fd[2 * (npq + o) + 1]);
+                    BD = cd(Fd[2 * (2 * npq + o)], Fd[2 * (2 * npq + o) + 1]);
+                }
                 M4 Gam[4];
-                vertex(q, qt4, p, pt4, Aqj, Cqj, Bqj, Api, Cpi, Bpi, rainbow, Gam);
+                vertex(q, qt4, p, pt4, Aqj, Cqj, Bqj, Api, Cpi, Bpi, AD, CD, BD, rainbow, Gam);
                 // sum_{mu nu} T_mu nu(k) g_mu S Gamma_nu, T = delta - k k / k^2
                 M4 Msum = zero();
                 for (int a = 0; a < 4; ++a) {
@@ -261,6 +274,17 @@ int oracle_mu_sweep(int np, const double* pv, const double* p4, int nq, const do
         Bo[2 * i + 1] = B1.imag();
     }
     return bad;
+}
+
+// oracle_mu_sweep_dq without M8: the exact difference numerators of M3.
+int oracle_mu_sweep(int np, const double* pv, const double* p4, int nq, const double* qv,
+                    const double* q4, const double* wq, int nz, const double* z,
+                    const double* wz, double D, double omega, double m, double mu, double cf,
+                    int rainbow, const double* Ap, const double* Cp, const double* Bp,
+                    const double* Aq, const double* Cq, const double* Bq, double* Ao, double* Co,
+                    double* Bo, int nthreads) {
+    return oracle_mu_sweep_dq(np, pv, p4, nq, qv, q4, wq, nz, z, wz, D, omega, m, mu, cf, rainbow,
+                              Ap, Cp, Bp, Aq, Cq, Bq, nullptr, Ao, Co, Bo, nthreads);
 }
 
 }  // extern "C"
