@@ -180,10 +180,10 @@ def solve(p_axis, p4_axis, q_abs, q4, w_q, z, wz, D, omega, m, mu, F0, tol=1e-10
     ray_eta (reading M8, off when None): the difference numerators F_q - F_p of the vertex take,
     per pair, F_p + beta (F_ray - F_p) in place of F_p, where F_ray is F interpolated (M6) at the
     point of q's ray with p's 4-radius, (|q|, q_4) sqrt(P^2 + p_4^2)/sqrt(Q^2 + q_4^2), and
-    beta = exp(-(2 mu |q_4 - p_4| / ray_eta)^2).  At mu = 0 the numerator then vanishes on the
-    4-sphere q^2 = p^2 for any grid function, so the discrete principal-value sum of
-    1/(q~^2 - p~^2) no longer couples F_p to itself; where 2 mu |q_4 - p_4| >> ray_eta it is the
-    exact quotient of M3.
+    beta = exp(-(2 mu |q_4 - p_4| / ray_eta)^2), ray_eta in GeV^2.  At mu = 0 the numerator then
+    vanishes on the 4-sphere q^2 = p^2 for any grid function, so the discrete principal-value sum
+    of 1/(q~^2 - p~^2) no longer couples F_p to itself; where 2 mu |q_4 - p_4| >> ray_eta it is
+    the exact quotient of M3.
     Returns (F [3, n_ext], iterations, converged)."""
     PR, P4 = np.meshgrid(p_axis, p4_axis, indexing="ij")
     pv, p4 = PR.ravel(), P4.ravel()
