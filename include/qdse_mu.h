@@ -103,7 +103,9 @@ int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double 
  * launches (the propagator prep and the sweep) on its stream, without synchronising.
  * qdse_mu_profile waits for the last recorded event, adds the elapsed times since the previous
  * read into ms[2] (prep, sweep; host double[2]) and the launch counts into launches[2] (host
- * long long[2]), and clears them.  Either output may be NULL. */
+ * long long[2]), and clears them.  Either output may be NULL.  Events accumulate (three per
+ * sweep, reused after each read) until qdse_mu_profile is called; qdse_mu_solve's sweeps are
+ * recorded too. */
 int qdse_mu_set_profiling(qdse_mu_grid* g, int on);
 int qdse_mu_profile(qdse_mu_grid* g, double* ms, long long* launches);
 
