@@ -292,3 +292,33 @@ def test_ray_blended_quotient_converges_at_mu_zero_and_matches_the_exact_one_els
     Fe, ite, oke = OM.solve(*args, 0.2, start, tol=1e-10, max_iter=150, nthreads=O.max_threads())
     assert okr and oke
     assert np.abs(Fr - Fe).max() < 1e-4 * np.abs(Fe).max()
+
+
+def test_ray_blended_quotient_at_mu_zero_approaches_the_vacuum_bc_solution():
+    """Reading M8 at mu = 0 with the Ball-Chiu vertex (the paper's interaction, where the vacuum
+    equation has the Nambu solution, A(0) = 1.18, M(0) = 0.30 GeV): the 2-D solve converges, and
+    its distance to the pinned vacuum oracle's B(p^2) and the O(4) breaking |C - A| shrink as the
+    grid is refined (observed: B 0.60 -> 0.070 -> 0.049 of max|B|, |C - A| 0.27 -> 0.17 ->
+    0.056 on 12 x 8, 16 x 12, 24 x 16).  Without M8 this case runs away (one point's
+    principal-value self-coupling exceeds 1)."""
+    from paper_2012_03667_gb300 import inputs as I
+    D_, om, m = 0.55, 0.678, 0.005
+    A, B, it, ch, st = O.solve(O.Problem(n=128, n_theta=64, D=D_, omega=om, m=m), tol=1e-12,
+                               nthreads=O.max_threads())
+    assert st == 0
+    sp, _, _, _ = O.radial_grid(128)
+    errs = []
+    for nr, n4 in ((12, 8), (16, 12)):
+        w = I.mu_workload(n_r=nr, n_4=n4, n_z=16, n_mu=1, D=D_, omega=om, m=m)
+        pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
+        start = np.array([np.ones(len(w.p_abs))] * 3, dtype=np.complex128)
+        F, it, ok = OM.solve(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, D_, om, m, 0.0, start,
+                             tol=1e-10, max_iter=100, ray_eta=0.002, nthreads=O.max_threads())
+        assert ok
+        s = w.p_abs ** 2 + w.p4 ** 2
+        sel = (s > 1e-3) & (s < 10)
+        Bv = np.interp(np.log(s[sel]), np.log(sp), B)
+        errs.append((np.abs(F[2].real[sel] - Bv).max() / np.abs(Bv).max(),
+                     np.abs(F[1] - F[0]).max()))
+    assert errs[1][0] < errs[0][0] / 3 and errs[1][0] < 0.15
+    assert errs[1][1] < 0.8 * errs[0][1]
