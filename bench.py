@@ -38,8 +38,12 @@ def parse():
     ap.add_argument("--workload", default="scan",
                     choices=["scan", "large", "small", "adjoint", "mu", "mu-small", "mu-solve",
                              "table1"],
-                    help="adjoint: 1024 scan instances at N_q = 256, N_theta = 64; one step = "
-                         "forward solve + condensate gradient w.r.t. (m, D, w, mu) by the adjoint")
+                    help="scan: 4096-instance mass/interaction scan (default); large/small: one "
+                         "N = 512 / N = 64 instance; adjoint: 1024 scan instances at N_q = 256, "
+                         "N_theta = 64, forward solve + condensate gradient by the adjoint; mu: "
+                         "finite-mu batched sweep, 256 mu on the full grid; mu-small: a small "
+                         "case of it; mu-solve: finite-mu solve of 32 mu; table1: Sec. IV "
+                         "Table 1 (with --impl reference, the four CPU algorithms)")
     ap.add_argument("--n-inst", type=int, default=4096)
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--check", type=int, default=8,
