@@ -6,7 +6,10 @@ host ``g++`` and wraps its C interface.  Only the test-suite may import it.  It 
 from the GPU package.
 
 The paper (arXiv:2012.03667) announces the finite-mu extension in Sec. V without giving its
-equations; the readings M1-M5 taken for it are listed in the header of ``qdse_oracle_mu.cpp``.
+equations.  Readings M1-M5 (the equation, vertex, projections and measure) are listed in the header
+of ``qdse_oracle_mu.cpp``; M6 (interpolation onto the internal points), M7 (the iteration and its
+convergence test) and M8 (the optional ray-blended difference quotient) are stated in
+``interpolate``, ``solve`` and ``solve``'s ``ray_eta`` below.
 """
 from __future__ import annotations
 
