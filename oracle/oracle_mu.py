@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of one sweep of the quark gap equation at finite chemical potential mu.
+"""FP64 CPU oracle of the quark gap equation at finite chemical potential mu: one sweep, the
+interpolation onto the internal points, and the solve.
 
 TEST INFRASTRUCTURE ONLY.  ``qdse_oracle_mu.cpp`` (plain C++ loops, explicit 4x4 complex Dirac
 matrices) is the independent checker for a finite-mu solver; this module compiles it with the
