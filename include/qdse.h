@@ -97,11 +97,26 @@ typedef struct {
                           returns QDSE_ERR_TIMEOUT and unfinished instances get that status       */
     int reuse_kernels; /* 1: keep the angular kernel matrices between calls while every instance's
                           omega is unchanged (an m- or D-scan); 0: rebuild them on every call   */
+    int stall_window;  /* no-progress stop (not in the paper; 0 = off, the paper's iteration):
+                          in a successive-approximation phase (FP32 or FP64 Picard) an instance
+                          keeps the lowest relative change it has reached in that phase; after
+                          stall_window consecutive sweeps without a new lowest value it ends
+                          with QDSE_ERR_NOT_CONVERGED.  A converging iteration keeps setting new
+                          lows; a limit cycle stops setting them after one period.  Must be
+                          >= 0                                                                  */
+    int stop_cycles;   /* cycle stop (not in the paper; 1 = on, 0 = off): a successive-
+                          approximation sweep is a fixed function of the iterate, so an instance
+                          whose iterate repeats exactly within a Picard phase (compared through a
+                          64-bit hash of every point's value) cycles forever and ends with
+                          QDSE_ERR_NOT_CONVERGED at once.  It never changes which instances
+                          converge, nor their results (up to a hash collision, chance below
+                          1e-10 per batch); A and B of a stopped instance hold its last iterate */
     void* stream;      /* cudaStream_t for all device work; NULL = legacy default stream         */
 } qdse_options;
 
 /* Defaults: QDSE_MIXED, BC vertex, cf = 4/3, tol = 1e-10, alpha = 1, max_iter = 20000,
- * no time limit, kernels rebuilt on every call, default stream. */
+ * no time limit, kernels rebuilt on every call, no no-progress stop, cycle stop on, default
+ * stream. */
 qdse_options qdse_default_options(void);
 
 /* Create a context for n_inst instances that share one grid (*g).  Builds the radial and angular
@@ -214,6 +229,21 @@ qdse_status qdse_last_stats(const qdse_ctx* ctx, long long* kernel_launches,
  * (n_p n_q n_theta per instance-sweep).  Synchronises the stream.  Either pointer may be NULL. */
 qdse_status qdse_last_work(const qdse_ctx* ctx, double* sweep_bytes, double* kernel_evals);
 
+/* Per-instance record of the last qdse_solve / qdse_iterate call (not in the paper: it splits the
+ * cost of a batched solve by instance).  out: host long long[5 n_inst]; for instance b,
+ *   out[5b + 0] = FP32 sweeps (Picard and tangent),
+ *   out[5b + 1] = FP64 sweeps (Picard and refinement residuals),
+ *   out[5b + 2] = the longest run of successive-approximation sweeps without a new lowest
+ *                 relative change (the quantity options.stall_window bounds),
+ *   out[5b + 3] = kernel-matrix entries one sweep reads per plane (the instance's row bands;
+ *                 0 before the first kernel precompute),
+ *   out[5b + 4] = the solver phase the instance ended in (0 FP32 Picard, 1 FP64 residual,
+ *                 2 FP32 tangent, 3 FP64 Picard, 4 finished),
+ * and, when out_cycles (host long long[2 n_inst]) is not NULL, out_cycles[2b] = the period of the
+ * cycle the cycle stop found (0: none) and out_cycles[2b + 1] = the sweep that found it.
+ * Synchronises the stream. */
+qdse_status qdse_last_instance_stats(const qdse_ctx* ctx, long long* out, long long* out_cycles);
+
 /* Turn CUDA-event timing of every kernel launch on (1) or off (0).  Off by default: when on,
  * each launch is bracketed by two events on the context's stream. */
 qdse_status qdse_set_profiling(qdse_ctx* ctx, int on);
@@ -234,7 +264,9 @@ qdse_status qdse_profile(const qdse_ctx* ctx, double* ms, long long* launches);
  * stream: cudaStream_t or NULL.  errbuf (host, errbuf_len bytes, may be NULL) receives a one-line
  * message ("" on success).  No cudaMalloc, cudaFree or allocating library call is made.  The first
  * call on each device looks up the scratch array's device address (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  All calls share the one scratch array: calls that
+ * that first call before any stream capture.  The looked-up address is kept for the life of the
+ * process; after a cudaDeviceReset of that device it is stale, so a process that resets a device
+ * must not call this entry point on it again.  All calls share the one scratch array: calls that
  * overlap on the GPU race and must be serialised by the caller.  Asynchronous on `stream`. */
 qdse_status qdse_sweep_fp64_noalloc(const qdse_grid* g, const qdse_params* p, int vertex,
                                     double cf, const double* A, const double* B, double* FA,

@@ -10,7 +10,10 @@ The paper (arXiv:2012.03667) announces the finite-mu extension in Sec. V without
 equations.  Readings M1-M5 (the equation, vertex, projections and measure) are listed in the header
 of ``qdse_oracle_mu.cpp``; M6 (interpolation onto the internal points), M7 (the iteration and its
 convergence test) and M8 (the optional ray-blended difference quotient) are stated in
-``interpolate``, ``solve`` and ``solve``'s ``ray_eta`` below.
+``interpolate``, ``solve`` and ``solve``'s ``ray_eta`` below.  The quadrature weights the oracle
+sums with (reading M5's measure and the cosine rule) are formed here from the node arrays alone
+(``measure``, ``angular_weights``: interpolatory rules from the moment equations), independently
+of the weights the library is given.
 """
 from __future__ import annotations
 
@@ -77,6 +80,51 @@ def _c(x):
 
 def _p(x):
     return x.ctypes.data_as(_dp)
+
+
+def interpolatory_weights(t):
+    """Weights of the interpolatory rule on the nodes t (in (-1, 1), distinct): the w with
+    sum_j w_j f(t_j) = int_{-1}^{1} f exactly for every polynomial of degree < len(t), from the
+    moment equations sum_j w_j P_k(t_j) = int P_k = 2 [k = 0] in the Legendre basis (Bonnet's
+    recurrence).  On Gauss-Legendre nodes these are the Gauss weights, exact to degree 2n - 1."""
+    t = np.asarray(t, dtype=np.float64)
+    n = len(t)
+    V = np.empty((n, n))
+    V[0] = 1.0
+    if n > 1:
+        V[1] = t
+    for k in range(1, n - 1):
+        V[k + 1] = ((2 * k + 1) * t * V[k] - k * V[k - 1]) / (k + 1)
+    rhs = np.zeros(n)
+    rhs[0] = 2.0
+    return np.linalg.solve(V, rhs)
+
+
+def log_rule(x, lo, hi):
+    """Weights of int_lo^hi f(x) dx on nodes x that carry an interpolatory rule in u = ln x on
+    [ln lo, ln hi] (dx = x du)."""
+    x = np.asarray(x, dtype=np.float64)
+    a, b = np.log(lo), np.log(hi)
+    t = (2.0 * np.log(x) - (a + b)) / (b - a)
+    return interpolatory_weights(t) * 0.5 * (b - a) * x
+
+
+def measure(q_abs, q4, lo, hi):
+    """Reading M5: the weights w_q of int |q|^2 d|q| dq_4 on the product grid q_abs x q4
+    (row-major, point r * len(q4) + f), built here from the node arrays alone: |q| and |q_4| carry
+    rules in ln x on [lo, hi] (log_rule); q_4 < 0 nodes mirror q_4 > 0 ones with their weights."""
+    q_abs = np.asarray(q_abs, dtype=np.float64)
+    q4 = np.asarray(q4, dtype=np.float64)
+    pos = np.unique(np.abs(q4))
+    w4p = log_rule(pos, lo, hi)
+    w4 = w4p[np.searchsorted(pos, np.abs(q4))]
+    wr = log_rule(q_abs, lo, hi) * q_abs ** 2
+    return np.outer(wr, w4).ravel()
+
+
+def angular_weights(z):
+    """Weights of int_{-1}^{1} dz on the cosine nodes z (interpolatory rule)."""
+    return interpolatory_weights(z)
 
 
 def vertex(q, q4, p, p4, fq, fp, vertex=BC):

@@ -77,6 +77,8 @@ qdse_status check_options(const qdse_options* o, std::string& why) {
     if (!finite(o->alpha) || o->alpha <= 0 || o->alpha > 1) { why = "options.alpha must be in (0, 1]"; return QDSE_ERR_ARG; }
     if (o->max_iter < 1) { why = "options.max_iter must be >= 1"; return QDSE_ERR_ARG; }
     if (std::isnan(o->time_limit)) { why = "options.time_limit is NaN"; return QDSE_ERR_ARG; }
+    if (o->stall_window < 0) { why = "options.stall_window must be >= 0"; return QDSE_ERR_ARG; }
+    if (o->stop_cycles != 0 && o->stop_cycles != 1) { why = "options.stop_cycles must be 0 or 1"; return QDSE_ERR_ARG; }
     return QDSE_OK;
 }
 
@@ -108,7 +110,7 @@ void free_ctx(qdse_ctx* c) {
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
                     c->grid.groups, c->grid.nnz, c->grid.gdesc, c->grid.gphase, c->work.ilist,
                     c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd,
-                    c->grid.W32, c->grid.wt32, c->grid.stc32};
+                    c->grid.W32, c->grid.wt32, c->grid.stc32, c->grid.expt, c->work.hring};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -185,6 +187,8 @@ Ctl make_ctl(const qdse_ctx* c) {
     t.final_phase = (c->opt.precision == QDSE_FP32) ? PH_PICARD32 : PH_PICARD64;
     t.never_converge = 0;
     t.stall_copies = c->stall_copies;
+    t.stall_window = c->opt.stall_window;
+    t.stop_cycles = c->opt.stop_cycles;
     return t;
 }
 
@@ -478,6 +482,9 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->grid.row_inst, N);
     CALLOC(c->grid.band, N);
     CALLOC(c->grid.nnz, n_inst);
+    std::vector<float2> expt;
+    exp_tables(expt);
+    CALLOC(c->grid.expt, expt.size());
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -486,6 +493,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->work.ilist, 3 * (size_t)n_inst);
     CALLOC(c->work.glist, 3 * (size_t)ng);
     CALLOC(c->work.lcount, 6);
+    CALLOC(c->work.hring, (size_t)kHashRing * n_inst);
     c->work.n_inst = n_inst;
     c->work.n_groups = ng;
     CALLOC(c->grid.groups, ng);
@@ -539,7 +547,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         {c->grid.row_inst, row_inst.data(), sizeof(int) * N},
         {c->grid.groups, groups.data(), sizeof(int2) * ng},
         {c->grid.gdesc, gdesc.data(), sizeof(GroupDesc) * ng},
-        {c->d_tiles, tiles.data(), sizeof(int4) * c->n_tiles}};
+        {c->d_tiles, tiles.data(), sizeof(int4) * c->n_tiles},
+        {c->grid.expt, expt.data(), sizeof(float2) * expt.size()}};
     for (auto& u : ups) {
         e = cudaMemcpy(u.d, u.h, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -571,6 +580,10 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         cudaGetLastError();
         c->sweep_kind = ring_ok ? 1 : 0;
         if (k && std::string(k) == "groups") c->sweep_kind = 0;
+        // kernel matrices: double-float on the FP32 pipe by default; QDSE_PRECOMPUTE=fp64
+        // selects the FP64 kernel (the same entries to about 1e-14)
+        const char* pk = std::getenv("QDSE_PRECOMPUTE");
+        c->precompute_kind = (pk && std::string(pk) == "fp64") ? 0 : 1;
         // test of the sweep's bounded waits (tests only): every tile wait runs out
         const char* st = std::getenv("QDSE_TEST_STALL");
         c->stall_copies = (st && std::string(st) == "1") ? 1 : 0;
@@ -612,6 +625,8 @@ qdse_options qdse_default_options(void) {
     o.max_iter = 20000;
     o.time_limit = 0.0;
     o.reuse_kernels = 0;
+    o.stall_window = 0;
+    o.stop_cycles = 1;
     o.stream = nullptr;
     return o;
 }
@@ -932,6 +947,32 @@ qdse_status qdse_last_work(const qdse_ctx* c, double* sweep_bytes, double* kerne
     if (e != cudaSuccess) return QDSE_ERR_CUDA;
     if (sweep_bytes) *sweep_bytes = (double)ctr[2];
     if (kernel_evals) *kernel_evals = (double)ctr[3];
+    return QDSE_OK;
+}
+
+qdse_status qdse_last_instance_stats(const qdse_ctx* c, long long* out, long long* out_cycles) {
+    if (!c || !out) return QDSE_ERR_ARG;
+    std::vector<DevState> st(c->n_inst);
+    std::vector<unsigned long long> nnz(c->n_inst);
+    cudaError_t e = cudaMemcpyAsync(st.data(), c->d_state, sizeof(DevState) * c->n_inst,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(nnz.data(), c->grid.nnz, sizeof(unsigned long long) * c->n_inst,
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return QDSE_ERR_CUDA;
+    for (int b = 0; b < c->n_inst; ++b) {
+        const DevState& s = st[b];
+        out[5 * (size_t)b + 0] = s.iters - s.n64;
+        out[5 * (size_t)b + 1] = s.n64;
+        out[5 * (size_t)b + 2] = s.stall_max;
+        out[5 * (size_t)b + 3] = c->k_valid_for ? (long long)nnz[b] : 0;
+        out[5 * (size_t)b + 4] = s.phase;
+        if (out_cycles) {
+            out_cycles[2 * (size_t)b] = s.cyc_p;
+            out_cycles[2 * (size_t)b + 1] = s.cyc_at;
+        }
+    }
     return QDSE_OK;
 }
 

@@ -5,6 +5,9 @@
 //   K_n(P_i, Q_j) = 8 pi^2/w^4 sum_k w_k exp(-k^2/w^2) g_n(P_i, Q_j, z_k),   n = 0, T, 3,
 //   g_0 = 1,  g_T = 2 P Q (1 - z^2)/k^2,  g_3 = [3 x (P + Q) - 4 x^2 - 2 P Q]/k^2,
 //   x = sqrt(P Q) z,  k^2 = (sqrt P - sqrt Q)^2 + 2 sqrt(P Q) (1 - z)  (no cancellation at z -> 1).
+// Since P + Q = k^2 + 2x, the numerator of g_3 is 3x k^2 - 2PQ(1 - z^2): g_3 = 3x - g_T exactly, so
+// K_3 = 3 sqrt(PQ) sum_k w_k E_k z_k - K_T, free of the cancellation of the numerator near the
+// diagonal (P = Q, z -> 1), where it vanishes with k^2.
 // The interaction strength D is factored out.  K_T only ever multiplies the difference quotients
 // (F(q^2) - F(p^2))/(q^2 - p^2), so the pool stores K_T/(Q_j - P_i) and the sweep multiplies it
 // by plain differences; on the collocated diagonal it stores K_T itself.
@@ -21,6 +24,10 @@
 // J >= I are evaluated, and each writes itself and its transpose (through shared memory, so both
 // stores are coalesced).  Staggered grids evaluate every tile.  Tiles whose pairs all have
 // (sqrt P - sqrt Q)^2 / w^2 beyond kSkipExponent are written as exact zeros without evaluation.
+#include <cmath>
+#include <vector>
+
+#include "f2.cuh"
 #include "qdse_internal.h"
 
 namespace qdse {
@@ -38,6 +45,50 @@ constexpr double kSkipExponent = 70.0;
 // (nodes down to theta = pi/129): the sum stops there.
 constexpr double kAngularCut = 60.0;
 
+// Writes one 32 x 32 tile of the three kernel planes into the pool (rows i0.., columns j0..) and,
+// for an off-diagonal tile of a collocated grid, its transpose (rows j0.., columns i0..; K_0 and
+// K_3 symmetric, K_T/(Q - P) odd).  val(p, idx, h, l) gives the (hi, lo) pair of plane p at tile
+// position idx = row * (kTile + 1) + column.  Threads walk the destination in layout order: row
+// group rg of the tile, 4-column block cb, stored plane-row slot (plane-row m = slot ^ kswz),
+// column inside the block; for full groups consecutive threads write consecutive floats.
+template <typename Val>
+__device__ __forceinline__ void store_tile(const DevInst& I, const Grid& g, const int4& t,
+                                           float* __restrict__ Hi, float* __restrict__ Lo,
+                                           bool diag, const Val& val) {
+    static_assert(kTile % kRows == 0 && kTile % 4 == 0,
+                  "precompute tiles must cover whole row groups and 4-column blocks");
+    constexpr int kRun = 3 * kRows * kTile;  // floats of one row group inside the tile
+    const int i0 = t.y * kTile, j0 = t.z * kTile;
+    const bool coll = (I.mode == QDSE_COLLOCATED);
+    const bool mirror = coll && t.z != t.y;
+    for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
+        const int rb0 = pass ? j0 : i0, cb0 = pass ? i0 : j0;
+        for (int e = threadIdx.x; e < 3 * kTile * kTile; e += blockDim.x) {
+            const int rg = e / kRun, off = e % kRun;
+            const int cb = off / (3 * kRows * 4), wq = off % (3 * kRows * 4);
+            const int slot = wq >> 2, cc = cb * 4 + (wq & 3);
+            const int g0 = rb0 + rg * kRows;
+            const int nr = min(kRows, I.n - g0);
+            const int j = cb0 + cc;
+            if (nr <= 0 || slot >= 3 * nr || j >= I.ld) continue;
+            const int m = slot ^ kswz(nr, j >> 2);
+            const int rr = rg * kRows + m / 3, p = m % 3, i = rb0 + rr;
+            float h = 0.f, l = 0.f;
+            if (j < I.n) {
+                val(p, pass ? cc * (kTile + 1) + rr : rr * (kTile + 1) + cc, h, l);
+                if (pass && p == 1) {
+                    h = -h;
+                    l = -l;
+                }
+            }
+            const long long idx = kpos(I.k_off, I.n, I.ld, i, p, j);
+            Hi[idx] = h;
+            Lo[idx] = l;
+            if (diag && coll && p == 1 && i == j) g.ktd[I.x_off + i] = h;
+        }
+    }
+}
+
 template <bool WITH_W>
 __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restrict__ inst, Grid g,
                                                           const int4* __restrict__ tiles,
@@ -54,13 +105,11 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
     double* sz = sy + I.nt;
     double* ss = sz + I.nt;
     double* sw = ss + I.nt;
-    double* sz2 = sw + I.nt;
     for (int k = threadIdx.x; k < I.nt; k += blockDim.x) {
         sy[k] = g.y[I.t_off + k];
         sz[k] = g.z[I.t_off + k];
         ss[k] = g.s2[I.t_off + k];
         sw[k] = g.wz[I.t_off + k];
-        sz2[k] = sz[k] * sz[k];
     }
     __syncthreads();
     const int i0 = t.y * kTile, j0 = t.z * kTile;
@@ -87,40 +136,33 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
             const double Q = g.sq[I.x_off + j], rQ = g.rsq[I.x_off + j];
             const double dd = (rP - rQ) * (rP - rQ);
             if (dd * iw2 < kSkipExponent) {
-                const double c2 = 2.0 * rP * rQ, x0 = rP * rQ, PQ = P * Q, PpQ = P + Q;
+                const double c2 = 2.0 * rP * rQ, x0 = rP * rQ, PQ = P * Q;
                 const double ex_last = (dd + c2 * sy[0]) * iw2 + kAngularCut;
-                // g_T and g_3 are polynomials in z over k^2 with pair-constant coefficients
-                // (x = sqrt(PQ) z): accumulate F = E/k^2 against 1 - z^2, 1, z, z^2 and form
-                // K_T = 2PQ sum(F (1 - z^2)), K_3 = 3 x0 (P+Q) sum(F z) - 4 x0^2 sum(F z^2)
-                // - 2PQ sum(F) once per pair (likewise for the w-derivatives, G = F f)
-                double Fs = 0.0, F1 = 0.0, Fz = 0.0, Fzz = 0.0;
-                double Gs = 0.0, G1 = 0.0, Gz = 0.0, Gzz = 0.0;
+                // g_3 = 3x - g_T (see the header): accumulate E against 1 and z and
+                // E (1 - z^2)/k^2, then K_T = 2PQ sum(E (1 - z^2)/k^2), K_3 = 3 x0 sum(E z) - K_T
+                // (likewise for the w-derivatives, every term times f)
+                double Sz = 0.0, St = 0.0, Wz = 0.0, Wt = 0.0;
                 for (int k = 0; k < I.nt; ++k) {
                     const double k2 = dd + c2 * sy[k];
                     const double ex = k2 * iw2;
                     if (ex > ex_last) break;
                     const double E = sw[k] * exp(-ex);
-                    const double F = E / k2;
+                    const double T = E * ss[k] / k2;
                     K0 += E;
-                    F1 += F;
-                    Fs = fma(F, ss[k], Fs);
-                    Fz = fma(F, sz[k], Fz);
-                    Fzz = fma(F, sz2[k], Fzz);
+                    Sz = fma(E, sz[k], Sz);
+                    St += T;
                     if (WITH_W) {
                         const double f = fw0 + fw1 * k2;
-                        const double G = F * f;
                         W0 = fma(E, f, W0);
-                        G1 += G;
-                        Gs = fma(G, ss[k], Gs);
-                        Gz = fma(G, sz[k], Gz);
-                        Gzz = fma(G, sz2[k], Gzz);
+                        Wz = fma(E * f, sz[k], Wz);
+                        Wt = fma(T, f, Wt);
                     }
                 }
-                KT = 2.0 * PQ * Fs;
-                K3 = 3.0 * x0 * PpQ * Fz - 4.0 * x0 * x0 * Fzz - 2.0 * PQ * F1;
+                KT = 2.0 * PQ * St;
+                K3 = 3.0 * x0 * Sz - KT;
                 if (WITH_W) {
-                    WT = 2.0 * PQ * Gs;
-                    W3 = 3.0 * x0 * PpQ * Gz - 4.0 * x0 * x0 * Gzz - 2.0 * PQ * G1;
+                    WT = 2.0 * PQ * Wt;
+                    W3 = 3.0 * x0 * Wz - WT;
                 }
                 const double dq = (coll && i == j) ? 1.0 : 1.0 / (Q - P);
                 K0 *= pref;
@@ -145,45 +187,101 @@ __global__ void __launch_bounds__(256) k_precompute_tiles(const DevInst* __restr
     }
     __syncthreads();
     // store the tile (rows i, columns j) and, for an off-diagonal symmetric tile, its transpose
-    const int nsets = WITH_W ? 2 : 1;
-    const bool mirror = coll && t.z != t.y;
-    // Threads walk the destination in layout order: row group rg of the tile, 4-column block
-    // cb, stored plane-row slot (plane-row m = slot ^ kswz), column inside the block; for full
-    // groups consecutive threads write consecutive floats.
-    static_assert(kTile % kRows == 0 && kTile % 4 == 0,
-                  "precompute tiles must cover whole row groups and 4-column blocks");
-    constexpr int kRun = 3 * kRows * kTile;  // floats of one row group inside the tile
-    for (int set = 0; set < nsets; ++set) {
-        float* Hi = set ? Kwhi : Khi;
-        float* Lo = set ? Kwlo : Klo;
+    for (int set = 0; set < (WITH_W ? 2 : 1); ++set) {
         const double* T = tileK + set * 3 * S;
-        for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
-            // pass 0: rows i0.., columns j0..; pass 1 (mirror): rows j0.., columns i0.., the
-            // transposed values (K_0, K_3 symmetric, K_T/(Q-P) odd)
-            const int rb0 = pass ? j0 : i0, cb0 = pass ? i0 : j0;
-            for (int e = threadIdx.x; e < 3 * kTile * kTile; e += blockDim.x) {
-                const int rg = e / kRun, off = e % kRun;
-                const int cb = off / (3 * kRows * 4), wq = off % (3 * kRows * 4);
-                const int slot = wq >> 2, cc = cb * 4 + (wq & 3);
-                const int g0 = rb0 + rg * kRows;
-                const int nr = min(kRows, I.n - g0);
-                const int j = cb0 + cc;
-                if (nr <= 0 || slot >= 3 * nr || j >= I.ld) continue;
-                const int m = slot ^ kswz(nr, j >> 2);
-                const int rr = rg * kRows + m / 3, p = m % 3, i = rb0 + rr;
-                double v = 0.0;
-                if (j < I.n) {
-                    v = pass ? T[p * S + cc * (kTile + 1) + rr] : T[p * S + rr * (kTile + 1) + cc];
-                    if (pass && p == 1) v = -v;
-                }
-                const float h = __double2float_rn(v);
-                const long long idx = kpos(I.k_off, I.n, I.ld, i, p, j);
-                Hi[idx] = h;
-                Lo[idx] = __double2float_rn(v - (double)h);
-                if (set == 0 && coll && p == 1 && i == j) g.ktd[I.x_off + i] = h;
+        store_tile(I, g, t, set ? Kwhi : Khi, set ? Kwlo : Klo, set == 0,
+                   [&](int p, int idx, float& h, float& l) {
+                       const double v = T[p * S + idx];
+                       h = __double2float_rn(v);
+                       l = __double2float_rn(v - (double)h);
+                   });
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// The same kernel matrices on the FP32 pipe.  GB300 issues FP64 at about 1/73 of its FP32 rate, and
+// the FP64 kernel above spends nearly all of its time in the FP64 exp and division of every angular
+// term.  Here each term is evaluated in double-float arithmetic: a value is the unevaluated sum
+// h + l of two floats with |l| <= ulp(h)/2 (48 significant bits, relative precision about 4e-15),
+// built from the error-free transformations of a sum (Knuth's TwoSum: a + b = s + e exactly) and of
+// a product (with a fused multiply-add, a b = p + e exactly, e = fma(a, b, -p)).  The stored pair
+// (hi, lo) is the double-float result itself.
+//
+// The arithmetic of one pair is qf2::pair_entries (f2.cuh).  Pairs whose first angular term already
+// has exp(-k^2/w^2) < e^-87.5 (below the FP32 range) are stored as zeros; the FP64 kernel stores
+// values of that order there, which move a sweep's A and B by less than 1e-30 of their values.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_precompute_tiles_f2(const DevInst* __restrict__ inst,
+                                                             Grid g,
+                                                             const int4* __restrict__ tiles,
+                                                             float* __restrict__ Khi,
+                                                             float* __restrict__ Klo) {
+    extern __shared__ float2 smf[];
+    constexpr int S = kTile * (kTile + 1);
+    float2* tileK = smf;                      // [plane][32][33] pairs
+    const int4 t = tiles[blockIdx.x];
+    const DevInst I = inst[t.x];
+    float2* ta = tileK + 3 * S;               // exp tables (qf2::exp_neg)
+    float2* tb = ta + qf2::kExpA;
+    float2* sdy = tb + qf2::kExpB;            // per node: y_k - y_0, w_k, w_k z_k, w_k (1 - z_k^2)
+    float2* sw = sdy + I.nt;
+    float2* swz = sw + I.nt;
+    float2* sws = swz + I.nt;
+    for (int k = threadIdx.x; k < qf2::kExpA + qf2::kExpB; k += blockDim.x) ta[k] = g.expt[k];
+    for (int k = threadIdx.x; k < I.nt; k += blockDim.x) {
+        const double y = g.y[I.t_off + k], w = g.wz[I.t_off + k];
+        const qf2::f2 a = qf2::of(y - g.y[I.t_off]), b = qf2::of(w),
+                      c = qf2::of(w * g.z[I.t_off + k]), d = qf2::of(w * g.s2[I.t_off + k]);
+        sdy[k] = make_float2(a.h, a.l);
+        sw[k] = make_float2(b.h, b.l);
+        swz[k] = make_float2(c.h, c.l);
+        sws[k] = make_float2(d.h, d.l);
+    }
+    __syncthreads();
+    const int i0 = t.y * kTile, j0 = t.z * kTile;
+    const double w = I.omega;
+    const double iw2 = 1.0 / (w * w);
+    const double pref = 8.0 * kPi * kPi / (w * w * w * w);
+    const double y0 = g.y[I.t_off];
+    const bool coll = (I.mode == QDSE_COLLOCATED);
+    bool skip_tile;
+    {
+        const int i1 = min(i0 + kTile, I.n) - 1, j1 = min(j0 + kTile, I.n) - 1;
+        const double pl = g.rsp[I.x_off + i0], ph = g.rsp[I.x_off + i1];
+        const double ql = g.rsq[I.x_off + j0], qh = g.rsq[I.x_off + j1];
+        const double gap = fmax(0.0, fmax(ql - ph, pl - qh));
+        skip_tile = gap * gap * iw2 >= kSkipExponent;
+    }
+    const float* fta = reinterpret_cast<const float*>(ta);
+    const float* ftb = reinterpret_cast<const float*>(tb);
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int li = e / kTile, lj = e % kTile;
+        const int i = i0 + li, j = j0 + lj;
+        qf2::f2 K0 = {0.f, 0.f}, KT = {0.f, 0.f}, K3 = {0.f, 0.f};
+        if (!skip_tile && i < I.n && j < I.n) {
+            const double P = g.sp[I.x_off + i], rP = g.rsp[I.x_off + i];
+            const double Q = g.sq[I.x_off + j], rQ = g.rsq[I.x_off + j];
+            if ((rP - rQ) * (rP - rQ) * iw2 < kSkipExponent &&
+                qf2::pair_entries(P, Q, rP, rQ, y0, iw2, pref, kAngularCut, I.nt,
+                                  reinterpret_cast<const float*>(sdy),
+                                  reinterpret_cast<const float*>(sw),
+                                  reinterpret_cast<const float*>(swz),
+                                  reinterpret_cast<const float*>(sws), fta, ftb, K0, KT, K3) &&
+                !(coll && i == j)) {
+                KT = qf2::div(KT, qf2::of(Q - P));
             }
         }
+        const int o = li * (kTile + 1) + lj;
+        tileK[0 * S + o] = make_float2(K0.h, K0.l);
+        tileK[1 * S + o] = make_float2(KT.h, KT.l);
+        tileK[2 * S + o] = make_float2(K3.h, K3.l);
     }
+    __syncthreads();
+    store_tile(I, g, t, Khi, Klo, true, [&](int p, int idx, float& h, float& l) {
+        const float2 v = tileK[p * S + idx];
+        h = v.x;
+        l = v.y;
+    });
 }
 
 // Row bands: the nonzero entries of row i are the j with (sqrt P_i - sqrt Q_j)^2 / w^2 below the
@@ -241,6 +339,11 @@ cudaError_t launch_precompute(qdse_ctx* c, bool with_w) {
     if (with_w) {
         k_precompute_tiles<true><<<c->n_tiles, 256, smem, c->stream>>>(
             c->d_inst, c->grid, c->d_tiles, c->d_Khi, c->d_Klo, c->d_Kwhi, c->d_Kwlo);
+    } else if (c->precompute_kind == 1) {
+        const size_t smem_f2 = (3 * kTile * (kTile + 1) + qf2::kExpA + qf2::kExpB + 4 * (size_t)c->max_nt) *
+                               sizeof(float2);
+        k_precompute_tiles_f2<<<c->n_tiles, 256, smem_f2, c->stream>>>(
+            c->d_inst, c->grid, c->d_tiles, c->d_Khi, c->d_Klo);
     } else {
         k_precompute_tiles<false><<<c->n_tiles, 256, smem, c->stream>>>(
             c->d_inst, c->grid, c->d_tiles, c->d_Khi, c->d_Klo, nullptr, nullptr);
@@ -263,7 +366,18 @@ cudaError_t configure_precompute(int max_nt) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_precompute_tiles<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem_f2 =
+        (3 * kTile * (kTile + 1) + qf2::kExpA + qf2::kExpB + 4 * (size_t)max_nt) * sizeof(float2);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_precompute_tiles_f2,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f2);
     return e;
+}
+
+// Host tables of qf2::exp_neg (exp(-a/4) and exp(-b/512) as (hi, lo) pairs of the FP64 values).
+void exp_tables(std::vector<float2>& out) {
+    out.resize(qf2::kExpA + qf2::kExpB);
+    qf2::exp_tables(reinterpret_cast<float*>(out.data()));
 }
 
 }  // namespace qdse

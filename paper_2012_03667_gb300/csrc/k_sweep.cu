@@ -102,6 +102,19 @@ struct BlockTeam {
         return warp_maxf(v);  // every warp reduces the per-warp maxima itself
     }
     __device__ bool any(bool v) const { return __syncthreads_or(v) != 0; }
+    // XOR of v over the block (every thread gets it)
+    __device__ unsigned long long xor_all(unsigned long long v) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
+        auto* u = reinterpret_cast<unsigned long long*>(sh);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) u[threadIdx.x >> 5] = v;
+        __syncthreads();
+        v = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v ^= u[k];
+        __syncthreads();
+        return v;
+    }
     __device__ bool leader() const { return threadIdx.x == 0; }
     // the leader's v to every thread
     __device__ int bcast(int v) const {
@@ -606,42 +619,73 @@ __global__ void k_group_bands(Grid g, int ngroups) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// FP64 on-the-fly sweep: the full (j, theta) double sum of Eqs. dsesys/dsesys2 for every point,
-// with exp() per term and no precomputed kernel matrices.  One block per external point.
+// FP64 on-the-fly sweep: the (j, theta) double sum of Eqs. dsesys/dsesys2 for every point, with
+// exp() per term and no precomputed kernel matrices.  One warp per external point; lanes stride
+// over the internal nodes of the row's band, the j with (sqrt P - sqrt Q)^2 / w^2 < kOtfSkip:
+// every term of any other pair carries exp(-k^2/w^2) <= e^-70 and moves the row's sum by less than
+// 1e-20 of it (the argument of the precompute's bands).  Inside a pair the exponents k^2/w^2 grow
+// with the node index, and the angular sum stops once a term's exponent exceeds the first one's by
+// kOtfCut.  With k^2 = P + Q - 2x, 3x(P + Q) - 4x^2 - 2PQ = 3x k^2 - 2PQ(1 - z^2), so
+// g_3 = 3x - g_T exactly: each term adds E = w_k exp(-k^2/w^2) against 1 and z and E(1 - z^2)/k^2
+// (one exp and one division), and K_3 = 3 sqrt(PQ) sum(E z) - K_T has no cancellation near the
+// diagonal (where the numerator of g_3 vanishes with k^2).
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ inst,
-                                                   const DevState* __restrict__ state,
-                                                   const Ctl* __restrict__ ctl, Grid g, Work w,
-                                                   const double* __restrict__ A,
-                                                   const double* __restrict__ B,
-                                                   double* __restrict__ FA,
-                                                   double* __restrict__ FB, int ntot,
-                                                   int only_active) {
-    extern __shared__ double sm[];
-    const int r = blockIdx.x;
+constexpr double kOtfSkip = 70.0;
+constexpr double kOtfCut = 60.0;
+
+// The band [jlo, jhi) of row P (sqrt P = rP) over the increasing internal nodes rq[0..n).
+__device__ __forceinline__ int2 otf_band(double rP, const double* __restrict__ rq, int n,
+                                         double iw2) {
+    auto inside = [&](int j) { return (rP - rq[j]) * (rP - rq[j]) * iw2 < kOtfSkip; };
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (rq[mid] < rP) lo = mid;
+        else hi = mid;
+    }
+    const int c = (fabs(rq[lo] - rP) <= fabs(rq[hi] - rP)) ? lo : hi;
+    if (!inside(c)) return make_int2(0, 0);
+    int a = -1, in = c;
+    while (in - a > 1) {
+        const int mid = (a + in) / 2;
+        if (inside(mid)) in = mid;
+        else a = mid;
+    }
+    int in2 = c, out = n;
+    while (out - in2 > 1) {
+        const int mid = (in2 + out) / 2;
+        if (inside(mid)) in2 = mid;
+        else out = mid;
+    }
+    return make_int2(in, in2 + 1);
+}
+
+constexpr int kOtfRowsPerBlock = 8;
+
+__global__ void __launch_bounds__(32 * kOtfRowsPerBlock)
+    k_sweep_otf(const DevInst* __restrict__ inst, const DevState* __restrict__ state,
+                const Ctl* __restrict__ ctl, Grid g, Work w, const double* __restrict__ A,
+                const double* __restrict__ B, double* __restrict__ FA, double* __restrict__ FB,
+                int ntot, int only_active) {
+    const int r = blockIdx.x * kOtfRowsPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= ntot) return;
     const int b = g.row_inst[r];
     if (only_active && state[b].phase == PH_DONE) return;
     const DevInst I = inst[b];
     const int i = r - I.x_off;
-    double* sy = sm;
-    double* sz = sm + I.nt;
-    double* ss = sm + 2 * I.nt;
-    double* sw = sm + 3 * I.nt;
-    double* red = sm + 4 * I.nt;
-    for (int k = threadIdx.x; k < I.nt; k += blockDim.x) {
-        sy[k] = g.y[I.t_off + k];
-        sz[k] = g.z[I.t_off + k];
-        ss[k] = g.s2[I.t_off + k];
-        sw[k] = g.wz[I.t_off + k];
-    }
-    __syncthreads();
+    const double* __restrict__ ty = g.y + I.t_off;
+    const double* __restrict__ tz = g.z + I.t_off;
+    const double* __restrict__ ts = g.s2 + I.t_off;
+    const double* __restrict__ tw = g.wz + I.t_off;
     const int vertex = ctl->vertex;
     const double P = g.sp[r], rP = g.rsp[r];
     const double Ai = A[r], Bi = B[r];
     const double iw2 = 1.0 / (I.omega * I.omega);
     const double pref = 8.0 * kPi * kPi * I.D / (I.omega * I.omega * I.omega * I.omega);
+    const int2 band = otf_band(rP, g.rsq + I.x_off, I.n, iw2);
     double sA = 0.0, sB = 0.0;
-    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+    for (int j = band.x + lane; j < band.y; j += 32) {
         const int gj = I.x_off + j;
         const double a = w.vec64[gj], bq = w.vec64[ntot + gj];
         const double Q = g.sq[gj], rQ = g.rsq[gj];
@@ -657,16 +701,19 @@ __global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ i
         const double SA = 0.5 * (Ai + a);
         const double dd = (rP - rQ) * (rP - rQ), c2 = 2.0 * rP * rQ, x0 = rP * rQ;
         const double PQ = P * Q, PpQ = P + Q;
-        double S0 = 0.0, ST = 0.0, S3 = 0.0;
+        const double ex_last = (dd + c2 * ty[0]) * iw2 + kOtfCut;
+        double S0 = 0.0, Sz = 0.0, St = 0.0;
         for (int k = 0; k < I.nt; ++k) {
-            const double k2 = dd + c2 * sy[k];
-            const double E = sw[k] * exp(-k2 * iw2);
-            const double rk = 1.0 / k2;
-            const double x = x0 * sz[k];
+            const double k2 = dd + c2 * ty[k];
+            const double ex = k2 * iw2;
+            if (ex > ex_last) break;
+            const double E = tw[k] * exp(-ex);
             S0 += E;
-            ST += E * 2.0 * PQ * ss[k] * rk;
-            S3 += E * (3.0 * x * PpQ - 4.0 * x * x - 2.0 * PQ) * rk;
+            Sz = fma(E, tz[k], Sz);
+            St += E * ts[k] / k2;
         }
+        const double ST = 2.0 * PQ * St;
+        const double S3 = 3.0 * x0 * Sz - ST;
         if (vertex == QDSE_VERTEX_BC) {
             sA += e * ((-bq * qB - 0.5 * PpQ * a * qA) * ST + a * SA * S3);
             sB += e * ((-a * qB + bq * qA) * ST + 3.0 * bq * SA * S0);
@@ -675,9 +722,9 @@ __global__ void __launch_bounds__(128) k_sweep_otf(const DevInst* __restrict__ i
             sB += 3.0 * e * bq * S0;
         }
     }
-    sA = block_sum(sA, red);
-    sB = block_sum(sB, red);
-    if (threadIdx.x == 0) {
+    sA = warp_sum(sA);
+    sB = warp_sum(sB);
+    if (lane == 0) {
         FA[r] = 1.0 + ctl->kappa * pref * sA / P;
         FB[r] = I.m + ctl->kappa * pref * sB;
     }
@@ -729,7 +776,16 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         s.change = INFINITY;
         s.dnorm = INFINITY;
         s.loc = (phase0 == PH_PICARD32) ? 1 : 0;
-        s.pad = 0;
+        s.n64 = 0;
+        s.cbest = INFINITY;
+        s.since = 0;
+        s.stall_max = 0;
+        s.nh = 0;
+        s.href = 0;
+        s.iref = 0;
+        s.plen = 1;
+        s.cyc_p = 0;
+        s.cyc_at = 0;
         state[b] = s;
         w.ilist[atomicAdd(w.lcount + 0, 1)] = b;
         const int ng = (I.n + kRows - 1) / kRows;
@@ -738,6 +794,93 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
     }
     for (int t = threadIdx.x; t < (I.n + kRows - 1) / kRows; t += blockDim.x) g.gphase[I.g_off + t] = phase0;
     prepare_phase(phase0, I, g, w, ntot, A, B);
+}
+
+// Iterate hashes for the cycle stop.  Every point contributes the SplitMix64 finaliser (Steele, Lea,
+// Flood 2014) of its bit pattern offset by its index; the contributions are combined by XOR, so
+// the hash does not depend on the order of the block reduction.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long point_hash32(float a, float b, int j) {
+    const unsigned long long v = ((unsigned long long)__float_as_uint(a) << 32) |
+                                 (unsigned long long)__float_as_uint(b);
+    return mix64(v + (unsigned long long)(j + 1) * 0x9E3779B97F4A7C15ull);
+}
+__device__ __forceinline__ unsigned long long point_hash64(double a, double b, int j) {
+    const unsigned long long k = (unsigned long long)(2 * j + 1) * 0x9E3779B97F4A7C15ull;
+    return mix64((unsigned long long)__double_as_longlong(a) + k) ^
+           mix64((unsigned long long)__double_as_longlong(b) + k + 0x9E3779B97F4A7C15ull);
+}
+
+// Cycle stop of a successive-approximation phase (leader thread).  One sweep of the batched solve
+// is a fixed function of the iterate alone (the sweep kernels and the update sum in a fixed
+// order), so once the iterate equals an earlier one of the same phase, the phase repeats that
+// stretch forever and can never reach the tolerance.  h is the hash of the new iterate; it is
+// compared with the last kHashRing hashes of the phase and with a reference hash that moves
+// forward after 1, 2, 4, ... hashes (Brent's cycle detection), so a cycle of any period p is found
+// within about 2 max(p, start of the cycle) sweeps, and one of period <= kHashRing as soon as it
+// has gone round once.  Equal hashes of different iterates (a 64-bit collision) would end an
+// instance early; over a batch of thousands of instances and thousands of sweeps that chance is
+// below 1e-10.  Returns the period found (0: none).
+__device__ __forceinline__ int cycle_check(DevState& s, unsigned long long h,
+                                           unsigned long long* ring) {
+    int period = 0;
+    const int valid = min(s.nh, kHashRing);
+    for (int k = 0; k < valid && !period; ++k) {
+        if (ring[k] == h) {
+            // entry k holds hash number t with t % kHashRing == k, the latest such t < nh
+            const int t = s.nh - 1 - ((s.nh - 1 - k) % kHashRing);
+            period = s.nh - t;
+        }
+    }
+    if (!period && s.nh > 0 && h == s.href) period = s.nh - s.iref;
+    ring[s.nh % kHashRing] = h;
+    if (s.nh == 0 || s.nh - s.iref >= s.plen) {
+        s.href = h;
+        s.iref = s.nh;
+        s.plen = (s.nh == 0) ? 1 : 2 * s.plen;
+    }
+    s.nh += 1;
+    return period;
+}
+
+// Progress of a successive-approximation phase: the lowest relative change reached so far and the
+// sweeps since it was set.  Returns true when the no-progress stop applies (stall_window > 0
+// consecutive sweeps without a new lowest change).  Only the leader's copy of the state is
+// stored, and every thread computes the same values.
+__device__ __forceinline__ bool track_progress(DevState& s, const Ctl& C) {
+    const float c = (float)s.change;
+    if (c < s.cbest) {
+        s.cbest = c;
+        s.since = 0;
+    } else {
+        s.since += 1;
+        if (s.since > s.stall_max) s.stall_max = s.since;
+    }
+    return C.stall_window > 0 && !C.never_converge && s.since >= C.stall_window;
+}
+
+// The block's hash of the new iterate (h: this thread's part) through cycle_check; true when the
+// cycle stop applies.  Every thread of the team gets the same answer.
+template <typename Team>
+__device__ __forceinline__ bool picard_cycle(const Team& T, DevState& s, const Ctl& C,
+                                             unsigned long long h, unsigned long long* ring) {
+    if (!C.stop_cycles || C.never_converge) return false;
+    h = T.xor_all(h);
+    int period = 0;
+    if (T.leader()) {
+        period = cycle_check(s, h, ring);
+        if (period && !s.cyc_p) {
+            s.cyc_p = period;
+            s.cyc_at = s.iters;
+        }
+    } else {
+        s.nh += 1;  // keep every thread's copy of the count in step (only the leader's is stored)
+    }
+    return T.bcast(period) != 0;
 }
 
 // Advance one instance after a tick.  One block (256 threads) per instance.
@@ -800,6 +943,7 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         const bool bad = T.any(badj);
         const float fl = 1e-12f * bmax;
         float ch = 0.f;
+        unsigned long long hsh = 0;
         for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
             const float xa = w.x32[gj], xb = w.x32[ntot + gj];
@@ -808,12 +952,18 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             ch = fmaxf(ch, fmaxf(rel_change32(fa - xa, fa, 0.f), rel_change32(fb - xb, fb, fl)));
             w.x32[gj] = fa;
             w.x32[ntot + gj] = fb;
+            hsh ^= point_hash32(fa, fb, j);
         }
         s.change = (double)T.maxf(ch);
         s.iters += 1;
+        const bool stalled = track_progress(s, C);
+        const bool cycled = picard_cycle(T, s, C, hsh, w.hring + (size_t)b * kHashRing);
         if (bad) {
             done = true;
             status = QDSE_ERR_NONFINITE;
+        } else if (stalled || cycled) {
+            done = true;
+            status = QDSE_ERR_NOT_CONVERGED;
         } else if (C.final_phase == PH_PICARD32) {
             // FP32-only solves finish here; mixed solves always finish in FP64
             if (!C.never_converge && s.change <= C.tol) {
@@ -842,6 +992,7 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         bad = T.max(bad);
         const double fl = 1e-12 * bmax;
         double ch = 0.0;
+        unsigned long long hsh = 0;
         for (int j = T.tid(); j < I.n; j += T.size()) {
             const int gj = o + j;
             double fa = __ldcg(w.xn64 + gj);
@@ -855,6 +1006,7 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             if (s.phase == PH_PICARD64) {
                 A[gj] = fa;
                 B[gj] = fb;
+                hsh ^= point_hash64(fa, fb, j);
             } else {  // residual: keep r = F(x) - x for the correction solve
                 w.r64[gj] = fa - xa;
                 w.r64[ntot + gj] = fb - xb;
@@ -863,12 +1015,19 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         ch = T.max(ch);
         s.change = ch;
         s.iters += 1;
+        s.n64 += 1;
+        const bool stalled = (s.phase == PH_PICARD64) &&
+                             (track_progress(s, C) ||
+                              picard_cycle(T, s, C, hsh, w.hring + (size_t)b * kHashRing));
         if (bad != 0.0) {
             done = true;
             status = QDSE_ERR_NONFINITE;
         } else if (!C.never_converge && ch <= C.tol) {
             done = true;
             status = QDSE_OK;
+        } else if (stalled) {
+            done = true;
+            status = QDSE_ERR_NOT_CONVERGED;
         }
         if (s.phase == PH_RESID64) {
             if (done && status == QDSE_OK) {
@@ -954,6 +1113,13 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
     }
     for (int t = T.tid(); t < (I.n + kRows - 1) / kRows; t += T.size()) g.gphase[I.g_off + t] = next;
     if (T.leader()) {
+        if (next != s.phase) {  // a new phase starts its own progress and cycle records
+            s.cbest = INFINITY;
+            s.since = 0;
+            s.nh = 0;
+            s.iref = 0;
+            s.plen = 1;
+        }
         s.phase = next;
         s.status = status;
         if (next == PH_PICARD32) s.loc = 1;
@@ -1679,11 +1845,10 @@ cudaError_t launch_update(qdse_ctx* c, double* A, double* B) {
 
 cudaError_t launch_sweep_otf(qdse_ctx* c, const double* A, const double* B, double* FA,
                              double* FB, int only_active) {
-    const size_t smem = (4 * (size_t)c->max_nt + 32) * sizeof(double);
     prof_begin(c, PK_SWEEP);
-    k_sweep_otf<<<c->n_total, 128, smem, c->stream>>>(c->d_inst, c->d_state, c->d_ctl, c->grid,
-                                                      c->work, A, B, FA, FB, c->n_total,
-                                                      only_active);
+    const int blocks = (c->n_total + kOtfRowsPerBlock - 1) / kOtfRowsPerBlock;
+    k_sweep_otf<<<blocks, 32 * kOtfRowsPerBlock, 0, c->stream>>>(
+        c->d_inst, c->d_state, c->d_ctl, c->grid, c->work, A, B, FA, FB, c->n_total, only_active);
     c->launches++;
     prof_end(c);
     return cudaGetLastError();

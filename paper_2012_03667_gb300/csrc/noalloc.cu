@@ -16,6 +16,7 @@
 // values) before reading it, so nothing depends on a previous call's contents.  All calls share
 // the one array: calls whose work overlaps on the GPU (two streams, or two host threads) race on it
 // and must be serialised by the caller.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -32,10 +33,14 @@ constexpr int kNoallocMaxTheta = 256;
 constexpr int kNoallocDoubles = 16384;
 static_assert(15 * kNoallocMaxN + 4 * kNoallocMaxTheta <= kNoallocDoubles, "scratch too small");
 
-__device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
 
+// Device address of g_noalloc_scratch per device index, looked up on the first call on that
+// device.  Atomic slots: concurrent first calls from several host threads store the same value.
+// A cudaDeviceReset unloads the module, so the address may change afterwards: the cache is not
+// valid across a reset (documented at the declaration in qdse.h).
 constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
 
 // Legendre P_n and P_n' by the three-term recurrence.
 __device__ void na_legendre(int n, double x, double& p, double& dp) {
@@ -261,17 +266,17 @@ extern "C" qdse_status qdse_sweep_fp64_noalloc(const qdse_grid* g, const qdse_pa
         na_error(errbuf, errbuf_len, "qdse_sweep_fp64_noalloc: no usable current device");
         return QDSE_ERR_CUDA;
     }
-    if (!g_scratch_ptr[dev]) {
+    void* cached = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!cached) {
         // first call on this device: look up the device address of the scratch array
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
+        e = cudaGetSymbolAddress(&cached, g_noalloc_scratch);
+        if (e != cudaSuccess || !cached) {
             na_error(errbuf, errbuf_len, "qdse_sweep_fp64_noalloc: cudaGetSymbolAddress failed");
             return QDSE_ERR_CUDA;
         }
-        g_scratch_ptr[dev] = ptr;
+        g_scratch_ptr[dev].store(cached, std::memory_order_release);
     }
-    double* scratch = static_cast<double*>(g_scratch_ptr[dev]);
+    double* scratch = static_cast<double*>(cached);
     cudaStream_t s = (cudaStream_t)stream;
     k_na_setup<<<1, kNoallocMaxN, 0, s>>>(scratch, *g, A, B);
     e = cudaGetLastError();

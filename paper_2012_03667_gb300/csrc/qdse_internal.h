@@ -67,8 +67,17 @@ struct DevState {         // per-instance solver state, updated by the update ke
     double change;        // last R7 relative change (Picard) or residual
     double dnorm;         // last relative change of the correction (inner solve)
     int loc;              // 1 if the current iterate lives in the FP32 copy, 0 if in A, B
-    int pad;
+    int n64;              // FP64 sweeps (Picard and refinement residuals) of this solve
+    float cbest;          // lowest relative change of the current Picard phase
+    int since;            // Picard sweeps since cbest was set
+    int stall_max;        // longest such run of this solve
+    int nh;               // iterate hashes recorded in the current Picard phase
+    unsigned long long href;  // cycle detection (Brent): the reference hash, recorded at hash
+    int iref, plen;           // number iref; it moves after plen more hashes, plen doubling
+    int cyc_p, cyc_at;        // period of a detected cycle and the sweep that found it (0: none)
 };
+constexpr int kHashRing = 16;  // recent iterate hashes per instance (cycles of period <= 16 are
+                               // found one period after they start; longer ones by Brent's rule)
 
 struct Ctl {              // solver controls shared by every instance of a call
     double kappa;         // C_F / (8 pi^3)
@@ -85,6 +94,8 @@ struct Ctl {              // solver controls shared by every instance of a call
     int never_converge;   // 1 for qdse_iterate (run exactly max_iter sweeps)
     int stall_copies;     // test of the bounded waits: the ring sweep expects 16 bytes more than
                           // it copies per tile, so each tile wait runs out (QDSE_TEST_STALL=1)
+    int stall_window;     // no-progress stop of the Picard phases (0 = off)
+    int stop_cycles;      // end a Picard phase whose iterate repeats exactly (0 = off)
 };
 
 // Work arrays (device).  Component counts in brackets, each of length n_total.
@@ -114,6 +125,7 @@ struct Work {
     int* ilist;     // [3][n_inst]
     int* glist;     // [3][n_groups]
     int* lcount;    // [6]
+    unsigned long long* hring;  // [n_inst][kHashRing] recent iterate hashes (cycle detection)
     int n_inst;
     int n_groups;
 };
@@ -146,6 +158,8 @@ struct Grid {              // FP64 grid arrays on the device (global point index
                               // sweep must read per plane)
     float* ktd;            // per external point: K_T at q = p (collocated grids; the entry the
                            // removable-limit term multiplies), 0 on staggered grids
+    float2* expt;          // exp(-a/4) and exp(-b/512) as (hi, lo) pairs for the FP32-pipe
+                           // precompute (see k_precompute.cu)
 };
 
 constexpr int kRows = 4;   // external points per warp in the batched sweeps (1, 2 or 4)
@@ -272,6 +286,7 @@ struct qdse_ctx {
     int ld_max = 0;           // widest kernel row of the batch
     int sweep_kind = 0;       // FP32 sweep: 1 ring (bulk copies through shared memory, the
                               // default), 0 register-only row groups
+    int precompute_kind = 1;  // kernel matrices: 1 double-float on the FP32 pipe (default), 0 FP64
     int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
     double* d_rel = nullptr;  // [n_inst] relative residual of the adjoint's fixed point
     // CUDA graph of a chunk of ticks, replayed between polls (captured on an internal stream)
@@ -316,6 +331,7 @@ void build_angular(int nt, double* z, double* y, double* s2, double* w);
 // ---- kernel launchers (return cudaError_t of the launch) -------------------------------------
 cudaError_t launch_precompute(qdse_ctx* c, bool with_omega_derivative);
 cudaError_t configure_precompute(int max_nt);
+void exp_tables(std::vector<float2>& out);
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B);

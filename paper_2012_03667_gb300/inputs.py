@@ -97,29 +97,28 @@ def params_array(batch: List[Instance]) -> np.ndarray:
 
 @dataclass
 class MuWorkload:
-    """A finite chemical potential sweep workload: external points (p_abs, p4) [n_ext], the product
-    grid of internal points (q_abs [n_r] x q4 [n_4], weights w_q [n_r * n_4] including
-    |q|^2 d|q| dq_4), the angular rule (z, w_z), the chemical potentials mu [n_mu] and the
-    interaction."""
+    """A finite chemical potential sweep workload: external points (p_abs, p4) [n_ext], the nodes
+    of the internal product grid (q_abs [n_r] x q4 [n_4]; |q| and |q_4| are Gauss-Legendre nodes
+    log-mapped onto [lo, hi]), the cosine nodes z (Gauss-Legendre on [-1, 1]), the chemical
+    potentials mu [n_mu] and the interaction.  Nodes only: each side forms its own weights."""
     p_abs: np.ndarray
     p4: np.ndarray
     q_abs: np.ndarray
     q4: np.ndarray
-    w_q: np.ndarray
     z: np.ndarray
-    w_z: np.ndarray
     mu: np.ndarray
     D: float
     omega: float
     m: float
+    lo: float
+    hi: float
 
 
-def _log_gl(n: int, lo: float, hi: float) -> Tuple[np.ndarray, np.ndarray]:
-    """n Gauss-Legendre nodes log-mapped onto [lo, hi] and the weights of dx there."""
-    t, v = np.polynomial.legendre.leggauss(n)
+def _log_gl_nodes(n: int, lo: float, hi: float) -> np.ndarray:
+    """n Gauss-Legendre nodes log-mapped onto [lo, hi]."""
+    t, _ = np.polynomial.legendre.leggauss(n)
     a, b = np.log(lo), np.log(hi)
-    x = np.exp(a + 0.5 * (t + 1.0) * (b - a))
-    return x, 0.5 * (b - a) * v * x
+    return np.exp(a + 0.5 * (t + 1.0) * (b - a))
 
 
 def mu_workload(n_r: int = 128, n_4: int = 128, n_z: int = 64, n_mu: int = 256,
@@ -132,17 +131,15 @@ def mu_workload(n_r: int = 128, n_4: int = 128, n_z: int = 64, n_mu: int = 256,
     ln |p|_i = (ln q_{i-1} + ln q_i)/2, likewise p_4 > 0 from the positive q_4 nodes, so
     n_ext = n_r * n_4 and no external point is an internal one.  mu ~ U[mu_range] from
     SplitMix64(seed ^ 0x6D75), in draw order."""
-    qr, wr = _log_gl(n_r, lo, hi)
-    q4p, w4p = _log_gl(n_4, lo, hi)
+    qr = _log_gl_nodes(n_r, lo, hi)
+    q4p = _log_gl_nodes(n_4, lo, hi)
     q4 = np.concatenate([-q4p[::-1], q4p])
-    w4 = np.concatenate([w4p[::-1], w4p])
-    w_q = np.outer(wr * qr ** 2, w4).ravel()
     stag = lambda x: np.concatenate([[lo], np.sqrt(x[:-1] * x[1:])])
     PR, P4 = np.meshgrid(stag(qr), stag(q4p), indexing="ij")
-    z, wz = np.polynomial.legendre.leggauss(n_z)
+    z, _ = np.polynomial.legendre.leggauss(n_z)
     rng = SplitMix64(seed ^ 0x6D75)
     mu = np.array([mu_range[0] + (mu_range[1] - mu_range[0]) * rng.uniform() for _ in range(n_mu)])
-    return MuWorkload(PR.ravel(), P4.ravel(), qr, q4, w_q, z, wz, mu, D, omega, m)
+    return MuWorkload(PR.ravel(), P4.ravel(), qr, q4, z, mu, D, omega, m, lo, hi)
 
 
 def mu_iterate(v_abs: np.ndarray, v4: np.ndarray, mu: float, m: float = 0.005) -> np.ndarray:

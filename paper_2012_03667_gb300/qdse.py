@@ -30,8 +30,8 @@ EXPORTS = ("qdse_default_options", "qdse_create", "qdse_create_ragged", "qdse_de
            "qdse_last_error", "qdse_sizes", "qdse_layout", "qdse_grid_nodes", "qdse_set_options",
            "qdse_iterate", "qdse_solve", "qdse_solve_host", "qdse_residual", "qdse_jvp",
            "qdse_vjp", "qdse_adjoint", "qdse_condensate", "qdse_condensate_vjp",
-           "qdse_last_stats", "qdse_last_work", "qdse_set_profiling", "qdse_profile",
-           "qdse_sweep_fp64_noalloc")
+           "qdse_last_stats", "qdse_last_work", "qdse_last_instance_stats",
+           "qdse_set_profiling", "qdse_profile", "qdse_sweep_fp64_noalloc")
 
 
 class qdse_grid(ctypes.Structure):
@@ -48,6 +48,7 @@ class qdse_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("vertex", ctypes.c_int), ("cf", ctypes.c_double),
                 ("tol", ctypes.c_double), ("alpha", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("time_limit", ctypes.c_double), ("reuse_kernels", ctypes.c_int),
+                ("stall_window", ctypes.c_int), ("stop_cycles", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qdse_last_stats": (ip, [vp, P(ctypes.c_longlong), P(ctypes.c_longlong),
                                  P(ctypes.c_longlong), P(ctypes.c_longlong)]),
         "qdse_last_work": (ip, [vp, P(dp), P(dp)]),
+        "qdse_last_instance_stats": (ip, [vp, vp, vp]),
         "qdse_set_profiling": (ip, [vp, ip]),
         "qdse_profile": (ip, [vp, P(dp), P(ctypes.c_longlong)]),
     }
@@ -161,12 +163,13 @@ class Context:
     def __init__(self, grid, n_inst: int = 1, precision: int = QDSE_MIXED,
                  vertex: int = QDSE_VERTEX_BC, cf: float = 4.0 / 3.0, tol: float = 1e-10,
                  alpha: float = 1.0, max_iter: int = 20000, time_limit: float = 0.0,
-                 reuse_kernels: int = 0):
+                 reuse_kernels: int = 0, stall_window: int = 0, stop_cycles: int = 1):
         self.lib = load_library()
         self.ptr = ctypes.c_void_p()
         o = self.lib.qdse_default_options()
         o.precision, o.vertex, o.cf, o.tol, o.alpha = precision, vertex, cf, tol, alpha
         o.max_iter, o.time_limit, o.reuse_kernels = max_iter, time_limit, reuse_kernels
+        o.stall_window, o.stop_cycles = stall_window, stop_cycles
         try:
             o.stream = _current_stream()
         except Exception:
@@ -276,6 +279,17 @@ class Context:
         b, e = ctypes.c_double(), ctypes.c_double()
         self._raise(self.lib.qdse_last_work(self.ptr, ctypes.byref(b), ctypes.byref(e)))
         return {"sweep_bytes": b.value, "kernel_evals": e.value}
+
+    def qdse_last_instance_stats(self) -> dict:
+        """Per-instance record of the last solve: FP32 and FP64 sweeps, the longest run of
+        Picard sweeps without a new lowest change, kernel entries per plane, final phase, and the
+        period of a cycle the cycle stop found with the sweep that found it."""
+        out = np.zeros((self.n_inst, 5), dtype=np.int64)
+        cyc = np.zeros((self.n_inst, 2), dtype=np.int64)
+        self._raise(self.lib.qdse_last_instance_stats(self.ptr, out.ctypes.data, cyc.ctypes.data))
+        return {"fp32_sweeps": out[:, 0], "fp64_sweeps": out[:, 1], "longest_stall": out[:, 2],
+                "nnz": out[:, 3], "phase": out[:, 4], "cycle_period": cyc[:, 0],
+                "cycle_found_at": cyc[:, 1]}
 
     def qdse_set_profiling(self, on: bool):
         self._raise(self.lib.qdse_set_profiling(self.ptr, int(bool(on))))

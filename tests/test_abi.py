@@ -79,7 +79,8 @@ def test_default_options(lib):
     o = lib.qdse_default_options()
     assert o.precision == Q.QDSE_MIXED and o.vertex == Q.QDSE_VERTEX_BC
     assert o.cf == pytest.approx(4 / 3) and o.tol == 1e-10 and o.alpha == 1.0
-    assert o.max_iter == 20000 and o.reuse_kernels == 0
+    assert o.max_iter == 20000 and o.reuse_kernels == 0 and o.stall_window == 0
+    assert o.stop_cycles == 1
 
 
 @pytest.mark.parametrize("grid,msg", [
@@ -101,7 +102,8 @@ def test_create_rejects_bad_grids(lib, grid, msg):
 
 @pytest.mark.parametrize("field,value", [("precision", 9), ("vertex", 3), ("cf", 0.0),
                                          ("tol", -1.0), ("alpha", 0.0), ("alpha", 1.5),
-                                         ("max_iter", 0), ("tol", float("inf"))])
+                                         ("max_iter", 0), ("tol", float("inf")),
+                                         ("stall_window", -1), ("stop_cycles", 2)])
 def test_create_rejects_bad_options(lib, field, value):
     o = lib.qdse_default_options()
     setattr(o, field, value)

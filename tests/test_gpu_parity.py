@@ -37,6 +37,17 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+def rel_pointwise(A, B, Ar, Br):
+    """Reading R7's pointwise form: max relative error of A at every point and of B and M = B/A at
+    the points where |B_i| >= 1e-6 max|B| (in the chiral limit B decays like exp(-p^2/w^2))."""
+    e = float((np.abs(A - Ar) / np.abs(Ar)).max())
+    keep = np.abs(Br) >= 1e-6 * np.abs(Br).max()
+    if keep.any():
+        e = max(e, float((np.abs(B - Br)[keep] / np.abs(Br)[keep]).max()),
+                float((np.abs(B / A - Br / Ar)[keep] / np.abs(Br / Ar)[keep]).max()))
+    return e
+
+
 def problem(inst, mode=O.COLLOCATED, vertex=O.BC):
     return O.Problem(n=inst.n_p, n_theta=inst.n_theta, s_min=inst.s_min, s_max=inst.s_max,
                      grid_mode=mode, vertex=vertex, D=inst.D, omega=inst.omega, m=inst.m)
@@ -176,6 +187,7 @@ def test_solve_matches_oracle_fixed_point(precision, tol, inst):
     eA, eB = rel(host(A), Ar), rel(host(B), Br)
     eM = rel(host(B) / host(A), Br / Ar)
     assert max(eA, eB, eM) < tol, (eA, eB, eM)
+    assert rel_pointwise(host(A), host(B), Ar, Br) < tol
 
 
 def test_staggered_solve_matches_oracle():
@@ -187,6 +199,7 @@ def test_staggered_solve_matches_oracle():
     ctx.qdse_solve(prm(inst), A, B, None, st)
     assert int(st.item()) == 0
     assert rel(host(A), Ar) < 1e-8 and rel(host(B), Br) < 1e-8
+    assert rel_pointwise(host(A), host(B), Ar, Br) < 1e-8
 
 
 def test_ragged_batch_matches_per_instance_oracle():
@@ -204,6 +217,31 @@ def test_ragged_batch_matches_per_instance_oracle():
         Ar, Br, _ = oracle_fixed_point(inst)
         sl = slice(x_off[b], x_off[b + 1])
         assert rel(Ah[sl], Ar) < 1e-8 and rel(Bh[sl], Br) < 1e-8, b
+        assert rel_pointwise(Ah[sl], Bh[sl], Ar, Br) < 1e-8, b
+
+
+SCAN_SHAPES = [inputs.Instance(384, 32, 0.55, 0.678, 0.005), inputs.Instance(512, 64, 0.6, 0.55, 0.02),
+               inputs.Instance(384, 64, 0.5, 0.6, 0.1), inputs.Instance(512, 32, 0.45, 0.7, 0.0)]
+
+
+def test_mixed_solve_matches_oracle_at_the_scan_shapes():
+    """The scan's large shapes (N_q = 384 and 512 with N_theta = 32 and 64) in one ragged batch, at
+    interactions below the BC fold (D omega <= 0.37), including the chiral limit m = 0: the mixed
+    solve against the oracle's fixed point to 1e-8, norm-relative and pointwise (R7)."""
+    ctx = Q.Context([grid(i) for i in SCAN_SHAPES], precision=Q.QDSE_MIXED, tol=1e-13,
+                    max_iter=40000)
+    x_off = ctx.layout()
+    A = dev(np.ones(ctx.n_total)); B = dev(np.full(ctx.n_total, 0.3))
+    st = torch.zeros(len(SCAN_SHAPES), dtype=torch.int32, device="cuda")
+    ctx.qdse_solve([[i.D, i.omega, i.m, 0] for i in SCAN_SHAPES], A, B, None, st)
+    Ah, Bh = host(A), host(B)
+    assert np.all(host(st) == 0)
+    for b, inst in enumerate(SCAN_SHAPES):
+        Ar, Br, _ = oracle_fixed_point(inst)
+        sl = slice(x_off[b], x_off[b + 1])
+        assert rel(Ah[sl], Ar) < 1e-8 and rel(Bh[sl], Br) < 1e-8, b
+        assert rel(Bh[sl] / Ah[sl], Br / Ar) < 1e-8, b
+        assert rel_pointwise(Ah[sl], Bh[sl], Ar, Br) < 1e-8, b
 
 
 LARGE_PAPER = inputs.Instance(512, 128, 0.55, 0.678, 0.005)
@@ -298,6 +336,28 @@ def test_adjoint_matches_oracle_adjoint():
     assert rel(host(lam), lam_ref) < 1e-10
     got = host(gp)
     np.testing.assert_allclose(got[:3], gp_ref[:3], rtol=1e-9)
+    assert got[3] == 0.0
+
+
+@pytest.mark.parametrize("inst", [inputs.Instance(256, 64, 0.55, 0.678, 0.02),
+                                  inputs.Instance(256, 64, 0.6, 0.55, 0.08)], ids=["paper", "scan"])
+def test_adjoint_matches_oracle_adjoint_at_the_adjoint_workload_shape(inst):
+    """N_q = 256, N_theta = 64 (the shape of the 1024-instance adjoint workload): lambda and the
+    parameter gradients of the GPU adjoint against the oracle's dense-LU adjoint."""
+    pr = problem(inst)
+    Ar, Br, it, ch, st = O.solve(pr, tol=1e-14, max_iter=20000, nthreads=O.max_threads())
+    assert st == 0
+    rng = np.random.default_rng(inst.n_p + int(100 * inst.D))
+    gA = rng.normal(size=inst.n_p); gB = rng.normal(size=inst.n_p)
+    gp_ref, lam_ref = O.adjoint(pr, Ar, Br, gA, gB, nthreads=O.max_threads())
+    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_MIXED, tol=1e-14, max_iter=40000)
+    gp = dev(np.zeros(4)); lam = dev(np.zeros(2 * inst.n_p))
+    ist = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_adjoint(prm(inst), dev(Ar), dev(Br), dev(gA), dev(gB), gp, lam, ist)
+    assert int(ist.item()) == 0
+    assert rel(host(lam), lam_ref) < 1e-9
+    got = host(gp)
+    np.testing.assert_allclose(got[:3], gp_ref[:3], rtol=1e-8)
     assert got[3] == 0.0
 
 

@@ -1,0 +1,91 @@
+"""GPU tests of the batched solver's own machinery (beyond parity with the oracle): the cycle stop
+on the full 4096-instance scan, and the FP32-pipe kernel precompute against the FP64 one."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2012_03667_gb300 import build as Bld
+from paper_2012_03667_gb300 import inputs
+from paper_2012_03667_gb300 import qdse as Q
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    Bld.build()
+    Q.load_library()
+    torch.cuda.set_device(0)
+
+
+def _solve_scan(batch, stop_cycles, max_iter=5000):
+    grids = [Q.Grid(b.n_p, b.n_theta, b.s_min, b.s_max) for b in batch]
+    ctx = Q.Context(grids, precision=Q.QDSE_MIXED, tol=1e-10, max_iter=max_iter,
+                    stop_cycles=stop_cycles)
+    n = ctx.n_total
+    A = torch.ones(n, dtype=torch.float64, device="cuda")
+    B = torch.full((n,), 0.3, dtype=torch.float64, device="cuda")
+    st = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    it = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    ctx.qdse_solve([[b.D, b.omega, b.m, 0.0] for b in batch], A, B, it, st)
+    out = (A.cpu().numpy(), B.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy(),
+           ctx.qdse_last_instance_stats(), ctx.layout())
+    ctx.close()
+    return out
+
+
+def test_cycle_stop_leaves_the_converged_set_of_the_scan_unchanged():
+    """The 4096-instance scan at the same cap (5000 sweeps) with and without the cycle stop: the
+    same instances converge, to bitwise the same A and B, with the same sweep counts; every
+    instance the stop ended reports a cycle period and ended before the cap as NOT_CONVERGED."""
+    batch = inputs.scan_batch(4096)
+    A0, B0, st0, it0, _, x_off = _solve_scan(batch, 0)
+    A1, B1, st1, it1, s1, _ = _solve_scan(batch, 1)
+    ok = st0 == 0
+    assert np.array_equal(ok, st1 == 0)
+    assert np.array_equal(it0[ok], it1[ok])
+    pts = np.repeat(ok, np.diff(x_off))
+    assert np.array_equal(A0[pts], A1[pts]) and np.array_equal(B0[pts], B1[pts])
+    stopped = s1["cycle_period"] > 0
+    assert np.all(st1[stopped] == Q.QDSE_ERR_NOT_CONVERGED)
+    assert np.all(it1[stopped] <= it0[stopped])
+    assert np.all(s1["cycle_found_at"][stopped] == it1[stopped])
+    # instances the stop did not end behave as without it
+    same = ~stopped
+    assert np.array_equal(st0[same], st1[same]) and np.array_equal(it0[same], it1[same])
+
+
+def _residual(grids, prm, A, B, precompute, monkeypatch, precision=Q.QDSE_FP64_PRE):
+    if precompute == "fp64":
+        monkeypatch.setenv("QDSE_PRECOMPUTE", "fp64")
+    else:
+        monkeypatch.delenv("QDSE_PRECOMPUTE", raising=False)
+    ctx = Q.Context(grids, precision=precision)
+    FA = torch.empty_like(A)
+    FB = torch.empty_like(B)
+    ctx.qdse_residual(prm, A, B, FA, FB)
+    torch.cuda.synchronize()
+    out = FA.cpu().numpy(), FB.cpu().numpy(), ctx.layout()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("mode", [Q.QDSE_COLLOCATED, Q.QDSE_STAGGERED])
+def test_fp32_pipe_precompute_gives_the_fp64_precompute_map(mode, monkeypatch):
+    """The double-float (FP32-pipe) kernel precompute and the FP64 one feed the same FP64 map
+    F(x) (hi + lo kernels) to 2e-13 per instance, on a ragged batch of the scan's shapes and
+    interactions (both grid modes)."""
+    batch = [b for b in inputs.scan_batch(64)][:24]
+    grids = [Q.Grid(b.n_p, b.n_theta, b.s_min, b.s_max, mode) for b in batch]
+    prm = [[b.D, b.omega, b.m, 0.0] for b in batch]
+    n = sum(b.n_p for b in batch)
+    rng = np.random.default_rng(17 + mode)
+    A = torch.as_tensor(1 + rng.uniform(0, 1.5, n), device="cuda")
+    B = torch.as_tensor(rng.uniform(0.01, 0.8, n), device="cuda")
+    FA2, FB2, x_off = _residual(grids, prm, A, B, "f2", monkeypatch)
+    FA6, FB6, _ = _residual(grids, prm, A, B, "fp64", monkeypatch)
+    for b in range(len(batch)):
+        sl = slice(x_off[b], x_off[b + 1])
+        ea = np.abs(FA2[sl] - FA6[sl]).max() / np.abs(FA6[sl]).max()
+        eb = np.abs(FB2[sl] - FB6[sl]).max() / np.abs(FB6[sl]).max()
+        assert ea < 2e-13 and eb < 2e-13, (b, ea, eb)

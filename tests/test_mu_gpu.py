@@ -11,6 +11,18 @@ import pytest
 
 from oracle import oracle_mu as OM
 from paper_2012_03667_gb300 import inputs as I
+from paper_2012_03667_gb300 import mu_rule as MR
+
+def gpu_rule(w):
+    """The library's quadrature inputs for workload w: internal weights, cosine nodes and weights
+    (formed on the package side, paper_2012_03667_gb300/mu_rule.py)."""
+    return MR.measure_weights(w.q_abs, w.q4, w.lo, w.hi), w.z, MR.angular_weights(w.z)
+
+
+def oracle_rule(w):
+    """The oracle's own weights for the same nodes (reading M5, interpolatory rules)."""
+    return OM.measure(w.q_abs, w.q4, w.lo, w.hi), w.z, OM.angular_weights(w.z)
+
 
 pytestmark = pytest.mark.gpu
 
@@ -66,13 +78,13 @@ def test_mu_sweep_matches_oracle(QM, precision, tol, vertex):
     w = I.mu_workload(**SMALL)
     mu_list = list(w.mu[:4]) + [0.0]
     qv, q4 = _internal(w)
-    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, precision)
+    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, *gpu_rule(w), w.omega, precision)
     assert g.info()["n_pairs"] == _window_count(w) < len(w.p_abs) * len(qv)
     Fe, Fi = _iterates(w, qv, q4, mu_list)
     got = _gpu_sweep(QM, g, w, mu_list, Fe, Fi, vertex)
     x0 = np.array([1.0, 1.0, w.m])[:, None]
     for b, mu in enumerate(mu_list):
-        ref = np.array(OM.sweep(w.p_abs, w.p4, qv, q4, w.w_q, w.z, w.w_z, w.D, w.omega, w.m, mu,
+        ref = np.array(OM.sweep(w.p_abs, w.p4, qv, q4, *oracle_rule(w), w.D, w.omega, w.m, mu,
                                 *Fe[b], *Fi[b], vertex=vertex, nthreads=0))
         scale = np.abs(ref - x0).max(axis=1)
         err = (np.abs(got[b] - ref).max(axis=1) / scale).max()
@@ -85,7 +97,7 @@ def test_mu_batch_position_does_not_change_results(QM):
     do not change the arithmetic.  n_mu = 0 is a no-op."""
     w = I.mu_workload(**SMALL)
     qv, q4 = _internal(w)
-    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, 3)
+    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, *gpu_rule(w), w.omega, 3)
     first = list(w.mu[:5]) + [0.37, 0.02, 0.3]
     mu_big = first + first + first[:3]
     Fe, Fi = _iterates(w, qv, q4, mu_big)
@@ -108,7 +120,7 @@ def test_mu_full_size_sampled_against_oracle(QM, precision, tol):
     chemical potentials (the largest, the smallest and one between) against the oracle."""
     w = I.mu_workload()
     qv, q4 = _internal(w)
-    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, precision)
+    g = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, *gpu_rule(w), w.omega, precision)
     assert g.info()["n_pairs"] == _window_count(w)
     Fe, Fi = _iterates(w, qv, q4, w.mu)
     got = _gpu_sweep(QM, g, w, list(w.mu), Fe, Fi, 0)
@@ -116,7 +128,7 @@ def test_mu_full_size_sampled_against_oracle(QM, precision, tol):
     idx = np.array([0, 130, 1000, 5000, 9999, 16383])
     x0 = np.array([1.0, 1.0, w.m])[:, None]
     for b in (int(np.argmax(w.mu)), int(np.argmin(w.mu)), 7):
-        ref = np.array(OM.sweep(w.p_abs[idx], w.p4[idx], qv, q4, w.w_q, w.z, w.w_z, w.D,
+        ref = np.array(OM.sweep(w.p_abs[idx], w.p4[idx], qv, q4, *oracle_rule(w), w.D,
                                 w.omega, w.m, w.mu[b], *Fe[b][:, idx], *Fi[b], nthreads=0))
         scale = np.abs(ref - x0).max(axis=1)
         err = (np.abs(got[b][:, idx] - ref).max(axis=1) / scale).max()
@@ -130,14 +142,14 @@ SOLVE = dict(n_r=12, n_4=8, n_z=24, n_mu=3)
 def _solve_setup(QM, precision, D=None):
     w = I.mu_workload(**SOLVE)
     pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
-    g = QM.MuGrid(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, precision, product=True)
+    g = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, precision, product=True)
     start = np.array([np.ones(len(w.p_abs)), np.ones(len(w.p_abs)),
                       0.3 * np.ones(len(w.p_abs))], dtype=np.complex128)
     return w, pa, p4a, g, start
 
 
 def _oracle_solve(w, pa, p4a, D, mu, start, **kw):
-    return OM.solve(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, D, w.omega, w.m, mu, start, **kw)
+    return OM.solve(pa, p4a, w.q_abs, w.q4, *oracle_rule(w), D, w.omega, w.m, mu, start, **kw)
 
 
 def test_mu_solve_reaches_the_oracle_fixed_point_rainbow(QM):
@@ -181,7 +193,7 @@ def test_mu_mixed_solve_reaches_the_fp64_fixed_point(QM):
     """FP32 sweeps to a change of 1e-5, then FP64 sweeps on a grid of the same points to 1e-12:
     the result is the FP64 solve's fixed point to 1e-9."""
     w, pa, p4a, g64, start = _solve_setup(QM, 0)
-    g32 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, 3, product=True)
+    g32 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, 3, product=True)
     mu_list = [0.1, 0.3]
     F64 = torch.from_numpy(np.stack([start] * 2)).cuda()
     it64, st64 = g64.solve(mu_list, 0.5, w.m, F64, tol=1e-12, max_iter=400, vertex=0)
@@ -208,6 +220,6 @@ def test_mu_solve_reports_non_convergence_and_non_finite_values(QM):
     F = torch.from_numpy(np.stack([start])).cuda()
     iters, status = g.solve([0.1], w.D, w.m, F, tol=1e-12, max_iter=3, vertex=1)
     assert list(status) == [QM.Q.QDSE_ERR_NOT_CONVERGED] and list(iters) == [3]
-    flat = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.omega, 0)
+    flat = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, *gpu_rule(w), w.omega, 0)
     with pytest.raises(QM.Q.QdseError):
         flat.solve([0.1], w.D, w.m, F)

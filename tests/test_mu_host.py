@@ -14,6 +14,18 @@ import pytest
 
 from oracle import oracle_mu as OM
 from paper_2012_03667_gb300 import inputs as I
+from paper_2012_03667_gb300 import mu_rule as MR
+
+def gpu_rule(w):
+    """The library's quadrature inputs for workload w: internal weights, cosine nodes and weights
+    (formed on the package side, paper_2012_03667_gb300/mu_rule.py)."""
+    return MR.measure_weights(w.q_abs, w.q4, w.lo, w.hi), w.z, MR.angular_weights(w.z)
+
+
+def oracle_rule(w):
+    """The oracle's own weights for the same nodes (reading M5, interpolatory rules)."""
+    return OM.measure(w.q_abs, w.q4, w.lo, w.hi), w.z, OM.angular_weights(w.z)
+
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "mu", "host_mu_sweep.cpp")
@@ -65,12 +77,12 @@ def test_pair_arithmetic_matches_the_oracle(host, vertex):
     for mu in list(w.mu) + [0.0]:
         Fp = I.mu_iterate(w.p_abs, w.p4, mu, w.m)
         Fq = I.mu_iterate(qv, q4, mu, w.m)
-        ref = np.array(OM.sweep(w.p_abs, w.p4, qv, q4, w.w_q, w.z, w.w_z, w.D, w.omega, w.m, mu,
+        ref = np.array(OM.sweep(w.p_abs, w.p4, qv, q4, *oracle_rule(w), w.D, w.omega, w.m, mu,
                                 *Fp, *Fq, vertex=vertex))
         scale = np.abs(ref - x0).max(axis=1)
         assert np.all(scale > 1e-3)
         for fp32, tol in ((0, 1e-12), (1, 1e-4)):
-            got = host(w.p_abs, w.p4, qv, q4, w.w_q, w.z, w.w_z, w.D, w.omega, w.m, mu, Fp, Fq,
+            got = host(w.p_abs, w.p4, qv, q4, *gpu_rule(w), w.D, w.omega, w.m, mu, Fp, Fq,
                        vertex, fp32)
             err = (np.abs(got - ref).max(axis=1) / scale).max()
             assert err < tol, (mu, fp32, err)

@@ -19,6 +19,11 @@ import pytest
 from oracle import oracle as O
 from oracle import oracle_mu as OM
 
+def oracle_rule(w):
+    """The oracle's own weights for the same nodes (reading M5, interpolatory rules)."""
+    return OM.measure(w.q_abs, w.q4, w.lo, w.hi), w.z, OM.angular_weights(w.z)
+
+
 D, OMEGA, M = 0.93, 0.5, 0.005
 
 
@@ -209,7 +214,7 @@ def test_solve_reaches_a_fixed_point_of_the_sweep():
     w = I.mu_workload(n_r=12, n_4=8, n_z=24, n_mu=1)
     pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
     F0 = np.array([np.ones(len(w.p_abs)), np.ones(len(w.p_abs)), 0.3 * np.ones(len(w.p_abs))])
-    args = (pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, w.D, w.omega, w.m, 0.1)
+    args = (pa, p4a, w.q_abs, w.q4, *oracle_rule(w), w.D, w.omega, w.m, 0.1)
     F, it, ok = OM.solve(*args, F0, tol=1e-11, max_iter=200, vertex=OM.RL)
     assert ok and 10 < it < 100
     G, _, _ = OM.solve(*args, F, tol=0.0, max_iter=1, vertex=OM.RL)
@@ -237,7 +242,7 @@ def test_mu_zero_solve_approaches_the_vacuum_solution_as_the_grid_is_refined():
         w = I.mu_workload(n_r=nr, n_4=n4, n_z=16, n_mu=1, D=D, omega=OMEGA, m=M)
         pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
         ones = np.ones(len(w.p_abs))
-        F, it, ok = OM.solve(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, D, OMEGA, M, 0.0,
+        F, it, ok = OM.solve(pa, p4a, w.q_abs, w.q4, *oracle_rule(w), D, OMEGA, M, 0.0,
                              np.array([ones, ones, 0.3 * ones]), tol=1e-10, max_iter=200,
                              vertex=OM.RL)
         assert ok and np.abs(F.imag).max() < 1e-13
@@ -265,7 +270,7 @@ def test_vectorised_interpolation_and_the_m8_hook_reduce_to_the_plain_forms():
     assert np.array_equal(OM.interpolate_points(pa, p4a, F, qv, q4), Fi)
     F = np.abs(F) + 0.5  # keep the propagator regular
     Fi = OM.interpolate(pa, p4a, F, w.q_abs, w.q4)
-    args = (w.p_abs, w.p4, qv, q4, w.w_q, w.z, w.w_z, 0.55, 0.678, w.m, 0.13, *F, *Fi)
+    args = (w.p_abs, w.p4, qv, q4, *oracle_rule(w), 0.55, 0.678, w.m, 0.13, *F, *Fi)
     plain = np.array(OM.sweep(*args))
     hooked = np.array(OM.sweep(*args, Fd=np.repeat(F, len(qv), axis=1)))
     assert np.array_equal(plain, hooked)
@@ -282,7 +287,7 @@ def test_ray_blended_quotient_converges_at_mu_zero_and_matches_the_exact_one_els
     w = I.mu_workload(n_r=12, n_4=8, n_z=16, n_mu=1, D=0.55, omega=0.678)
     pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
     start = np.array([np.ones(len(w.p_abs))] * 3, dtype=np.complex128)
-    args = (pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, 0.55, 0.678, w.m)
+    args = (pa, p4a, w.q_abs, w.q4, *oracle_rule(w), 0.55, 0.678, w.m)
     F0, it0, ok0 = OM.solve(*args, 0.0, start, tol=1e-10, max_iter=80, ray_eta=0.002,
                             nthreads=O.max_threads())
     assert ok0 and it0 <= 60
@@ -312,7 +317,7 @@ def test_ray_blended_quotient_at_mu_zero_approaches_the_vacuum_bc_solution():
         w = I.mu_workload(n_r=nr, n_4=n4, n_z=16, n_mu=1, D=D_, omega=om, m=m)
         pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
         start = np.array([np.ones(len(w.p_abs))] * 3, dtype=np.complex128)
-        F, it, ok = OM.solve(pa, p4a, w.q_abs, w.q4, w.w_q, w.z, w.w_z, D_, om, m, 0.0, start,
+        F, it, ok = OM.solve(pa, p4a, w.q_abs, w.q4, *oracle_rule(w), D_, om, m, 0.0, start,
                              tol=1e-10, max_iter=100, ray_eta=0.002, nthreads=O.max_threads())
         assert ok
         s = w.p_abs ** 2 + w.p4 ** 2
@@ -322,3 +327,39 @@ def test_ray_blended_quotient_at_mu_zero_approaches_the_vacuum_bc_solution():
                      np.abs(F[1] - F[0]).max()))
     assert errs[1][0] < errs[0][0] / 3 and errs[1][0] < 0.15
     assert errs[1][1] < 0.8 * errs[0][1]
+
+
+def test_oracle_weights_are_gauss_rules_on_gauss_legendre_nodes():
+    """The oracle's interpolatory weights, built from the nodes alone, integrate every monomial up
+    to degree 2n - 1 exactly on Gauss-Legendre nodes (the Gauss property), so they are the Gauss
+    weights; a rule with a wrong weight anywhere fails some degree."""
+    for n in (8, 40, 64):
+        t, _ = np.polynomial.legendre.leggauss(n)
+        w = OM.interpolatory_weights(t)
+        for k in range(2 * n):
+            exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+            assert abs(float((w * t ** k).sum()) - exact) < 1e-13, (n, k)
+    w = OM.interpolatory_weights(np.array([-0.5, 0.5]))  # two nodes, not Gauss: degree < 2 only
+    assert np.allclose(w, [1.0, 1.0], rtol=0, atol=1e-15)
+
+
+def test_oracle_measure_integrates_a_gaussian_in_closed_form():
+    """Reading M5's measure |q|^2 d|q| dq_4 on the workload's product grid: the sum of
+    exp(-(|q|^2 + q_4^2)/a) over the oracle's weights equals
+    int_lo^hi x^2 e^{-x^2/a} dx * 2 int_lo^hi e^{-y^2/a} dy (q_4 on both sides of 0) in closed
+    form with erf, to 1e-13 on the full 128 x 256 grid.  A dropped |q|^2, a missing mirror or a
+    wrong Jacobian of the log map each miss it by orders of magnitude."""
+    from math import erf, exp, pi, sqrt
+    from paper_2012_03667_gb300 import inputs as I
+    w = I.mu_workload(n_r=128, n_4=128, n_z=16, n_mu=1)
+    a = 0.7
+    QR, Q4 = np.meshgrid(w.q_abs, w.q4, indexing="ij")
+    got = float((OM.measure(w.q_abs, w.q4, w.lo, w.hi) * np.exp(-(QR ** 2 + Q4 ** 2) / a).ravel())
+                .sum())
+    F = lambda x: a ** 1.5 * sqrt(pi) / 4 * erf(x / sqrt(a)) - a * x / 2 * exp(-x * x / a)
+    G = lambda y: sqrt(pi * a) / 2 * erf(y / sqrt(a))
+    exact = (F(w.hi) - F(w.lo)) * 2.0 * (G(w.hi) - G(w.lo))
+    assert abs(got / exact - 1.0) < 1e-13
+    # the angular rule: int_{-1}^{1} z^2 dz = 2/3
+    wz = OM.angular_weights(w.z)
+    assert abs(float((wz * w.z ** 2).sum()) - 2.0 / 3.0) < 1e-14
