@@ -322,8 +322,8 @@ def run_ours(args):
         Bhost.fill(0.3)
         ctx.qdse_solve_host(prm, Ahost, Bhost, None, st_h)
     e2e_s = time.perf_counter() - t0
-    same_as_device = bool(np.array_equal(st_h, st) and np.array_equal(Ahost, Ah)
-                          and np.array_equal(Bhost, Bh))
+    same_as_device = bool(np.array_equal(st_h, st) and np.array_equal(Ahost, Ah, equal_nan=True)
+                          and np.array_equal(Bhost, Bh, equal_nan=True))
 
     # per-instance accuracy gate against the plain FP64 GPU forms, and those forms' own rates
     gate, arms, counted = None, None, np.zeros(n_inst, dtype=bool)

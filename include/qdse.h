@@ -123,9 +123,14 @@ qdse_options qdse_default_options(void);
  * nodes on the host in FP64, uploads them and allocates the kernel-matrix pool (6 n_p^2 floats
  * per instance) and workspaces on the current device.  *out receives the context (NULL on
  * failure).  Errors: QDSE_ERR_ARG (bad sizes/options), QDSE_ERR_OOM, QDSE_ERR_CUDA.
- * The FP32 sweeps of the batched solve use the shared-memory ring kernel; the environment
- * variable QDSE_SWEEP=groups, read here, selects the register-only kernel instead (the same sums
- * in another order). */
+ * The FP32 sweeps of the batched solve use the shared-memory ring kernel, followed in every tick by
+ * a launch that advances each instance (relaxed step, convergence test, next node vectors).
+ * Environment variables read here select alternatives that compute the same quantities:
+ * QDSE_SWEEP=groups the register-only sweep kernel (the same sums in another order),
+ * QDSE_FUSED_UPDATE=1 the ring sweep advancing each instance itself as soon as its last row group
+ * is swept (one launch per tick, bitwise the same results, slower on GB300),
+ * QDSE_PRECOMPUTE=fp64 the kernel matrices in FP64 arithmetic instead of double-float arithmetic on
+ * the FP32 pipe (the same entries to about 1e-14). */
 qdse_status qdse_create(const qdse_grid* g, int n_inst, const qdse_options* o, qdse_ctx** out);
 
 /* As qdse_create with one grid per instance: g points to n_inst host structs (ragged batch). */
@@ -191,12 +196,13 @@ qdse_status qdse_residual(qdse_ctx* ctx, const qdse_params* p, const double* A, 
 qdse_status qdse_jvp(qdse_ctx* ctx, const qdse_params* p, const double* A, const double* B,
                      const double* vA, const double* vB, double* JvA, double* JvB);
 
-/* Transposed product (JtA, JtB) = (dF/dx)^T (wA, wB).  Collocated grids only
- * (QDSE_ERR_UNSUPPORTED for staggered).  All arrays device double[n_total]. */
+/* Transposed product (JtA, JtB) = (dF/dx)^T (wA, wB), both grid modes (on staggered grids the
+ * derivatives through each internal node's interpolated values are summed with atomic adds, so
+ * their last bits depend on the order of the adds).  All arrays device double[n_total]. */
 qdse_status qdse_vjp(qdse_ctx* ctx, const qdse_params* p, const double* A, const double* B,
                      const double* wA, const double* wB, double* JtA, double* JtB);
 
-/* Implicit-function adjoint at a converged solution x* = F(x*) (collocated grids; instances whose
+/* Implicit-function adjoint at a converged solution x* = F(x*) (both grid modes; instances whose
  * (A, B) is not a fixed point to 1e-6 relative are skipped with QDSE_ERR_NOT_CONVERGED):
  * solves lambda = J^T lambda + g, g = (gA, gB) the cotangent dL/d(A, B), and returns
  *     g_params[4 b + t] = dL/dtheta_t,  theta = (m, D, omega, mu),

@@ -110,7 +110,7 @@ void free_ctx(qdse_ctx* c) {
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
                     c->grid.groups, c->grid.nnz, c->grid.gdesc, c->grid.gphase, c->work.ilist,
                     c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd,
-                    c->grid.W32, c->grid.wt32, c->grid.stc32, c->grid.expt, c->work.hring};
+                    c->grid.W32, c->grid.wt32, c->grid.stc32, c->grid.expt, c->work.hring, c->work.ticket, c->work.col};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -213,7 +213,9 @@ cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
     if (otf) {
         e = launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1);
     } else if (c->sweep_kind == 1) {
+        // the ring sweep advances every instance itself once its last row group is swept
         e = launch_tick_ring(c, A, B);
+        if (e != cudaSuccess || c->fused_update) return e;
     } else {
         e = launch_tick(c, A, B);
     }
@@ -423,6 +425,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
             d.ld = h.ld;
             d.kbase = h.k_off + (long long)i0 * 3 * h.ld;
             d.mode = h.g.grid_mode;
+            d.ng = (h.g.n_p + kRows - 1) / kRows;
             gdesc.push_back(d);
         }
     }
@@ -494,6 +497,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->work.glist, 3 * (size_t)ng);
     CALLOC(c->work.lcount, 6);
     CALLOC(c->work.hring, (size_t)kHashRing * n_inst);
+    CALLOC(c->work.ticket, n_inst);
+    CALLOC(c->work.col, 2 * (size_t)N);
     c->work.n_inst = n_inst;
     c->work.n_groups = ng;
     CALLOC(c->grid.groups, ng);
@@ -580,6 +585,11 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         cudaGetLastError();
         c->sweep_kind = ring_ok ? 1 : 0;
         if (k && std::string(k) == "groups") c->sweep_kind = 0;
+        // QDSE_FUSED_UPDATE=1: the ring sweep advances each instance itself (one launch per tick;
+        // the same arithmetic in the same order as the separate update launch, but measured
+        // slower: the update's dependent loads by one warp, among the sweep's 12 warps per SM)
+        const char* fu = std::getenv("QDSE_FUSED_UPDATE");
+        c->fused_update = (fu && std::string(fu) == "1") ? 1 : 0;
         // kernel matrices: double-float on the FP32 pipe by default; QDSE_PRECOMPUTE=fp64
         // selects the FP64 kernel (the same entries to about 1e-14)
         const char* pk = std::getenv("QDSE_PRECOMPUTE");
@@ -826,8 +836,6 @@ qdse_status qdse_vjp(qdse_ctx* c, const qdse_params* p, const double* A, const d
     const void* ptrs[] = {A, B, wA, wB, JtA, JtB};
     for (const void* q : ptrs)
         if (!q) return fail(c, QDSE_ERR_ARG, "vjp: null pointer");
-    if (c->any_staggered)
-        return fail(c, QDSE_ERR_UNSUPPORTED, "transposed sweep: collocated grids only");
     bool rebuild = false;
     qdse_status s = set_params(c, p, rebuild);
     if (s != QDSE_OK) return s;
@@ -848,8 +856,6 @@ qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, con
     const void* ptrs[] = {A, B, gA, gB, g_params};
     for (const void* q : ptrs)
         if (!q) return fail(c, QDSE_ERR_ARG, "adjoint: null pointer");
-    if (c->any_staggered)
-        return fail(c, QDSE_ERR_UNSUPPORTED, "adjoint: collocated grids only");
     bool rebuild = false;
     qdse_status s = set_params(c, p, rebuild);
     if (s != QDSE_OK) return s;
@@ -878,7 +884,7 @@ qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, con
     int chunk = 4;
     while (true) {
         for (int t = 0; t < chunk; ++t) {
-            QCHECK(c, launch_adjoint_sweep(c, gA, gB), "transposed sweep");
+            QCHECK(c, launch_adjoint_sweep(c, A, B, gA, gB), "transposed sweep");
             if (t == chunk - 1)
                 QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
             QCHECK(c, launch_adjoint_update(c, c->work.lam, c->work.lamn, c->d_count), "adjoint update");

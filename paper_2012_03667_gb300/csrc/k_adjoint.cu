@@ -5,7 +5,8 @@
 // and g = dL/dx (implicit function theorem; no unrolled iterations are stored).  The transposed
 // fixed point is solved by the same successive approximation, sweep by sweep.
 //
-// J^T w for a collocated grid is computed row by row: with alpha_i = w^A_i kappa D/P_i and
+// J^T w for a collocated grid is computed row by row (k_vjp_row; staggered grids: k_vjp_stag_rows
+// and k_vjp_stag_assemble below): with alpha_i = w^A_i kappa D/P_i and
 // beta_i = w^B_i kappa D, entry l collects
 //   (own)     sum_j alpha_l dT^A_lj/dx_l + beta_l dT^B_lj/dx_l          (row l of the kernels)
 //   (partner) sum_i alpha_i dT^A_il/dx_l + beta_i dT^B_il/dx_l          (column l = row l, since
@@ -68,17 +69,27 @@ __global__ void k_vjp_prep(const DevInst* __restrict__ inst, const Ctl* __restri
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
         const int gj = I.x_off + j;
         if (with_x) {
-            const double a = A[gj], b = B[gj], Q = g.sq[gj];
+            // values at internal node j (on a staggered grid the modified interpolation
+            // between p_j and p_j+1, Eq. chazhiresult)
+            const double wt = g.wt[gj];
+            double a = A[gj], b = B[gj];
+            if (wt != 0.0) {
+                a += wt * (A[gj + 1] - a);
+                b += wt * (B[gj + 1] - b);
+            }
+            const double Q = g.sq[gj];
             const double e = g.W[gj] / (Q * a * a + b * b);
             w.vec64[gj] = a;
             w.vec64[ntot + gj] = b;
             w.vec64[2 * ntot + gj] = e * b;
             w.vec64[3 * ntot + gj] = e * a;
             w.vec64[4 * ntot + gj] = e * a * Q;
-            const int s0 = I.x_off + g.sta[gj];
-            const double* c = g.stc + 3 * (size_t)gj;
-            w.dia64[gj] = c[0] * A[s0] + c[1] * A[s0 + 1] + c[2] * A[s0 + 2];
-            w.dia64[ntot + gj] = c[0] * B[s0] + c[1] * B[s0 + 1] + c[2] * B[s0 + 2];
+            if (I.mode == QDSE_COLLOCATED) {
+                const int s0 = I.x_off + g.sta[gj];
+                const double* c = g.stc + 3 * (size_t)gj;
+                w.dia64[gj] = c[0] * A[s0] + c[1] * A[s0 + 1] + c[2] * A[s0 + 2];
+                w.dia64[ntot + gj] = c[0] * B[s0] + c[1] * B[s0 + 1] + c[2] * B[s0 + 2];
+            }
         }
         const double scale = ctl->kappa * I.D;
         w.dvec64[gj] = wA[gj] * scale / g.sp[gj];
@@ -101,6 +112,7 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     const int bi = g.row_inst[r];
     if (only_active && state[bi].phase == PH_DONE) return;
     const DevInst I = inst[bi];
+    if (I.mode != QDSE_COLLOCATED) return;  // k_vjp_stag_rows / k_vjp_stag_assemble
     const int l = r - I.x_off;
     const int o = I.x_off;
     const KRow row(I, l);
@@ -194,6 +206,104 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     }
     JA[r] = gAl;
     JB[r] = gBl;
+}
+
+// J^T w on a staggered grid, where the internal nodes q_j are not the external points and the
+// kernel matrices are not symmetric.  Row pass, one warp per external point i: the row's own
+// derivatives (through A_i, B_i in the pair terms) go to JA_i, JB_i; the derivatives through the
+// values a_j, b_j at internal node j (and e_j = W_j/(Q_j a_j^2 + b_j^2)) are summed over the rows
+// into col[j] by FP64 atomic adds (so the last bits depend on the order of the adds).  The
+// assembly pulls col back through the interpolation a_j = (1 - wt_j) A_j + wt_j A_j+1 (Eq.
+// chazhiresult): point l receives (1 - wt_l) col[l] + wt_l-1 col[l - 1].
+__global__ void __launch_bounds__(256) k_vjp_stag_rows(const DevInst* __restrict__ inst,
+                                                       const Ctl* __restrict__ ctl, Grid g,
+                                                       Work w, const float* __restrict__ Khi,
+                                                       const float* __restrict__ Klo,
+                                                       const DevState* __restrict__ state,
+                                                       const double* A, const double* B,
+                                                       double* JA, double* JB, double* col,
+                                                       int ntot, int only_active) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= ntot) return;
+    const int bi = g.row_inst[r];
+    if (only_active && state[bi].phase == PH_DONE) return;
+    const DevInst I = inst[bi];
+    if (I.mode == QDSE_COLLOCATED) return;  // k_vjp_row
+    const int i = r - I.x_off, o = I.x_off;
+    const KRow row(I, i);
+    const double Pi = g.sp[r], Ai = A[r], Bi = B[r];
+    const double ai = w.dvec64[r], bi_ = w.dvec64[ntot + r];  // alpha_i, beta_i
+    const bool bc = ctl->vertex == QDSE_VERTEX_BC;
+    double oA = 0.0, oB = 0.0;
+    const int2 bd = g.band[r];
+    for (int j = bd.x + lane; j < min(bd.y, I.n); j += 32) {
+        const int gj = o + j;
+        const long long o0 = row.off(0, j), o1 = row.off(1, j), o2 = row.off(2, j);
+        const double K0 = (double)Khi[o0] + (double)Klo[o0];
+        const double KT = bc ? (double)Khi[o1] + (double)Klo[o1] : 0.0;
+        const double K3 = (double)Khi[o2] + (double)Klo[o2];
+        const double a = w.vec64[gj], b = w.vec64[ntot + gj];
+        const double u1 = w.vec64[2 * ntot + gj], u2 = w.vec64[3 * ntot + gj],
+                     u3 = w.vec64[4 * ntot + gj];
+        const double Q = g.sq[gj], d = Q * a * a + b * b, e = g.W[gj] / d;
+        const double ea = -2.0 * e * Q * a / d, eb = -2.0 * e * b / d;  // de/da, de/db
+        double ca, cb;
+        if (bc) {
+            oA += ai * (0.5 * (Pi * u2 + u3) * KT + 0.5 * u2 * K3) +
+                  bi_ * (-u1 * KT + 1.5 * u1 * K0);
+            oB += ai * (u1 * KT) + bi_ * (u2 * KT);
+            const double TAe = (-b * (b - Bi) - 0.5 * (Pi + Q) * a * (a - Ai)) * KT +
+                               0.5 * a * (Ai + a) * K3;
+            const double TBe = (a * Bi - b * Ai) * KT + 1.5 * b * (Ai + a) * K0;
+            ca = ai * (e * (-0.5 * (Pi + Q) * (2.0 * a - Ai) * KT + 0.5 * (Ai + 2.0 * a) * K3) +
+                       TAe * ea) +
+                 bi_ * (e * (Bi * KT + 1.5 * b * K0) + TBe * ea);
+            cb = ai * (e * (-(2.0 * b - Bi) * KT) + TAe * eb) +
+                 bi_ * (e * (-Ai * KT + 1.5 * (Ai + a) * K0) + TBe * eb);
+        } else {
+            // rainbow: T^A = u2 K3, T^B = 3 u1 K0 (no dependence on A_i, B_i)
+            ca = ai * (e + a * ea) * K3 + bi_ * 3.0 * b * ea * K0;
+            cb = ai * a * eb * K3 + bi_ * 3.0 * (e + b * eb) * K0;
+        }
+        atomicAdd(col + gj, ca);
+        atomicAdd(col + ntot + gj, cb);
+    }
+#pragma unroll
+    for (int sft = 16; sft > 0; sft >>= 1) {
+        oA += __shfl_xor_sync(0xffffffffu, oA, sft);
+        oB += __shfl_xor_sync(0xffffffffu, oB, sft);
+    }
+    if (lane == 0) {
+        JA[r] = oA;
+        JB[r] = oB;
+    }
+}
+
+__global__ void k_vjp_stag_assemble(const DevInst* __restrict__ inst, Grid g,
+                                    const DevState* __restrict__ state, double* JA, double* JB,
+                                    const double* col, const double* gA, const double* gB,
+                                    int ntot, int add_g, int only_active) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ntot) return;
+    const int bi = g.row_inst[r];
+    if (only_active && state[bi].phase == PH_DONE) return;
+    const DevInst I = inst[bi];
+    if (I.mode == QDSE_COLLOCATED) return;
+    const int l = r - I.x_off;
+    const double wl = g.wt[r];
+    double ja = JA[r] + (1.0 - wl) * col[r], jb = JB[r] + (1.0 - wl) * col[ntot + r];
+    if (l > 0) {
+        const double wp = g.wt[r - 1];
+        ja += wp * col[r - 1];
+        jb += wp * col[ntot + r - 1];
+    }
+    if (add_g) {
+        ja += gA[r];
+        jb += gB[r];
+    }
+    JA[r] = ja;
+    JB[r] = jb;
 }
 
 // lambda <- (1 - alpha) lambda + alpha lambda_new with a max-norm relative stopping test.
@@ -354,6 +464,30 @@ __global__ void k_condensate_vjp(const DevInst* __restrict__ inst, Grid g, const
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
+// The staggered instances' part of J^T w (row pass with column scatter, then the assembly).
+static cudaError_t launch_vjp_staggered(qdse_ctx* c, const double* A, const double* B, double* JA,
+                                        double* JB, int add_g, const double* gA, const double* gB,
+                                        int only_active) {
+    if (!c->any_staggered) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->work.col, 0, 2 * sizeof(double) * c->n_total, c->stream);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, PK_SWEEP);
+    k_vjp_stag_rows<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, A, B, JA, JB,
+        c->work.col, c->n_total, only_active);
+    c->launches++;
+    prof_end(c);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(c, PK_OTHER);
+    k_vjp_stag_assemble<<<(c->n_total + 255) / 256, 256, 0, c->stream>>>(
+        c->d_inst, c->grid, c->d_state, JA, JB, c->work.col, gA, gB, c->n_total, add_g,
+        only_active);
+    c->launches++;
+    prof_end(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const double* wA,
                        const double* wB, double* JA, double* JB, int add_g, const double* gA,
                        const double* gB) {
@@ -370,7 +504,9 @@ cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const doub
                                                             JB, gA, gB, c->n_total, add_g, 0);
     c->launches++;
     prof_end(c);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_vjp_staggered(c, A, B, JA, JB, add_g, gA, gB, 0);
 }
 
 cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB,
@@ -394,14 +530,17 @@ cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* gA, const double* gB) {
+cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* A, const double* B, const double* gA,
+                                 const double* gB) {
     prof_begin(c, PK_SWEEP);
     k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
         c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, c->work.lamn,
         c->work.lamn + c->n_total, gA, gB, c->n_total, 1, 1);
     c->launches++;
     prof_end(c);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_vjp_staggered(c, A, B, c->work.lamn, c->work.lamn + c->n_total, 1, gA, gB, 1);
 }
 
 cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active) {

@@ -127,6 +127,24 @@ struct BlockTeam {
     }
 };
 
+// The set of threads that updates one instance inside the ring sweep: one warp (the one that swept
+// the instance's last row group of the tick).
+struct WarpTeam {
+    __device__ int tid() const { return threadIdx.x & 31; }
+    __device__ int size() const { return 32; }
+    __device__ void sync() const { __syncwarp(); }
+    __device__ double max(double v) const { return warp_max(v); }
+    __device__ float maxf(float v) const { return warp_maxf(v); }
+    __device__ bool any(bool v) const { return __any_sync(0xffffffffu, v) != 0; }
+    __device__ bool leader() const { return (threadIdx.x & 31) == 0; }
+    __device__ int bcast(int v) const { return __shfl_sync(0xffffffffu, v, 0); }
+    __device__ unsigned long long xor_all(unsigned long long v) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+};
+
 template <typename T, bool LO>
 __device__ __forceinline__ T kload(const float* __restrict__ hi, const float* __restrict__ lo,
                                    long long idx) {
@@ -793,6 +811,7 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
     }
     for (int t = threadIdx.x; t < (I.n + kRows - 1) / kRows; t += blockDim.x) g.gphase[I.g_off + t] = phase0;
+    if (threadIdx.x == 0) w.ticket[b] = 0;
     prepare_phase(phase0, I, g, w, ntot, A, B);
 }
 
@@ -1370,11 +1389,22 @@ __device__ __forceinline__ void narrow_tile32(Rows32& R, const float* sl, int c,
     }
 }
 
+// The update of one instance by one warp inside the ring sweep (kept out of line: it runs once per
+// instance and tick, and inlining it would cost the sweep registers).
+__device__ __noinline__ void update_by_warp(int b, const DevInst* __restrict__ inst,
+                                            DevState* state, const Ctl* __restrict__ ctl,
+                                            const Grid& g, const Work& w, double* A, double* B,
+                                            int ntot, int* count, unsigned long long* ctr,
+                                            int next_list) {
+    update_instance(WarpTeam{}, b, inst, state, ctl, g, w, A, B, ntot, count, ctr, next_list);
+}
+
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
-    k_tick_ring(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g, Work w,
-                const float* __restrict__ Khi, const float* __restrict__ Klo, const double* A,
-                const double* B, int ntot, int list, int* err) {
+    k_tick_ring(const DevInst* __restrict__ inst, DevState* state, const Ctl* __restrict__ ctl,
+                Grid g, Work w, const float* __restrict__ Khi, const float* __restrict__ Klo,
+                double* A, double* B, int ntot, int list, int* count, unsigned long long* ctr,
+                int fused, int* err) {
     constexpr int S = Cfg::kSlots;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1396,6 +1426,13 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     // groups take more of them.
     __shared__ int s_next;
     if (threadIdx.x == 0) s_next = 0;
+    if (fused && blockIdx.x == 0 && threadIdx.x == 0) {
+        // the lists of two ticks ahead start empty (read by the previous tick, appended to by
+        // the next one)
+        const int clr = (list + 2) % 3;
+        w.lcount[clr] = 0;
+        w.lcount[3 + clr] = 0;
+    }
     __syncthreads();
     const int nact = w.lcount[3 + list];
     const int G = gridDim.x;
@@ -1530,6 +1567,24 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         }
     };
 
+    // Once a group's outputs are stored, the warp counts it on its instance's ticket; the warp
+    // whose count completes the instance (every other group's outputs are then stored and fenced)
+    // advances the instance at once: the relaxed step, its convergence test and phase, and the
+    // node vectors of the next sweep (the work of k_update in the two-launch form).
+    const int next_list = (list + 1) % 3;
+    auto group_done = [&](int b, int ngb) {
+        if (!fused) return;  // k_update advances the instances after the sweep
+        __threadfence();  // this warp's stores of the group's outputs, before its count
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = (atomicAdd(w.ticket + b, 1) == ngb - 1);
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+            __threadfence();  // then the other groups' outputs (read through L2)
+            update_by_warp(b, inst, state, ctl, g, w, A, B, ntot, count, ctr, next_list);
+            if (lane == 0) w.ticket[b] = 0;
+        }
+    };
+
     // the lane that stores a total: value qv (rows' A sums, then B sums) of row rr
     const int qv = group_total_index(lane), rr = qv % kRows;
     const bool isB = qv >= kRows;
@@ -1546,6 +1601,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         if (phase != PH_PICARD32 && phase != PH_TANGENT32) {
             const GroupDesc dc = d;
             tick_group(dc, phase, lane, inst[dc.b], ctl, g, w, Khi, Klo, A, B, ntot);
+            group_done(dc.b, dc.ng);
             continue;
         }
         const bool tan = (phase == PH_TANGENT32);
@@ -1631,6 +1687,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
             if (!isB) w.xn32[o + rr] = tan ? __fdividef(sc * tot, Pl) : 1.f + __fdividef(sc * tot, Pl);
             else w.xn32[ntot + o + rr] = tan ? sc * tot : d.m32 + sc * tot;
         }
+        group_done(d.b, d.ng);
     }
     cp_wait(0);  // no small copy may land after the block has released its shared memory
     if (!ok) {
@@ -1813,8 +1870,9 @@ cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B) {
     const int blocks =
         std::max(1, std::min((c->n_groups + RingSweep::kWarps - 1) / RingSweep::kWarps, sms));
     k_tick_ring<RingSweep><<<blocks, RingSweep::kWarps * 32, RingSweep::kSmem, c->stream>>>(
-        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
-        (int)(c->tick % 3), c->d_err);
+        c->d_inst, c->d_state, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
+        (int)(c->tick % 3), c->d_count, c->d_sweeps, c->fused_update, c->d_err);
+    if (c->fused_update) c->tick++;  // otherwise launch_update advances the tick
     c->launches++;
     prof_end(c);
     return cudaGetLastError();

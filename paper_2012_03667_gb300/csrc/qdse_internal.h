@@ -56,7 +56,8 @@ struct GroupDesc {        // one row group (kRows consecutive external points of
     int mode;             // grid mode of the instance
     float sc32, m32;      // kappa D and m of the instance in FP32 (refreshed with every
                           // parameter upload)
-    int pad[3];
+    int ng;               // row groups of the instance
+    int pad[2];
 };
 
 struct DevState {         // per-instance solver state, updated by the update kernel
@@ -126,6 +127,10 @@ struct Work {
     int* glist;     // [3][n_groups]
     int* lcount;    // [6]
     unsigned long long* hring;  // [n_inst][kHashRing] recent iterate hashes (cycle detection)
+    int* ticket;    // [n_inst] row groups of the instance swept in the current tick (the fused
+                    // update: the warp that completes the last one advances the instance)
+    double* col;    // [2] transposed sweep on staggered grids: per internal node, the summed
+                    // derivatives through its interpolated values
     int n_inst;
     int n_groups;
 };
@@ -287,6 +292,8 @@ struct qdse_ctx {
     int sweep_kind = 0;       // FP32 sweep: 1 ring (bulk copies through shared memory, the
                               // default), 0 register-only row groups
     int precompute_kind = 1;  // kernel matrices: 1 double-float on the FP32 pipe (default), 0 FP64
+    int fused_update = 0;     // ring sweep: 1 advances each instance inside the sweep launch (one
+                              // launch per tick), 0 in a separate k_update launch (the default)
     int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
     double* d_rel = nullptr;  // [n_inst] relative residual of the adjoint's fixed point
     // CUDA graph of a chunk of ticks, replayed between polls (captured on an internal stream)
@@ -356,7 +363,8 @@ cudaError_t launch_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
                                   const double* cbar, double* gA, double* gB);
 cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active);
 cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B);
-cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* gA, const double* gB);
+cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* A, const double* B, const double* gA,
+                                 const double* gB);
 cudaError_t launch_finish_timeout(qdse_ctx* c, double* A, double* B, double* change_out,
                                   int* iters, int* status);
 cudaError_t launch_prep64(qdse_ctx* c, const double* A, const double* B, const double* vA,

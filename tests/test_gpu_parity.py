@@ -151,13 +151,14 @@ def test_jvp_matches_complex_step_jacobian():
         assert rel(got, ref) < 1e-11
 
 
+@pytest.mark.parametrize("mode", [O.COLLOCATED, O.STAGGERED])
 @pytest.mark.parametrize("vertex", [O.BC, O.RL])
-def test_vjp_matches_transposed_jacobian(vertex):
+def test_vjp_matches_transposed_jacobian(vertex, mode):
     inst = TINY
-    rng = np.random.default_rng(4)
+    rng = np.random.default_rng(4 + mode)
     A = 1 + rng.uniform(0, 1.5, inst.n_p); B = rng.uniform(0.05, 0.8, inst.n_p)
-    J = O.jacobian(problem(inst, vertex=vertex), A, B)
-    ctx = Q.Context(grid(inst), 1, precision=Q.QDSE_FP64_PRE, vertex=vertex)
+    J = O.jacobian(problem(inst, mode, vertex), A, B)
+    ctx = Q.Context(grid(inst, mode), 1, precision=Q.QDSE_FP64_PRE, vertex=vertex)
     w = rng.normal(size=2 * inst.n_p)
     JA = dev(np.zeros(inst.n_p)); JB = dev(np.zeros(inst.n_p))
     ctx.qdse_vjp(prm(inst), dev(A), dev(B), dev(w[:inst.n_p]), dev(w[inst.n_p:]), JA, JB)
@@ -359,6 +360,27 @@ def test_adjoint_matches_oracle_adjoint_at_the_adjoint_workload_shape(inst):
     got = host(gp)
     np.testing.assert_allclose(got[:3], gp_ref[:3], rtol=1e-8)
     assert got[3] == 0.0
+
+
+def test_adjoint_on_a_staggered_grid_matches_oracle_adjoint():
+    """The paper's own grid mode (Eqs. pqrelationship, chazhiresult): the transposed fixed point and
+    the parameter gradients against the oracle's dense-LU adjoint of the staggered sweep."""
+    inst = inputs.Instance(40, 16, 0.55, 0.678, 0.02)
+    pr = problem(inst, O.STAGGERED)
+    Ar, Br, it, ch, st = O.solve(pr, tol=1e-14, max_iter=20000)
+    assert st == 0
+    rng = np.random.default_rng(6)
+    gA = rng.normal(size=inst.n_p); gB = rng.normal(size=inst.n_p)
+    gp_ref, lam_ref = O.adjoint(pr, Ar, Br, gA, gB)
+    ctx = Q.Context(grid(inst, Q.QDSE_STAGGERED), 1, precision=Q.QDSE_MIXED, tol=1e-14,
+                    max_iter=40000)
+    gp = dev(np.zeros(4)); lam = dev(np.zeros(2 * inst.n_p))
+    ist = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.qdse_adjoint(prm(inst), dev(Ar), dev(Br), dev(gA), dev(gB), gp, lam, ist)
+    assert int(ist.item()) == 0
+    assert rel(host(lam), lam_ref) < 1e-10
+    got = host(gp)
+    np.testing.assert_allclose(got[:3], gp_ref[:3], rtol=1e-9)
 
 
 def test_condensate_and_its_cotangent():

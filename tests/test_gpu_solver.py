@@ -89,3 +89,19 @@ def test_fp32_pipe_precompute_gives_the_fp64_precompute_map(mode, monkeypatch):
         ea = np.abs(FA2[sl] - FA6[sl]).max() / np.abs(FA6[sl]).max()
         eb = np.abs(FB2[sl] - FB6[sl]).max() / np.abs(FB6[sl]).max()
         assert ea < 2e-13 and eb < 2e-13, (b, ea, eb)
+
+
+def test_fused_update_gives_bitwise_the_two_launch_results(monkeypatch):
+    """The ring sweep that advances each instance itself (one launch per sweep) and the ring sweep
+    followed by a separate update launch compute the same arithmetic in the same order: a ragged
+    batch of the scan (both FP32 and FP64 phases, converging, cycling and diverging instances)
+    ends bitwise equal, with equal statuses and sweep counts."""
+    batch = inputs.scan_batch(192)
+    res = []
+    for fused in ("1", "0"):
+        monkeypatch.setenv("QDSE_FUSED_UPDATE", fused)  # 1: one launch per tick
+        res.append(_solve_scan(batch, 1, max_iter=3000))
+    (A1, B1, s1, i1, _, _), (A0, B0, s0, i0, _, _) = res
+    assert np.array_equal(s1, s0) and np.array_equal(i1, i0)
+    assert np.array_equal(A1, A0, equal_nan=True) and np.array_equal(B1, B0, equal_nan=True)
+    assert (s1 == 0).sum() > 50
