@@ -110,7 +110,8 @@ void free_ctx(qdse_ctx* c) {
                     c->d_count, c->d_sweeps, c->d_hostA, c->d_hostI, c->grid.band,
                     c->grid.groups, c->grid.nnz, c->grid.gdesc, c->grid.gphase, c->work.ilist,
                     c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd,
-                    c->grid.W32, c->grid.wt32, c->grid.stc32, c->grid.expt, c->work.hring, c->work.ticket, c->work.col};
+                    c->grid.W32, c->grid.wt32, c->grid.stc32, c->grid.expt, c->work.hring, c->work.ticket, c->work.col,
+                    c->work.slist, c->grid.slabs, c->work.sphase, c->work.claim};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -151,6 +152,7 @@ qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
         d.mode = h.g.grid_mode;
         d.v_off = h.v_off;
         d.g_off = h.g_off;
+        d.s_off = h.s_off;
         d.D = p[b].D;
         d.omega = p[b].omega;
         d.m = p[b].m;
@@ -212,6 +214,8 @@ cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
     if (e != cudaSuccess) return e;
     if (otf) {
         e = launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1);
+    } else if (c->sweep_kind == 2) {
+        e = launch_tick_slab(c, A, B);
     } else if (c->sweep_kind == 1) {
         // the ring sweep advances every instance itself once its last row group is swept
         e = launch_tick_ring(c, A, B);
@@ -407,11 +411,28 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     c->n_tiles = (int)tiles.size();
     std::vector<int2> groups;
     std::vector<GroupDesc> gdesc;
+    std::vector<SlabRec> slabs;
     groups.reserve(ng);
     gdesc.reserve(ng);
     for (int b = 0; b < n_inst; ++b) {
         HostInst& h = c->hinst[b];
         h.g_off = (int)groups.size();
+        h.s_off = (int)slabs.size();
+        const int ngb = (h.g.n_p + kRows - 1) / kRows;
+        for (int g0 = 0; g0 < ngb; g0 += kSlabGroups) {
+            SlabRec r{};
+            r.b = b;
+            r.g0 = g0;
+            r.ng = std::min(kSlabGroups, ngb - g0);
+            r.x_off = h.x_off;
+            r.v_off = h.v_off;
+            r.n = h.g.n_p;
+            r.ld = h.ld;
+            r.mode = h.g.grid_mode;
+            r.k_off = h.k_off;
+            for (int q = 0; q < kSlabGroups; ++q) r.band[q] = make_int2(0, q < r.ng ? h.ld : 0);
+            slabs.push_back(r);
+        }
         for (int i0 = 0; i0 < h.g.n_p; i0 += kRows) {
             groups.push_back(make_int2(b, i0));
             GroupDesc d{};
@@ -495,7 +516,13 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     }
     CALLOC(c->work.ilist, 3 * (size_t)n_inst);
     CALLOC(c->work.glist, 3 * (size_t)ng);
-    CALLOC(c->work.lcount, 6);
+    CALLOC(c->work.lcount, 9);
+    c->n_slabs = (int)slabs.size();
+    c->work.n_slabs = c->n_slabs;
+    CALLOC(c->work.slist, 3 * (size_t)c->n_slabs);
+    CALLOC(c->work.sphase, c->n_slabs);
+    CALLOC(c->work.claim, 3);
+    CALLOC(c->grid.slabs, c->n_slabs);
     CALLOC(c->work.hring, (size_t)kHashRing * n_inst);
     CALLOC(c->work.ticket, n_inst);
     CALLOC(c->work.col, 2 * (size_t)N);
@@ -553,7 +580,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         {c->grid.groups, groups.data(), sizeof(int2) * ng},
         {c->grid.gdesc, gdesc.data(), sizeof(GroupDesc) * ng},
         {c->d_tiles, tiles.data(), sizeof(int4) * c->n_tiles},
-        {c->grid.expt, expt.data(), sizeof(float2) * expt.size()}};
+        {c->grid.expt, expt.data(), sizeof(float2) * expt.size()},
+        {c->grid.slabs, slabs.data(), sizeof(SlabRec) * slabs.size()}};
     for (auto& u : ups) {
         e = cudaMemcpy(u.d, u.h, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -583,7 +611,10 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         const char* k = std::getenv("QDSE_SWEEP");
         const bool ring_ok = configure_tick_ring() == cudaSuccess;
         cudaGetLastError();
+        const bool slab_ok = configure_tick_slab() == cudaSuccess;
+        cudaGetLastError();
         c->sweep_kind = ring_ok ? 1 : 0;
+        if (k && std::string(k) == "slab" && slab_ok) c->sweep_kind = 2;
         if (k && std::string(k) == "groups") c->sweep_kind = 0;
         // QDSE_FUSED_UPDATE=1: the ring sweep advances each instance itself (one launch per tick;
         // the same arithmetic in the same order as the separate update launch, but measured

@@ -102,6 +102,53 @@ struct BlockTeam {
         return warp_maxf(v);  // every warp reduces the per-warp maxima itself
     }
     __device__ bool any(bool v) const { return __syncthreads_or(v) != 0; }
+    // max of a and OR of f over the block in one exchange (every thread gets both)
+    __device__ void maxf_or(float& a, int& f) const {
+        a = warp_maxf(a);
+        f = __any_sync(0xffffffffu, f != 0) ? 1 : 0;
+        float* fs = reinterpret_cast<float*>(sh);
+        int* is = reinterpret_cast<int*>(sh) + 32;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            fs[threadIdx.x >> 5] = a;
+            is[threadIdx.x >> 5] = f;
+        }
+        __syncthreads();
+        const int nw = blockDim.x >> 5;
+        float m = fs[0];
+        int o = is[0];
+        for (int k = 1; k < nw; ++k) {
+            m = fmaxf(m, fs[k]);
+            o |= is[k];
+        }
+        __syncthreads();
+        a = m;
+        f = o;
+    }
+    // max of a and XOR of h over the block in one exchange (every thread gets both)
+    __device__ void maxf_xor(float& a, unsigned long long& h) const {
+        a = warp_maxf(a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
+        float* fs = reinterpret_cast<float*>(sh);
+        auto* hs = reinterpret_cast<unsigned long long*>(sh) + 8;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            fs[threadIdx.x >> 5] = a;
+            hs[threadIdx.x >> 5] = h;
+        }
+        __syncthreads();
+        const int nw = blockDim.x >> 5;
+        float m = fs[0];
+        unsigned long long x = hs[0];
+        for (int k = 1; k < nw; ++k) {
+            m = fmaxf(m, fs[k]);
+            x ^= hs[k];
+        }
+        __syncthreads();
+        a = m;
+        h = x;
+    }
     // XOR of v over the block (every thread gets it)
     __device__ unsigned long long xor_all(unsigned long long v) const {
 #pragma unroll
@@ -138,6 +185,14 @@ struct WarpTeam {
     __device__ bool any(bool v) const { return __any_sync(0xffffffffu, v) != 0; }
     __device__ bool leader() const { return (threadIdx.x & 31) == 0; }
     __device__ int bcast(int v) const { return __shfl_sync(0xffffffffu, v, 0); }
+    __device__ void maxf_or(float& a, int& f) const {
+        a = warp_maxf(a);
+        f = __any_sync(0xffffffffu, f != 0) ? 1 : 0;
+    }
+    __device__ void maxf_xor(float& a, unsigned long long& h) const {
+        a = warp_maxf(a);
+        h = xor_all(h);
+    }
     __device__ unsigned long long xor_all(unsigned long long v) const {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
@@ -610,18 +665,24 @@ __device__ __forceinline__ void tick_group(const GroupDesc& d, int phase, int la
 
 // Copy every instance's parameters into its row groups' descriptors (after each upload): the
 // FP32 sweep's scale kappa D and mass m.
-__global__ void k_group_params(const DevInst* __restrict__ inst, Grid g, int ngroups,
+__global__ void k_group_params(const DevInst* __restrict__ inst, Grid g, int ngroups, int nslabs,
                                double kappa) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ngroups) return;
-    const DevInst I = inst[g.gdesc[t].b];
-    g.gdesc[t].mode = I.mode;
-    g.gdesc[t].sc32 = (float)(kappa * I.D);
-    g.gdesc[t].m32 = (float)I.m;
+    if (t < ngroups) {
+        const DevInst I = inst[g.gdesc[t].b];
+        g.gdesc[t].mode = I.mode;
+        g.gdesc[t].sc32 = (float)(kappa * I.D);
+        g.gdesc[t].m32 = (float)I.m;
+    }
+    if (t < nslabs) {
+        const DevInst I = inst[g.slabs[t].b];
+        g.slabs[t].sc32 = (float)(kappa * I.D);
+        g.slabs[t].m32 = (float)I.m;
+    }
 }
 
 // Narrow every group's column range to the union of its rows' nonzero bands.
-__global__ void k_group_bands(Grid g, int ngroups) {
+__global__ void k_group_bands(const DevInst* __restrict__ inst, Grid g, int ngroups) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ngroups) return;
     GroupDesc d = g.gdesc[t];
@@ -634,6 +695,10 @@ __global__ void k_group_bands(Grid g, int ngroups) {
     if (hi <= lo) lo = hi = 0;
     g.gdesc[t].jlo = lo;
     g.gdesc[t].jhi = hi;
+    // ... and the same band in the group's slab record
+    const int lg = d.i0 / kRows;  // the group's index in its instance
+    const int s_off = inst[d.b].s_off;
+    g.slabs[s_off + lg / kSlabGroups].band[lg % kSlabGroups] = make_int2(lo, hi);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -809,8 +874,14 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         const int ng = (I.n + kRows - 1) / kRows;
         const int gb = atomicAdd(w.lcount + 3, ng);
         for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
+        const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
+        const int sb = atomicAdd(w.lcount + 6, ns);
+        for (int t = 0; t < ns; ++t) w.slist[sb + t] = I.s_off + t;
     }
     for (int t = threadIdx.x; t < (I.n + kRows - 1) / kRows; t += blockDim.x) g.gphase[I.g_off + t] = phase0;
+    for (int t = threadIdx.x; t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
+         t += blockDim.x)
+        w.sphase[I.s_off + t] = phase0;
     if (threadIdx.x == 0) w.ticket[b] = 0;
     prepare_phase(phase0, I, g, w, ntot, A, B);
 }
@@ -885,10 +956,21 @@ __device__ __forceinline__ bool track_progress(DevState& s, const Ctl& C) {
 // The block's hash of the new iterate (h: this thread's part) through cycle_check; true when the
 // cycle stop applies.  Every thread of the team gets the same answer.
 template <typename Team>
+__device__ __forceinline__ bool picard_cycle_reduced(const Team& T, DevState& s, const Ctl& C,
+                                                     unsigned long long h,
+                                                     unsigned long long* ring);
+template <typename Team>
 __device__ __forceinline__ bool picard_cycle(const Team& T, DevState& s, const Ctl& C,
                                              unsigned long long h, unsigned long long* ring) {
     if (!C.stop_cycles || C.never_converge) return false;
-    h = T.xor_all(h);
+    return picard_cycle_reduced(T, s, C, T.xor_all(h), ring);
+}
+// The same with the block's hash h already reduced.
+template <typename Team>
+__device__ __forceinline__ bool picard_cycle_reduced(const Team& T, DevState& s, const Ctl& C,
+                                                     unsigned long long h,
+                                                     unsigned long long* ring) {
+    if (!C.stop_cycles || C.never_converge) return false;
     int period = 0;
     if (T.leader()) {
         period = cycle_check(s, h, ring);
@@ -905,11 +987,48 @@ __device__ __forceinline__ bool picard_cycle(const Team& T, DevState& s, const C
 // Advance one instance after a tick.  One block (256 threads) per instance.
 // Sweep outputs (xn32, xn64) are read with L2-coherent loads (they come from other SMs; this keeps
 // the update correct even when it runs inside the kernel that wrote them).
+// snew: NULL, or shared memory for 2 kMaxN floats: the block then keeps its points in registers
+// (kUpdPts per thread) and builds the next FP32 sweep's node vectors from the new iterate there.
+constexpr int kUpdThreads = 128;                                  // k_update's block
+constexpr int kUpdPts = (kMaxN + kUpdThreads - 1) / kUpdThreads;  // points per thread
+
+// prepare_vectors32 with the instance's new FP32 iterate in shared memory (xs[j], xs[kMaxN + j]):
+// the same values, bitwise (the same operations on the same inputs).
+__device__ void prepare_vectors32_shared(const DevInst& I, const Grid& g, int ntot,
+                                         const float* xs, float* vec, int vb, float* dia, int tid,
+                                         int nth) {
+    const float* xa = xs;
+    const float* xb = xs + kMaxN;
+    for (int j = tid; j < I.n; j += nth) {
+        const int gj = I.x_off + j;
+        const float wt = g.wt32[gj];
+        float a = xa[j], b = xb[j];
+        if (wt != 0.f) {
+            a = fmaf(wt, xa[j + 1] - a, a);
+            b = fmaf(wt, xb[j + 1] - b, b);
+        }
+        const float Q = g.sq32[gj];
+        const float e = g.W32[gj] / fmaf(Q * a, a, b * b);
+        const float ea = e * a;
+        vec[vpos(vb + j, 0)] = a;
+        vec[vpos(vb + j, 1)] = b;
+        vec[vpos(vb + j, 2)] = e * b;
+        vec[vpos(vb + j, 3)] = ea;
+        vec[vpos(vb + j, 4)] = ea * Q;
+        if (I.mode == QDSE_COLLOCATED) {
+            const int s0 = g.sta[gj];
+            const float* c = g.stc32 + 3 * (size_t)gj;
+            dia[gj] = fmaf(c[0], xa[s0] - xa[s0 + 1], c[2] * (xa[s0 + 2] - xa[s0 + 1]));
+            dia[ntot + gj] = fmaf(c[0], xb[s0] - xb[s0 + 1], c[2] * (xb[s0 + 2] - xb[s0 + 1]));
+        }
+    }
+}
+
 template <typename Team>
 __device__ void update_instance(const Team& T, int b, const DevInst* __restrict__ inst,
                                 DevState* state, const Ctl* __restrict__ ctl, const Grid& g,
                                 const Work& w, double* A, double* B, int ntot, int* count,
-                                unsigned long long* ctr, int next_list) {
+                                unsigned long long* ctr, int next_list, float* snew = nullptr) {
     DevState s = state[b];
     if (s.phase == PH_DONE) return;
     const DevInst I = inst[b];
@@ -946,37 +1065,85 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         if (pf) asm volatile("prefetch.global.L1 [%0];" ::"l"(pf));
     }
 
+    bool fast32 = false;  // the FP32 iterate of this update is also in snew (see below)
     if (s.phase == PH_PICARD32) {
         // relaxed FP32 Picard step and its R7 relative change, in FP32 like the iterate
         const float al = (float)C.alpha, am = (float)(1.0 - C.alpha);
-        float bmax = 0.f;
-        bool badj = false;
-        for (int j = T.tid(); j < I.n; j += T.size()) {
-            const int gj = o + j;
-            const float fa = am * w.x32[gj] + al * __ldcg(w.xn32 + gj);
-            const float fb = am * w.x32[ntot + gj] + al * __ldcg(w.xn32 + ntot + gj);
-            bmax = fmaxf(bmax, fabsf(fb));
-            badj = badj || !isfinite(fa) || !isfinite(fb);
+        bool bad;
+        bool cycled;
+        if (snew && I.n <= kUpdPts * T.size()) {
+            // one pass of loads: every thread keeps its points in registers (the same arithmetic
+            // as the loop form below, with two block exchanges instead of five)
+            fast32 = true;
+            float xa[kUpdPts], xb[kUpdPts], fa[kUpdPts], fb[kUpdPts];
+            float bmax = 0.f;
+            int badj = 0;
+#pragma unroll
+            for (int k = 0; k < kUpdPts; ++k) {
+                const int j = T.tid() + k * T.size();
+                if (j < I.n) {
+                    const int gj = o + j;
+                    xa[k] = w.x32[gj];
+                    xb[k] = w.x32[ntot + gj];
+                    fa[k] = fmaf(al, __ldcg(w.xn32 + gj), am * xa[k]);
+                    fb[k] = fmaf(al, __ldcg(w.xn32 + ntot + gj), am * xb[k]);
+                    bmax = fmaxf(bmax, fabsf(fb[k]));
+                    badj |= (!isfinite(fa[k]) || !isfinite(fb[k])) ? 1 : 0;
+                }
+            }
+            T.maxf_or(bmax, badj);
+            bad = badj != 0;
+            const float fl = 1e-12f * bmax;
+            float ch = 0.f;
+            unsigned long long hsh = 0;
+#pragma unroll
+            for (int k = 0; k < kUpdPts; ++k) {
+                const int j = T.tid() + k * T.size();
+                if (j < I.n) {
+                    const int gj = o + j;
+                    ch = fmaxf(ch, fmaxf(rel_change32(fa[k] - xa[k], fa[k], 0.f),
+                                         rel_change32(fb[k] - xb[k], fb[k], fl)));
+                    w.x32[gj] = fa[k];
+                    w.x32[ntot + gj] = fb[k];
+                    snew[j] = fa[k];
+                    snew[kMaxN + j] = fb[k];
+                    hsh ^= point_hash32(fa[k], fb[k], j);
+                }
+            }
+            T.maxf_xor(ch, hsh);
+            s.change = (double)ch;
+            s.iters += 1;
+            cycled = picard_cycle_reduced(T, s, C, hsh, w.hring + (size_t)b * kHashRing);
+        } else {
+            float bmax = 0.f;
+            bool badj = false;
+            for (int j = T.tid(); j < I.n; j += T.size()) {
+                const int gj = o + j;
+                const float fa = fmaf(al, __ldcg(w.xn32 + gj), am * w.x32[gj]);
+                const float fb = fmaf(al, __ldcg(w.xn32 + ntot + gj), am * w.x32[ntot + gj]);
+                bmax = fmaxf(bmax, fabsf(fb));
+                badj = badj || !isfinite(fa) || !isfinite(fb);
+            }
+            bmax = T.maxf(bmax);
+            bad = T.any(badj);
+            const float fl = 1e-12f * bmax;
+            float ch = 0.f;
+            unsigned long long hsh = 0;
+            for (int j = T.tid(); j < I.n; j += T.size()) {
+                const int gj = o + j;
+                const float xa = w.x32[gj], xb = w.x32[ntot + gj];
+                const float fa = fmaf(al, __ldcg(w.xn32 + gj), am * xa);
+                const float fb = fmaf(al, __ldcg(w.xn32 + ntot + gj), am * xb);
+                ch = fmaxf(ch, fmaxf(rel_change32(fa - xa, fa, 0.f), rel_change32(fb - xb, fb, fl)));
+                w.x32[gj] = fa;
+                w.x32[ntot + gj] = fb;
+                hsh ^= point_hash32(fa, fb, j);
+            }
+            s.change = (double)T.maxf(ch);
+            s.iters += 1;
+            cycled = picard_cycle(T, s, C, hsh, w.hring + (size_t)b * kHashRing);
         }
-        bmax = T.maxf(bmax);
-        const bool bad = T.any(badj);
-        const float fl = 1e-12f * bmax;
-        float ch = 0.f;
-        unsigned long long hsh = 0;
-        for (int j = T.tid(); j < I.n; j += T.size()) {
-            const int gj = o + j;
-            const float xa = w.x32[gj], xb = w.x32[ntot + gj];
-            const float fa = am * xa + al * __ldcg(w.xn32 + gj);
-            const float fb = am * xb + al * __ldcg(w.xn32 + ntot + gj);
-            ch = fmaxf(ch, fmaxf(rel_change32(fa - xa, fa, 0.f), rel_change32(fb - xb, fb, fl)));
-            w.x32[gj] = fa;
-            w.x32[ntot + gj] = fb;
-            hsh ^= point_hash32(fa, fb, j);
-        }
-        s.change = (double)T.maxf(ch);
-        s.iters += 1;
         const bool stalled = track_progress(s, C);
-        const bool cycled = picard_cycle(T, s, C, hsh, w.hring + (size_t)b * kHashRing);
         if (bad) {
             done = true;
             status = QDSE_ERR_NONFINITE;
@@ -1122,7 +1289,10 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             }
             T.sync();
         }
-        if (next != PH_TANGENT32 || s.phase == PH_TANGENT32) {
+        if (fast32 && next == PH_PICARD32) {
+            prepare_vectors32_shared(I, g, ntot, snew, w.vec32, I.v_off, w.dia32, T.tid(),
+                                     T.size());
+        } else if (next != PH_TANGENT32 || s.phase == PH_TANGENT32) {
             prepare_phase(next, I, g, w, ntot, A, B, T.tid(), T.size());
         } else {
             prepare_tangent<float, float, float>(I, g, ntot, w.x32, w.x32 + ntot, w.d32,
@@ -1131,6 +1301,9 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         }
     }
     for (int t = T.tid(); t < (I.n + kRows - 1) / kRows; t += T.size()) g.gphase[I.g_off + t] = next;
+    for (int t = T.tid(); t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
+         t += T.size())
+        w.sphase[I.s_off + t] = next;
     if (T.leader()) {
         if (next != s.phase) {  // a new phase starts its own progress and cycle records
             s.cbest = INFINITY;
@@ -1151,11 +1324,15 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         }
     }
     if (!done) {
-        // ... and so do its row groups
+        // ... and so do its row groups and slabs
         const int ng = (I.n + kRows - 1) / kRows;
+        const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
         const int gb = T.bcast(T.leader() ? atomicAdd(w.lcount + 3 + next_list, ng) : 0);
+        const int sb = T.bcast(T.leader() ? atomicAdd(w.lcount + 6 + next_list, ns) : 0);
         for (int t = T.tid(); t < ng; t += T.size())
             w.glist[(size_t)next_list * w.n_groups + gb + t] = I.g_off + t;
+        for (int t = T.tid(); t < ns; t += T.size())
+            w.slist[(size_t)next_list * w.n_slabs + sb + t] = I.s_off + t;
     }
     T.sync();
 }
@@ -1432,6 +1609,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         const int clr = (list + 2) % 3;
         w.lcount[clr] = 0;
         w.lcount[3 + clr] = 0;
+        w.lcount[6 + clr] = 0;
     }
     __syncthreads();
     const int nact = w.lcount[3 + list];
@@ -1699,9 +1877,319 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Slab sweep: the tick of k_tick_ring with the bookkeeping done per slab instead of per row group.
+// A slab is up to kSlabGroups consecutive row groups (32 rows) of one instance, so its groups share
+// the instance's phase, grid mode, vectors and parameters.  Per slab a warp
+//   - reads the slab's 128-byte record (instance offsets, parameters, every group's band) and its
+//     phase, requested two slabs ahead by small asynchronous copies (cp.async), like the list id
+//     of the slab after that;
+//   - finds the row constants of its 32 rows in shared memory: lane l copies row l's constants
+//     (A_i, B_i, P_i, the stencil quotients, K_T(i,i), u1 and u2 at p_i) one slab ahead;
+//   - streams every group's tiles through the same two-slot bulk-copy ring as k_tick_ring, the
+//     copying side running on into the next slab, never beyond it.
+// The tile arithmetic, the warp totals and the stores of a group are those of k_tick_ring.
+// Slabs in an FP64 phase take the global-memory path of tick_group, group by group.
+constexpr int kSlabWarps = 11;   // 11 warps x 2 slots x 8.5 KB + queues fit the 227 KB of an SM
+constexpr int kSlabRc = 8;       // row constants per row (see above)
+constexpr int kSlabRing = 4;     // records and ids: slabs k .. k + 3
+struct SlabQueue {
+    SlabRec rec[kSlabRing];
+    int phase[kSlabRing];
+    int id[kSlabRing];
+    float rc[2][kSlabRc][32];    // row constants of slabs k and k + 1 (by parity), [constant][row]
+};
+static_assert(sizeof(SlabQueue) % 16 == 0, "slab queues must stay 16-byte aligned");
+constexpr size_t kSlabTileBytes = (size_t)kSlabWarps * 2 * kTileFloats * sizeof(float);
+constexpr size_t kSlabBarBytes = (size_t)kSlabWarps * 2 * 8;
+constexpr size_t kSlabSmem = kSlabTileBytes + kSlabBarBytes + kSlabWarps * sizeof(SlabQueue);
+static_assert(kSlabSmem <= 227 * 1024, "slab sweep shared memory");
+static_assert(kSlabBarBytes % 16 == 0, "slab queues must start 16-byte aligned");
+static_assert(kRows * kSlabGroups == 32, "a slab's rows are one per lane");
+
+__global__ void __launch_bounds__(kSlabWarps * 32, 1)
+    k_tick_slab(const DevInst* __restrict__ inst, const Ctl* __restrict__ ctl, Grid g, Work w,
+                const float* __restrict__ Khi, const float* __restrict__ Klo, const double* A,
+                const double* B, int ntot, int list, int* err) {
+    constexpr int S = 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * S * kTileFloats;
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(smem + kSlabTileBytes) + warp * S;
+    SlabQueue& q = reinterpret_cast<SlabQueue*>(smem + kSlabTileBytes + kSlabBarBytes)[warp];
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[k]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // Every warp of the grid claims slabs from one counter of the active list (the counter of the
+    // next tick is cleared here); each claim is issued one slab before its result is used, so the
+    // atomic's round trip overlaps a slab's work.
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.claim[(list + 1) % 3] = 0;
+    const int nact = w.lcount[6 + list];
+    const int* ids = w.slist + (size_t)list * w.n_slabs;
+    int* ctr_claim = w.claim + list;
+    int pending = (lane == 0) ? atomicAdd(ctr_claim, 1) : 0;
+    auto claim = [&]() -> int {
+        const int c = __shfl_sync(0xffffffffu, pending, 0);
+        if (lane == 0) pending = (c < nact) ? atomicAdd(ctr_claim, 1) : c;
+        return c < nact ? c : -1;
+    };
+    if (*reinterpret_cast<volatile const int*>(err)) return;
+    const bool bc = (ctl->vertex == QDSE_VERTEX_BC);
+    const int stall = ctl->stall_copies ? 16 : 0;
+    const uint64_t pol = lane == 0 ? evict_first_policy() : evict_last_policy();
+
+    int nmine = 1 << 30;  // slabs this warp claimed: known once a claim fails
+    // the record (eight 16-byte words) and phase of slab k, whose id is in the queue
+    auto request_rec = [&](int k) {
+        const int id = q.id[k % kSlabRing];
+        if (lane < 8) {
+            cp16(reinterpret_cast<int4*>(&q.rec[k % kSlabRing]) + lane,
+                 reinterpret_cast<const int4*>(g.slabs + id) + lane);
+        } else if (lane == 8) {
+            cp4(&q.phase[k % kSlabRing], w.sphase + id);
+        }
+    };
+    // the row constants of slab k (record in the queue): lane l copies row 4 g0 + l's
+    auto request_rc = [&](int k) {
+        const SlabRec& R = q.rec[k % kSlabRing];
+        const int i = kRows * R.g0 + lane;
+        if (lane < kRows * R.ng && i < R.n) {
+            const int o = R.x_off + i;
+            float(*rc)[32] = q.rc[k & 1];
+            cp4(&rc[0][lane], w.x32 + o);
+            cp4(&rc[1][lane], w.x32 + ntot + o);
+            cp4(&rc[2][lane], g.sp32 + o);
+            cp4(&rc[3][lane], w.dia32 + o);
+            cp4(&rc[4][lane], w.dia32 + ntot + o);
+            cp4(&rc[5][lane], g.ktd + o);
+            cp4(&rc[6][lane], w.vec32 + vpos(R.v_off + i, 2));
+            cp4(&rc[7][lane], w.vec32 + vpos(R.v_off + i, 3));
+        }
+    };
+    // prologue: ids of slabs 0 .. 2, then the records of slabs 0 and 1, then slab 0's rows
+    for (int k = 0; k < 3 && k < nmine; ++k) {
+        const int c = claim();
+        if (c < 0) nmine = k;
+        else if (lane == 0) cp4(&q.id[k], ids + c);
+    }
+    if (nmine == 0) return;
+    cp_commit();
+    cp_wait(0);
+    __syncwarp();
+    for (int k = 0; k < 2 && k < nmine; ++k) request_rec(k);
+    cp_commit();
+    cp_wait(0);
+    __syncwarp();
+    request_rc(0);
+    cp_commit();
+
+    // copying side: slab ps, group pg of it, its tiles from column pc while ptiles
+    int ps = 0, pg = -1, pc = 0, pjhi = 0, pnr = 0, pvoff = 0;
+    long long pkbase = 0;
+    bool ptiles = false;
+    unsigned issued = 0, consumed = 0;
+    // one step of the copying side: issue one tile, or move onto the next group with tiles
+    // (possibly in the next slab, never beyond the slab after the computing side's ck)
+    auto produce = [&](int ck) -> bool {
+        while (!ptiles) {
+            int s_ = ps, g_ = pg + 1;
+            if (s_ >= nmine || s_ > ck + 1) return false;
+            const SlabRec* R = &q.rec[s_ % kSlabRing];
+            int ph = q.phase[s_ % kSlabRing];
+            if (g_ >= R->ng || (ph != PH_PICARD32 && ph != PH_TANGENT32)) {
+                s_ += 1;
+                g_ = 0;
+                if (s_ >= nmine || s_ > ck + 1) return false;
+                R = &q.rec[s_ % kSlabRing];
+                ph = q.phase[s_ % kSlabRing];
+                if (ph != PH_PICARD32 && ph != PH_TANGENT32) {  // an FP64 slab: no tiles
+                    ps = s_;
+                    pg = R->ng;
+                    continue;
+                }
+            }
+            ps = s_;
+            pg = g_;
+            const int2 bd = R->band[g_];
+            const int i0 = kRows * (R->g0 + g_);
+            if (bd.y > bd.x) {
+                pc = bd.x;
+                pjhi = bd.y;
+                pnr = min(kRows, R->n - i0);
+                pvoff = R->v_off;
+                pkbase = R->k_off + 3LL * i0 * R->ld;
+                ptiles = true;
+            }
+        }
+        const int slot = issued % S;
+        const uint32_t bar = smem_addr(&bars[slot]);
+        const int cols = min(kTileCols, pjhi - pc);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"((uint32_t)(cols * (3 * pnr + 5) * 4 + stall))
+                         : "memory");
+        __syncwarp();
+        if (lane < 2) {
+            float* dst = ring + slot * kTileFloats + (lane ? kVecOff : 0);
+            const float* src = lane ? w.vec32 + vpos(pvoff + pc, 0)
+                                    : Khi + pkbase + (long long)(pc >> 2) * 3 * pnr * 4;
+            bulk_copy_hint(dst, src, cols * (lane ? 5 : 3 * pnr) * 4, bar, pol);
+        }
+        ++issued;
+        pc += kTileCols;
+        if (pc >= pjhi) ptiles = false;
+        return true;
+    };
+    auto fill = [&](int ck) {
+        while (issued - consumed < (unsigned)S && produce(ck)) {
+        }
+    };
+
+    const int qv = group_total_index(lane), rr = qv % kRows;
+    const bool isB = qv >= kRows;
+    bool ok = true;
+    for (int ck = 0; ck < nmine && ok; ++ck) {
+        // slab ck's rows, slab ck + 1's record and slab ck + 2's id have arrived (requested one
+        // slab earlier); request slab ck + 1's rows, slab ck + 2's record, slab ck + 3's id
+        cp_wait(0);
+        __syncwarp();
+        if (ck + 1 < nmine) request_rc(ck + 1);
+        if (ck + 2 < nmine) request_rec(ck + 2);
+        if (ck + 3 < nmine) {
+            const int c = claim();
+            if (c < 0) nmine = ck + 3;
+            else if (lane == 0) cp4(&q.id[(ck + 3) % kSlabRing], ids + c);
+        }
+        cp_commit();
+        const SlabRec& R = q.rec[ck % kSlabRing];
+        const int phase = q.phase[ck % kSlabRing];
+        if (phase != PH_PICARD32 && phase != PH_TANGENT32) {
+            if (phase == PH_RESID64 || phase == PH_PICARD64) {
+                const DevInst I = inst[R.b];
+                for (int gi = 0; gi < R.ng; ++gi) {
+                    GroupDesc d{};
+                    d.b = R.b;
+                    d.i0 = kRows * (R.g0 + gi);
+                    d.nr = min(kRows, R.n - d.i0);
+                    tick_group(d, phase, lane, I, ctl, g, w, Khi, Klo, A, B, ntot);
+                }
+            }
+            continue;
+        }
+        const float(*rc)[32] = q.rc[ck & 1];
+        const bool tan = (phase == PH_TANGENT32);
+        const int collocated = (R.mode == QDSE_COLLOCATED) && bc;
+        for (int gi = 0; gi < R.ng; ++gi) {
+            const int i0 = kRows * (R.g0 + gi), nr = min(kRows, R.n - i0), o = R.x_off + i0;
+            const int jlo = R.band[gi].x, jhi = R.band[gi].y;
+            const bool full = !tan && bc && nr == kRows;
+            Rows32 Rw;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                Rw.sA[r] = 0.f;
+                Rw.sB[r] = 0.f;
+                const bool v = r < nr;
+                Rw.Ai[r] = rc[0][kRows * gi + r];
+                Rw.Bi[r] = rc[1][kRows * gi + r];
+                Rw.Pi[r] = rc[2][kRows * gi + r];
+                Rw.dAi[r] = (tan && v) ? __ldg(w.d32 + o + r) : 0.f;
+                Rw.dBi[r] = (tan && v) ? __ldg(w.d32 + ntot + o + r) : 0.f;
+            }
+            fill(ck);
+            for (int c = jlo; c < jhi; c += kTileCols) {
+                const int slot = consumed % S;
+                const bool got = ring_wait(smem_addr(&bars[slot]), (consumed / S) & 1);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                const int col = c + 4 * lane;
+                const int wc = min(kTileCols, jhi - c);
+                const float* sl = ring + slot * kTileFloats;
+                if (full && wc <= kTileCols / 4) {
+                    narrow_tile32<4>(Rw, sl, c, jhi, lane);
+                } else if (full && wc <= kTileCols / 2) {
+                    narrow_tile32<2>(Rw, sl, c, jhi, lane);
+                } else if (col < jhi) {
+                    const float* vb = sl + kVecOff + lane * 20;
+                    auto V4 = [&](int comp) {
+                        return *reinterpret_cast<const float4*>(vb + 4 * comp);
+                    };
+                    const float4 a = V4(0), b = V4(1), u1 = V4(2), u2 = V4(3), u3 = V4(4);
+                    if (full) {
+                        const float* kb = sl + lane * (3 * kRows * 4);
+                        const int sw = ((col >> 2) >> 1) & 3;
+                        auto K = [&](int r, int pl) {
+                            return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
+                        };
+                        rows32_chunk<false>(Rw, K, kRows, 0, true, 0, a, b, u1, u2, u3, a, a, a, a,
+                                            a);
+                    } else {
+                        const float* kb = sl + lane * 3 * nr * 4;
+                        const int sw = kswz(nr, col >> 2);
+                        auto K = [&](int r, int pl) {
+                            return *reinterpret_cast<const float4*>(kb + ((3 * r + pl) ^ sw) * 4);
+                        };
+                        if (tan) {
+                            const float* db_ = w.dvec32 + vpos(R.v_off + col, 0);
+                            const float4 ea = ld4(db_), eb = ld4(db_ + 4), e1 = ld4(db_ + 8),
+                                         e2 = ld4(db_ + 12), e3 = ld4(db_ + 16);
+                            rows32_chunk<true>(Rw, K, nr, 0, bc, 0, a, b, u1, u2, u3, ea, eb, e1,
+                                               e2, e3);
+                        } else {
+                            rows32_chunk<false>(Rw, K, nr, 0, bc, 0, a, b, u1, u2, u3, a, a, a, a,
+                                                a);
+                        }
+                    }
+                }
+                __syncwarp();
+                ++consumed;
+                fill(ck);
+            }
+            if (!ok) break;
+            float tot = group_totals(Rw.sA, Rw.sB, lane);
+            if (group_total_leader(lane) && rr < nr) {
+                const int row = kRows * gi + rr;
+                const float Pl = rc[2][row];
+                if (collocated) {
+                    // removable limit q^2 -> p^2 of row i0 + rr
+                    const float KTd = rc[5][row], qA = rc[3][row], qB = rc[4][row];
+                    const float x1 = rc[6][row], x2 = rc[7][row];
+                    if (!tan) {
+                        tot += isB ? (x1 * qA - x2 * qB) * KTd : (-x1 * qB - Pl * x2 * qA) * KTd;
+                    } else {
+                        const int ir = R.v_off + i0 + rr;
+                        const float y1 = __ldg(w.dvec32 + vpos(ir, 2)),
+                                    y2 = __ldg(w.dvec32 + vpos(ir, 3));
+                        const float eqA = __ldg(w.ddia32 + o + rr),
+                                    eqB = __ldg(w.ddia32 + ntot + o + rr);
+                        tot += isB ? (y1 * qA + x1 * eqA - y2 * qB - x2 * eqB) * KTd
+                                   : (-y1 * qB - x1 * eqB - Pl * (y2 * qA + x2 * eqA)) * KTd;
+                    }
+                }
+                const float sc = R.sc32;
+                if (!isB) w.xn32[o + rr] = tan ? __fdividef(sc * tot, Pl) : 1.f + __fdividef(sc * tot, Pl);
+                else w.xn32[ntot + o + rr] = tan ? sc * tot : R.m32 + sc * tot;
+            }
+        }
+    }
+    cp_wait(0);  // no small copy may land after the block has released its shared memory
+    if (!ok) {
+        if (lane == 0) atomicExch(err, 1);
+        for (unsigned u = consumed; u < issued; ++u)
+            ring_wait(smem_addr(&bars[u % S]), (u / S) & 1);
+    }
+}
+
 // Advance every instance on the current active list after a tick's sweep (one block per instance,
 // blocks persistent over the list).
-__global__ void __launch_bounds__(128) k_update(const DevInst* __restrict__ inst, DevState* state,
+__global__ void __launch_bounds__(kUpdThreads, 6) k_update(const DevInst* __restrict__ inst, DevState* state,
                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
                                                 double* A, double* B, int ntot, int* count,
                                                 unsigned long long* ctr, int list,
@@ -1712,14 +2200,16 @@ __global__ void __launch_bounds__(128) k_update(const DevInst* __restrict__ inst
         const int clr = (list + 2) % 3;  // lists of two ticks ahead start empty
         w.lcount[clr] = 0;
         w.lcount[3 + clr] = 0;
+        w.lcount[6 + clr] = 0;
     }
     __shared__ double sh[32];
+    __shared__ float snew[2 * kMaxN];
     const BlockTeam T{sh};  // one block per instance
     const int n = w.lcount[list];
     const int* ids = w.ilist + (size_t)list * w.n_inst;
     for (int k = blockIdx.x; k < n; k += gridDim.x)
         update_instance(T, ids[k], inst, state, ctl, g, w, A, B, ntot, count, ctr,
-                        (list + 1) % 3);
+                        (list + 1) % 3, blockDim.x == kUpdThreads ? snew : nullptr);
 }
 
 // Copy the final iterate out of the FP32 store where needed and report per-instance results.
@@ -1831,7 +2321,9 @@ static inline int row_blocks(int ntot) { return (ntot + 7) / 8; }
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0) {
     cudaError_t e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c->work.lcount, 0, 6 * sizeof(int), c->stream);
+    e = cudaMemsetAsync(c->work.lcount, 0, 9 * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c->work.claim, 0, 3 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     c->tick = 0;
     prof_begin(c, PK_OTHER);
@@ -1844,7 +2336,8 @@ cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B,
 
 cudaError_t launch_group_bands(qdse_ctx* c) {
     prof_begin(c, PK_OTHER);
-    k_group_bands<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(c->grid, c->n_groups);
+    k_group_bands<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(c->d_inst, c->grid,
+                                                                     c->n_groups);
     c->launches++;
     prof_end(c);
     return cudaGetLastError();
@@ -1853,7 +2346,7 @@ cudaError_t launch_group_bands(qdse_ctx* c) {
 cudaError_t launch_group_params(qdse_ctx* c) {
     if (c->n_groups <= 0) return cudaSuccess;
     k_group_params<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(
-        c->d_inst, c->grid, c->n_groups, c->opt.cf / (8.0 * kPi * kPi * kPi));
+        c->d_inst, c->grid, c->n_groups, c->n_slabs, c->opt.cf / (8.0 * kPi * kPi * kPi));
     c->launches++;
     return cudaGetLastError();
 }
@@ -1873,6 +2366,23 @@ cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B) {
         c->d_inst, c->d_state, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
         (int)(c->tick % 3), c->d_count, c->d_sweeps, c->fused_update, c->d_err);
     if (c->fused_update) c->tick++;  // otherwise launch_update advances the tick
+    c->launches++;
+    prof_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t configure_tick_slab() {
+    return cudaFuncSetAttribute(k_tick_slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSlabSmem);
+}
+
+cudaError_t launch_tick_slab(qdse_ctx* c, double* A, double* B) {
+    prof_begin(c, PK_SWEEP);
+    const int sms = c->n_sms > 0 ? c->n_sms : 152;
+    const int blocks = std::max(1, std::min((c->n_slabs + kSlabWarps - 1) / kSlabWarps, sms));
+    k_tick_slab<<<blocks, kSlabWarps * 32, kSlabSmem, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
+        (int)(c->tick % 3), c->d_err);
     c->launches++;
     prof_end(c);
     return cudaGetLastError();

@@ -46,6 +46,8 @@ struct DevInst {          // per-instance descriptor, read-only during a solve
     int mode;             // QDSE_COLLOCATED / QDSE_STAGGERED
     int v_off;            // first node of this instance in the padded FP32 node vectors
     int g_off;            // first row group of this instance
+    int s_off;            // first slab (kSlabGroups row groups) of this instance
+    int pad;
     double D, omega, m;   // current parameters
 };
 
@@ -59,6 +61,18 @@ struct GroupDesc {        // one row group (kRows consecutive external points of
     int ng;               // row groups of the instance
     int pad[2];
 };
+
+constexpr int kSlabGroups = 8;  // row groups per slab (the slab sweep's unit of work: 32 rows)
+
+struct SlabRec {          // one slab: up to kSlabGroups consecutive row groups of one instance
+    int b, g0, ng, x_off;      // instance, first group, groups in the slab, the instance's first point
+    int v_off, n, ld, mode;    // node-vector base, points, kernel columns, grid mode
+    long long k_off;           // the instance's kernel-pool block
+    float sc32, m32;           // kappa D and m in FP32 (refreshed with every parameter upload)
+    int2 band[kSlabGroups];    // union band [jlo, jhi) of every group of the slab
+    int pad[4];
+};
+static_assert(sizeof(SlabRec) == 128, "slab records are copied as eight 16-byte words");
 
 struct DevState {         // per-instance solver state, updated by the update kernel
     int phase;
@@ -120,12 +134,16 @@ struct Work {
     double* ddia64; // [2]
     double* lam;    // [2] adjoint iterate
     double* lamn;   // [2] adjoint sweep output
-    // active lists: instances and row groups still running, three buffers (tick t reads list
-    // t % 3, appends the survivors to (t + 1) % 3 and empties (t + 2) % 3);
-    // lcount = {instances[0..2], groups[0..2]}
+    // active lists: instances, row groups and slabs still running, three buffers (tick t reads
+    // list t % 3, appends the survivors to (t + 1) % 3 and empties (t + 2) % 3);
+    // lcount = {instances[0..2], groups[0..2], slabs[0..2]}
     int* ilist;     // [3][n_inst]
     int* glist;     // [3][n_groups]
-    int* lcount;    // [6]
+    int* lcount;    // [9]: instances, groups, slabs (three buffers each)
+    int* slist;     // [3][n_slabs] active slabs (same three-buffer scheme)
+    int* sphase;    // [n_slabs] the phase of the slab's instance for the coming sweep
+    int* claim;     // [3] slab claims of the tick that reads list t % 3 (the slab sweep)
+    int n_slabs;
     unsigned long long* hring;  // [n_inst][kHashRing] recent iterate hashes (cycle detection)
     int* ticket;    // [n_inst] row groups of the instance swept in the current tick (the fused
                     // update: the warp that completes the last one advances the instance)
@@ -163,6 +181,7 @@ struct Grid {              // FP64 grid arrays on the device (global point index
                               // sweep must read per plane)
     float* ktd;            // per external point: K_T at q = p (collocated grids; the entry the
                            // removable-limit term multiplies), 0 on staggered grids
+    struct SlabRec* slabs; // per slab: the slab sweep's record (bands refreshed with the kernels)
     float2* expt;          // exp(-a/4) and exp(-b/512) as (hi, lo) pairs for the FP32-pipe
                            // precompute (see k_precompute.cu)
 };
@@ -196,7 +215,7 @@ __host__ __device__ inline long long vpos(int x, int c) {
 
 struct HostInst {
     qdse_grid g;
-    int x_off, t_off, ld, v_off, g_off;
+    int x_off, t_off, ld, v_off, g_off, s_off;
     long long k_off;
 };
 
@@ -262,6 +281,7 @@ struct qdse_ctx {
     int n_total = 0;
     int nv_total = 0;        // sum of ld (padded FP32 vector length)
     int n_groups = 0;        // row groups of kRows
+    int n_slabs = 0;         // slabs of kSlabGroups row groups
     int t_total = 0;
     long long k_total = 0;   // floats per kernel plane set (sum of 3 n ld)
     int max_n = 0, max_nt = 0;
@@ -289,8 +309,8 @@ struct qdse_ctx {
     int* d_err = nullptr;     // = d_count + 1: set when a bounded device wait ran out
     int n_sms = 0;
     int ld_max = 0;           // widest kernel row of the batch
-    int sweep_kind = 0;       // FP32 sweep: 1 ring (bulk copies through shared memory, the
-                              // default), 0 register-only row groups
+    int sweep_kind = 0;       // FP32 sweep: 2 slab (bulk copies through shared memory, slabs of
+                              // row groups), 1 ring (the same per row group), 0 register-only
     int precompute_kind = 1;  // kernel matrices: 1 double-float on the FP32 pipe (default), 0 FP64
     int fused_update = 0;     // ring sweep: 1 advances each instance inside the sweep launch (one
                               // launch per tick), 0 in a separate k_update launch (the default)
@@ -342,6 +362,8 @@ void exp_tables(std::vector<float2>& out);
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B);
+cudaError_t launch_tick_slab(qdse_ctx* c, double* A, double* B);
+cudaError_t configure_tick_slab();
 cudaError_t configure_tick_ring();
 cudaError_t launch_group_bands(qdse_ctx* c);
 cudaError_t launch_group_params(qdse_ctx* c);

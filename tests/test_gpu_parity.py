@@ -114,15 +114,13 @@ RAGGED32 = [inputs.Instance(37, 16, 0.93, 0.5, 0.005), inputs.Instance(64, 32, 0
             inputs.Instance(130, 24, 1.1, 0.6, 0.1), inputs.Instance(300, 32, 0.6, 0.4, 0.0)]
 
 
-@pytest.mark.parametrize("kind", ["ring", "groups"])
+@pytest.mark.parametrize("kind", ["slab", "ring", "groups"])
 def test_fp32_sweep_kernels_track_oracle_on_ragged_batch(kind, monkeypatch):
-    """Both FP32 sweep kernels (the shared-memory ring, the default, and the register-only row
-    groups) on one ragged batch: last groups of 1, 2 and 4 rows, bands from a few columns to a
-    few hundred (tiles split at 128 columns), three sweeps each against the oracle's FP64 sweeps."""
-    if kind == "groups":
-        monkeypatch.setenv("QDSE_SWEEP", "groups")
-    else:
-        monkeypatch.delenv("QDSE_SWEEP", raising=False)
+    """The FP32 sweep kernels (slabs of row groups and single row groups through the shared-memory
+    ring, and the register-only row groups) on one ragged batch: last groups of 1, 2 and 4 rows,
+    last slabs of 1 to 8 groups, bands from a few columns to a few hundred (tiles split at 128
+    columns), three sweeps each against the oracle's FP64 sweeps."""
+    monkeypatch.setenv("QDSE_SWEEP", kind)
     ctx = Q.Context([grid(i) for i in RAGGED32], precision=Q.QDSE_FP32)
     x_off = ctx.layout()
     A = dev(np.ones(ctx.n_total)); B = dev(np.full(ctx.n_total, 0.3))

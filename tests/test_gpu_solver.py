@@ -105,3 +105,18 @@ def test_fused_update_gives_bitwise_the_two_launch_results(monkeypatch):
     assert np.array_equal(s1, s0) and np.array_equal(i1, i0)
     assert np.array_equal(A1, A0, equal_nan=True) and np.array_equal(B1, B0, equal_nan=True)
     assert (s1 == 0).sum() > 50
+
+
+def test_slab_and_ring_sweeps_end_bitwise_equal(monkeypatch):
+    """The slab sweep and the per-group ring sweep run the same tile arithmetic in the same order
+    for every row group: a ragged batch of the scan solved with each ends bitwise equal, with the
+    same statuses and sweep counts (FP32 Picard, tangent and FP64 phases all visited)."""
+    batch = inputs.scan_batch(160)
+    res = []
+    for kind in ("slab", "ring"):
+        monkeypatch.setenv("QDSE_SWEEP", kind)
+        res.append(_solve_scan(batch, 1, max_iter=2500))
+    (A1, B1, s1, i1, _, _), (A0, B0, s0, i0, _, _) = res
+    assert np.array_equal(s1, s0) and np.array_equal(i1, i0)
+    assert np.array_equal(A1, A0, equal_nan=True) and np.array_equal(B1, B0, equal_nan=True)
+    assert (s1 == 0).sum() > 40
