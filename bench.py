@@ -61,6 +61,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mu-d", type=float, default=0.55, help="D of --workload mu-solve")
     ap.add_argument("--mu-omega", type=float, default=0.678, help="omega of --workload mu-solve")
+    ap.add_argument("--mu-ray-eta", type=float, default=0.002,
+                    help="eta (GeV^2) of the ray-blended difference quotient in --workload "
+                         "mu-solve; 0 = the exact quotient")
+    ap.add_argument("--mu-rounds", type=int, default=4,
+                    help="continuation rounds of --workload mu-solve (1 = no continuation)")
     return ap.parse_args()
 
 
@@ -991,7 +996,9 @@ def run_mu_reference(args):
 def run_mu_solve(args):
     """One step = solving the finite-mu equation (Ball-Chiu vertex) for 32 chemical potentials on
     the full grid from A = C = 1, B = 0.3: FP32 sweeps to a change of 1e-5, then FP64 sweeps on an
-    FP64 table of the same points to 1e-10, at most 200 sweeps.  Interaction: the paper's Sec. IV
+    FP64 table of the same points to 1e-10, at most 200 sweeps per round; the BC difference
+    quotients ray-blended (eta = --mu-ray-eta); then up to --mu-rounds - 1 continuation rounds in
+    which each unconverged mu restarts from its nearest converged neighbour.  Interaction: the paper's Sec. IV
     values D = 0.55, omega = 0.678 (with the Ball-Chiu vertex at omega = 0.5 the Nambu solution
     ends at a fold near D = 0.75, so at D = 0.93 the iteration has no physical fixed point to
     reach; --mu-d 0.93 --mu-omega 0.5 runs that case).  Both moment tables are built once, outside
@@ -1009,6 +1016,8 @@ def run_mu_solve(args):
     pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
     g32 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, 3, product=True)
     g64 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, 0, product=True)
+    g32.set_ray_quotient(args.mu_ray_eta)
+    g64.set_ray_quotient(args.mu_ray_eta)
     dev = torch.device("cuda", local)
     start = np.zeros((n_mu, 3, g32.n_ext), dtype=np.complex128)
     start[:, 0] = start[:, 1] = 1.0
@@ -1020,8 +1029,9 @@ def run_mu_solve(args):
 
     def step():
         F.copy_(torch.from_numpy(start).to(dev))
-        res["iters"], res["status"] = g32.solve(mu, w.D, w.m, F, tol=1e-10, max_iter=200,
-                                                vertex=0, refine=g64, switch_tol=1e-5)
+        res["iters"], res["status"], res["rounds"] = g32.solve_continued(
+            mu, w.D, w.m, F, max_rounds=args.mu_rounds, tol=1e-10, max_iter=200, vertex=0,
+            refine=g64, switch_tol=1e-5)
 
     for _ in range(args.warmup):
         step()
@@ -1038,7 +1048,7 @@ def run_mu_solve(args):
     if rank != 0:
         return
     line = {"metric": "finite-mu solves per second (BC vertex, 1e-10, FP32 sweeps + FP64 "
-                      "refinement)",
+                      "refinement, continuation in mu)",
             "value": ok * args.steps / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1047,9 +1057,15 @@ def run_mu_solve(args):
                                    "external, |q| 128 x q4 256 internal, 64 angles, "
                                    f"D = {w.D}, omega = {w.omega}, m = 0.005, start A = C = 1, "
                                    "B = 0.3",
-                       "max_sweeps": 200},
-            "converged": ok, "sweeps": [int(x) for x in res["iters"]],
-            "status": [int(x) for x in res["status"]], "clocks": clk.summary()}
+                       "max_sweeps_per_round": 200, "ray_eta": args.mu_ray_eta,
+                       "rounds": args.mu_rounds},
+            "converged": ok, "mu": [round(float(x), 5) for x in mu],
+            "sweeps": [int(x) for x in res["iters"]],
+            "status": [int(x) for x in res["status"]],
+            "round": [int(x) for x in res["rounds"]],
+            "M0": [round(float(x), 5) for x in
+                   (F[:, 2, 0] / F[:, 0, 0]).real.cpu().numpy()],
+            "clocks": clk.summary()}
     print(json.dumps(line))
 
 

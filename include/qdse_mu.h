@@ -82,6 +82,22 @@ int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double*
                   double m, double cf, int vertex, double alpha, double tol, double switch_tol,
                   int max_iter, double* F, int* iters, int* status, void* stream);
 
+/* Continuation in mu: qdse_mu_solve of all n_mu from F's starts, then up to max_rounds - 1 further
+ * rounds in which every chemical potential that has not converged restarts from its nearest
+ * converged neighbour in mu (the lower mu on a tie) -- all restarts of a round run as one batched
+ * solve with max_iter sweeps.  A mu is not retried from the neighbour its previous attempt started
+ * from; the rounds end when no mu has a new neighbour.  Near the chiral transition the Picard map
+ * contracts slowly from a distant start; a converged neighbour puts the start on the same branch.
+ * Arguments as qdse_mu_solve, plus max_rounds >= 1 (1: qdse_mu_solve alone).
+ * F: a converged restart replaces the iterate; an unconverged one keeps the earlier attempt's.
+ * iters: sweeps summed over the rounds; rounds: host int[n_mu] or NULL -- the round of the last
+ * attempt (0 = the first solve).  Allocates one device buffer of n_mu solutions for the rounds.
+ * Returns QDSE_OK unless an argument or CUDA error occurred. */
+int qdse_mu_solve_continued(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double* mu,
+                            double D, double m, double cf, int vertex, double alpha, double tol,
+                            double switch_tol, int max_iter, int max_rounds, double* F,
+                            int* iters, int* status, int* rounds, void* stream);
+
 /* Sizes: the pairs kept in the table and its device bytes (either pointer may be NULL). */
 int qdse_mu_grid_info(const qdse_mu_grid* g, long long* n_pairs, long long* table_bytes);
 
@@ -98,6 +114,17 @@ int qdse_mu_grid_info(const qdse_mu_grid* g, long long* n_pairs, long long* tabl
 int qdse_mu_sweep(qdse_mu_grid* g, int n_mu, const double* mu, double D, double m, double cf,
                   int vertex, const double* F_ext, const double* F_int, double* F_out,
                   void* stream);
+
+/* Reading M8 (not in the paper; off by default): the Ball-Chiu vertex's difference numerators
+ * F_q - F_p take, per (external p, internal q) pair, F_p + beta (F_ray - F_p) in place of F_p, where
+ * F_ray is F interpolated (the rule of qdse_mu_grid_create_product) at the point where q~'s ray
+ * crosses p~'s real 4-radius, (|q|, q_4) sqrt(|p|^2 + p_4^2)/sqrt(|q|^2 + q_4^2), and
+ * beta = exp(-(2 mu |q_4 - p_4|/eta)^2).  As mu -> 0 the numerator then vanishes on the 4-sphere
+ * q^2 = p^2 for any grid function, so the discrete principal-value sum of 1/(q~^2 - p~^2) no longer
+ * couples F_p to itself; where 2 mu |q_4 - p_4| >> eta it is the exact quotient.  Applies to every
+ * later qdse_mu_sweep and qdse_mu_solve on g (BC vertex).  g: a product grid; eta in GeV^2, > 0 turns
+ * it on, 0 off.  Returns QDSE_OK or QDSE_ERR_ARG. */
+int qdse_mu_set_ray_quotient(qdse_mu_grid* g, double eta);
 
 /* Kernel timing.  With profiling on, every qdse_mu_sweep records CUDA events around its two
  * launches (the propagator prep and the sweep) on its stream, without synchronising.

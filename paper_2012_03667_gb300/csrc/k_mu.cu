@@ -251,13 +251,49 @@ __device__ __forceinline__ void load_point<double>(const double* p, qmu::cx<doub
     }
 }
 
-template <class T, int TB, int MINB>
+// Reading M8 (optional): the difference numerators F_q - F_p of the vertex take, per pair,
+// F_p + beta (F_ray - F_p) in place of F_p, with F_ray the interpolation (reading M6) of F where q~'s
+// ray crosses p~'s real 4-radius, (|q|, q_4) sqrt(P^2 + p_4^2)/sqrt(Q^2 + q_4^2), and
+// beta = exp(-(2 mu |q_4 - p_4|/eta)^2).  The ray point depends on the pair only; beta on the
+// pair and mu.  Pairs with beta below kRayMin keep F_p (the difference is below 1e-17 of F).
+struct RayArgs {
+    const double* pax;   // external product grid: |p| axis [n_pr]
+    const double* p4ax;  // p_4 axis [n_p4]
+    int n_pr, n_p4;
+    double eta;          // GeV^2
+};
+constexpr double kRayMin = 1e-17;
+
+// (lower index, upper index, weight of the upper node) of x on an ascending axis: held at the first
+// or last node outside it (the rule of reading M6, as in bracket() on the host).
+__device__ __forceinline__ void ray_bracket(const double* __restrict__ axis, int n, double x,
+                                            int& i0, int& i1, double& wgt) {
+    int lo = -1, hi = n;  // axis[lo] <= x < axis[hi] (lo = -1: below the first node)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (axis[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    if (lo < 0) {
+        i0 = i1 = 0;
+        wgt = 0.0;
+    } else if (lo >= n - 1) {
+        i0 = i1 = n - 1;
+        wgt = 0.0;
+    } else {
+        i0 = lo;
+        i1 = lo + 1;
+        wgt = (x - axis[lo]) / (axis[lo + 1] - axis[lo]);
+    }
+}
+
+template <class T, int TB, int MINB, bool RAY>
 __global__ void __launch_bounds__(kSweepThreads, MINB)
 k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
            const double* __restrict__ q4, const T* __restrict__ table, const T* __restrict__ vec,
            int n_int, int n_4, int n_mu, const int* __restrict__ list, int n_tiles,
            const double* __restrict__ mu, const double* __restrict__ F_ext, int n_ext,
-           double kappa, double m_cur, int bc, double* __restrict__ F_out) {
+           double kappa, double m_cur, int bc, double* __restrict__ F_out, RayArgs ray) {
     // n_mu slots; slot cb is chemical potential list[cb] (cb itself when list is NULL): F_ext,
     // F_out and mu are indexed by the chemical potential, vec by the slot.
     using C = qmu::cx<T>;
@@ -297,15 +333,55 @@ k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
         const double q4f = q4[f];
         const qmu::PairReal<T> pr = qmu::mu_pair_real<T>(v, P, T(qr[r]), T(row.p4 - q4f));
         const T s = T(row.p4 + q4f);
+        // reading M8: the ray point's corners and weights (reading M6), once per pair
+        int e00 = 0, e10 = 0, e01 = 0, e11 = 0, rconj = 0;
+        double ra = 0.0, rb = 0.0;
+        if (RAY) {
+            const double Q = qr[r];
+            const double lam = sqrt(row.P * row.P + row.p4 * row.p4) / sqrt(Q * Q + q4f * q4f);
+            int i0, i1, k0, k1;
+            ray_bracket(ray.pax, ray.n_pr, Q * lam, i0, i1, ra);
+            ray_bracket(ray.p4ax, ray.n_p4, fabs(q4f * lam), k0, k1, rb);
+            e00 = i0 * ray.n_p4 + k0;
+            e10 = i1 * ray.n_p4 + k0;
+            e01 = i0 * ray.n_p4 + k1;
+            e11 = i1 * ray.n_p4 + k1;
+            rconj = q4f * lam < 0.0;
+        }
 #pragma unroll
         for (int t = 0; t < TB; ++t) {
             if (t < nb) {
                 C x[6];  // A, C, B, sv, s4 q~_4, ss at the internal point
                 load_point<T>(vec + ((size_t)(b0 + t) * n_int + j) * 12, x);
                 const T* d = ext[wib][t];
-                qmu::mu_pair_add<T>(pr, s, d[6], bc != 0, C{d[0], d[1]}, C{d[2], d[3]},
-                                    C{d[4], d[5]}, x[0], x[1], x[2], x[3], x[4], x[5], SA[t],
-                                    SC[t], SB[t]);
+                const C Ai{d[0], d[1]}, Ci{d[2], d[3]}, Bi{d[4], d[5]};
+                C Ad = Ai, Cd = Ci, Bd = Bi;
+                if (RAY) {
+                    const double u = 2.0 * (double)d[6] * fabs(row.p4 - q4f) / ray.eta;
+                    const double beta = exp(-u * u);
+                    if (beta > kRayMin) {
+                        const int b = list ? list[b0 + t] : b0 + t;
+                        const double w00 = (1.0 - ra) * (1.0 - rb), w10 = ra * (1.0 - rb);
+                        const double w01 = (1.0 - ra) * rb, w11 = ra * rb;
+                        C* dst[3] = {&Ad, &Cd, &Bd};
+                        const C own[3] = {Ai, Ci, Bi};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const double* Fc = F_ext + ((size_t)b * 3 + c) * 2 * n_ext;
+                            double xr = Fc[2 * e00] * w00 + Fc[2 * e10] * w10;
+                            double xi = Fc[2 * e00 + 1] * w00 + Fc[2 * e10 + 1] * w10;
+                            xr = xr + Fc[2 * e01] * w01;
+                            xi = xi + Fc[2 * e01 + 1] * w01;
+                            xr = xr + Fc[2 * e11] * w11;
+                            xi = xi + Fc[2 * e11 + 1] * w11;
+                            if (rconj) xi = -xi;
+                            *dst[c] = C{own[c].re + T(beta) * (T(xr) - own[c].re),
+                                        own[c].im + T(beta) * (T(xi) - own[c].im)};
+                        }
+                    }
+                }
+                qmu::mu_pair_add_dq<T>(pr, s, d[6], bc != 0, Ai, Ci, Bi, Ad, Cd, Bd, x[0], x[1],
+                                       x[2], x[3], x[4], x[5], SA[t], SC[t], SB[t]);
             }
         }
     }
@@ -364,6 +440,8 @@ struct qdse_mu_grid {
     // external product grid and interpolation onto the internal points (create_product only)
     int n_pr = 0, n_p4 = 0;
     MuInterp* interp = nullptr;
+    double *pax = nullptr, *p4ax = nullptr;  // the product grid's axes (reading M8's ray points)
+    double ray_eta = 0.0;                     // reading M8 on (> 0, GeV^2) or off (0)
     double fingerprint = 0;  // of every node and weight: grids with equal points match
     // solve workspace: the new iterate, per-mu change, non-finite and done flags
     double* G = nullptr;
@@ -385,7 +463,8 @@ const char* qdse_mu_last_error(void) { return g_mu_err.c_str(); }
 void qdse_mu_grid_destroy(qdse_mu_grid* g) {
     if (!g) return;
     for (void* p : {(void*)g->rows, (void*)g->qr, (void*)g->q4, (void*)g->wq, (void*)g->z,
-                    (void*)g->wz, g->table, g->vec, (void*)g->mu, (void*)g->interp, (void*)g->G,
+                    (void*)g->wz, g->table, g->vec, (void*)g->mu, (void*)g->interp,
+                    (void*)g->pax, (void*)g->p4ax, (void*)g->G,
                     (void*)g->change, (void*)g->bad, (void*)g->done, (void*)g->list})
         if (p) cudaFree(p);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
@@ -571,6 +650,8 @@ int mu_launch(qdse_mu_grid* g, int n_mu, const int* list, double D, double m, do
     const int prep_blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     const double kappa = cf * D;
     const int bc = vertex == QDSE_VERTEX_BC;
+    RayArgs ray{g->pax, g->p4ax, g->n_pr, g->n_p4, 0.0};
+    if (g->ray_eta > 0.0 && g->pax && bc) ray.eta = g->ray_eta;
     cudaEvent_t* evt = nullptr;
     if (g->profiling) {
         if ((size_t)(3 * g->n_rec + 3) > g->ev.size()) {
@@ -599,9 +680,15 @@ int mu_launch(qdse_mu_grid* g, int n_mu, const int* list, double D, double m, do
         mark(1);
         const int n_tiles = (n_mu + kTileF32 - 1) / kTileF32;
         const long long warps = (long long)g->n_ext * n_tiles;
-        k_mu_sweep<float, kTileF32, 4><<<(unsigned)((warps + 3) / 4), kSweepThreads, 0, st>>>(
-            g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int, g->n_4,
-            n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+        const unsigned blocks = (unsigned)((warps + 3) / 4);
+        if (ray.eta > 0.0)
+            k_mu_sweep<float, kTileF32, 4, true><<<blocks, kSweepThreads, 0, st>>>(
+                g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int,
+                g->n_4, n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out, ray);
+        else
+            k_mu_sweep<float, kTileF32, 4, false><<<blocks, kSweepThreads, 0, st>>>(
+                g->rows, g->qr, g->q4, (const float*)g->table, (const float*)g->vec, g->n_int,
+                g->n_4, n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out, ray);
     } else {
         if (F_int)
             k_mu_prep<double><<<prep_blocks, 256, 0, st>>>(n_mu, g->mu, g->n_int, g->n_4, g->qr,
@@ -613,9 +700,15 @@ int mu_launch(qdse_mu_grid* g, int n_mu, const int* list, double D, double m, do
         mark(1);
         const int n_tiles = (n_mu + kTileF64 - 1) / kTileF64;
         const long long warps = (long long)g->n_ext * n_tiles;
-        k_mu_sweep<double, kTileF64, 2><<<(unsigned)((warps + 3) / 4), kSweepThreads, 0, st>>>(
-            g->rows, g->qr, g->q4, (const double*)g->table, (const double*)g->vec, g->n_int,
-            g->n_4, n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out);
+        const unsigned blocks = (unsigned)((warps + 3) / 4);
+        if (ray.eta > 0.0)
+            k_mu_sweep<double, kTileF64, 2, true><<<blocks, kSweepThreads, 0, st>>>(
+                g->rows, g->qr, g->q4, (const double*)g->table, (const double*)g->vec, g->n_int,
+                g->n_4, n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out, ray);
+        else
+            k_mu_sweep<double, kTileF64, 2, false><<<blocks, kSweepThreads, 0, st>>>(
+                g->rows, g->qr, g->q4, (const double*)g->table, (const double*)g->vec, g->n_int,
+                g->n_4, n_mu, list, n_tiles, g->mu, F_ext, g->n_ext, kappa, m, bc, F_out, ray);
     }
     mark(2);
     return mu_cuda(cudaGetLastError(), "finite-mu sweep launch");
@@ -709,6 +802,14 @@ int qdse_mu_grid_create_product(int n_pr, const double* p_axis, int n_p4, const 
         rc = mu_cuda(cudaMemcpyAsync(g->interp, ip.data(), sizeof(MuInterp) * ip.size(),
                                      cudaMemcpyHostToDevice, st),
                      "cudaMemcpyAsync(interpolation)");
+    if (rc == QDSE_OK) rc = mu_cuda(cudaMalloc((void**)&g->pax, sizeof(double) * n_pr), "cudaMalloc(axis)");
+    if (rc == QDSE_OK) rc = mu_cuda(cudaMalloc((void**)&g->p4ax, sizeof(double) * n_p4), "cudaMalloc(axis)");
+    if (rc == QDSE_OK)
+        rc = mu_cuda(cudaMemcpyAsync(g->pax, p_axis, sizeof(double) * n_pr, cudaMemcpyHostToDevice,
+                                     st), "cudaMemcpyAsync(axis)");
+    if (rc == QDSE_OK)
+        rc = mu_cuda(cudaMemcpyAsync(g->p4ax, p4_axis, sizeof(double) * n_p4,
+                                     cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(axis)");
     if (rc == QDSE_OK) rc = mu_cuda(cudaStreamSynchronize(st), "qdse_mu_grid_create_product");
     if (rc != QDSE_OK) {
         qdse_mu_grid_destroy(g);
@@ -843,6 +944,102 @@ int qdse_mu_solve(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double*
         if (status)
             status[b] = bad[b] ? QDSE_ERR_NONFINITE : done[b] ? QDSE_OK : QDSE_ERR_NOT_CONVERGED;
     }
+    return QDSE_OK;
+}
+
+int qdse_mu_solve_continued(qdse_mu_grid* g, qdse_mu_grid* refine, int n_mu, const double* mu,
+                            double D, double m, double cf, int vertex, double alpha, double tol,
+                            double switch_tol, int max_iter, int max_rounds, double* F,
+                            int* iters, int* status, int* rounds, void* stream) {
+    const char* who = "qdse_mu_solve_continued";
+    if (max_rounds < 1) return mu_fail(QDSE_ERR_ARG, "%s: max_rounds must be >= 1", who);
+    if (n_mu < 0) return mu_fail(QDSE_ERR_ARG, "%s: n_mu < 0", who);
+    if (n_mu == 0) return QDSE_OK;
+    if (!mu || !F) return mu_fail(QDSE_ERR_ARG, "%s: NULL array", who);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> it_all(n_mu, 0), st_all(n_mu, QDSE_ERR_NOT_CONVERGED), rnd(n_mu, 0);
+    std::vector<int> from(n_mu, -1);  // the converged neighbour the last attempt started from
+    // round 0: every chemical potential from the caller's start
+    int rc = qdse_mu_solve(g, refine, n_mu, mu, D, m, cf, vertex, alpha, tol, switch_tol, max_iter,
+                           F, it_all.data(), st_all.data(), stream);
+    if (rc != QDSE_OK) return rc;
+    const size_t fbytes = sizeof(double) * 6 * (size_t)g->n_ext;  // one mu's A, C, B
+    double* sub = nullptr;
+    for (int r = 1; r < max_rounds; ++r) {
+        // each unconverged mu restarts from its nearest converged neighbour in mu (the lower one on
+        // a tie), unless that is the neighbour its last attempt already started from
+        std::vector<int> pick, nb;
+        for (int b = 0; b < n_mu; ++b) {
+            if (st_all[b] == QDSE_OK) continue;
+            int best = -1;
+            for (int c = 0; c < n_mu; ++c) {
+                if (st_all[c] != QDSE_OK) continue;
+                const double d = std::fabs(mu[c] - mu[b]);
+                const double e = best < 0 ? 0.0 : std::fabs(mu[best] - mu[b]);
+                if (best < 0 || d < e || (d == e && mu[c] < mu[best])) best = c;
+            }
+            if (best >= 0 && best != from[b]) {
+                pick.push_back(b);
+                nb.push_back(best);
+            }
+        }
+        if (pick.empty()) break;
+        const int n_sub = (int)pick.size();
+        if (!sub) {
+            rc = mu_cuda(cudaMalloc((void**)&sub, fbytes * n_mu), "cudaMalloc(continuation)");
+            if (rc != QDSE_OK) return rc;
+        }
+        std::vector<double> mu_sub(n_sub);
+        for (int k = 0; k < n_sub && rc == QDSE_OK; ++k) {
+            mu_sub[k] = mu[pick[k]];
+            rc = mu_cuda(cudaMemcpyAsync(sub + (size_t)k * 6 * g->n_ext,
+                                         F + (size_t)nb[k] * 6 * g->n_ext, fbytes,
+                                         cudaMemcpyDeviceToDevice, st),
+                         "cudaMemcpyAsync(continuation start)");
+        }
+        std::vector<int> it_sub(n_sub), st_sub(n_sub);
+        if (rc == QDSE_OK)
+            rc = qdse_mu_solve(g, refine, n_sub, mu_sub.data(), D, m, cf, vertex, alpha, tol,
+                               switch_tol, max_iter, sub, it_sub.data(), st_sub.data(), stream);
+        for (int k = 0; k < n_sub && rc == QDSE_OK; ++k) {
+            const int b = pick[k];
+            from[b] = nb[k];
+            it_all[b] += it_sub[k];
+            rnd[b] = r;
+            // a converged restart replaces the iterate; a failed one leaves the last attempt's
+            if (st_sub[k] == QDSE_OK || st_all[b] == QDSE_ERR_NONFINITE) {
+                st_all[b] = st_sub[k];
+                rc = mu_cuda(cudaMemcpyAsync(F + (size_t)b * 6 * g->n_ext,
+                                             sub + (size_t)k * 6 * g->n_ext, fbytes,
+                                             cudaMemcpyDeviceToDevice, st),
+                             "cudaMemcpyAsync(continuation result)");
+            }
+        }
+        if (rc != QDSE_OK) break;
+    }
+    if (sub) {
+        const int r2 = mu_cuda(cudaStreamSynchronize(st), who);
+        cudaFree(sub);
+        if (rc == QDSE_OK) rc = r2;
+    }
+    if (rc != QDSE_OK) return rc;
+    for (int b = 0; b < n_mu; ++b) {
+        if (iters) iters[b] = it_all[b];
+        if (status) status[b] = st_all[b];
+        if (rounds) rounds[b] = rnd[b];
+    }
+    return QDSE_OK;
+}
+
+int qdse_mu_set_ray_quotient(qdse_mu_grid* g, double eta) {
+    if (!g) return mu_fail(QDSE_ERR_ARG, "qdse_mu_set_ray_quotient: grid is NULL");
+    if (!g->pax)
+        return mu_fail(QDSE_ERR_ARG,
+                       "qdse_mu_set_ray_quotient: the grid was not made by "
+                       "qdse_mu_grid_create_product");
+    if (!(eta >= 0) || !std::isfinite(eta))
+        return mu_fail(QDSE_ERR_ARG, "qdse_mu_set_ray_quotient: eta must be finite and >= 0");
+    g->ray_eta = eta;
     return QDSE_OK;
 }
 

@@ -144,10 +144,13 @@ QMU_HD void mu_propagator(T Q, cx<T> qt, cx<T> A, cx<T> C, cx<T> B, cx<T>* sv, c
 // Adds one pair's contribution at one mu: to SA (the A projection), SCp (the C projection times
 // p~_4) and SB (the B projection).  s = p_4 + q_4 is real; p~_4 + q~_4 = s + 2 i mu.
 // bc = false gives the bare vertex gamma_nu (rainbow truncation).
+// (Adi, Cdi, Bdi): the values subtracted in the vertex's difference numerators F_q - F_p, which
+// are the external point's own (Ai, Ci, Bi) except under reading M8 (k_mu.cu).
 template <class T>
-QMU_HD void mu_pair_add(const PairReal<T>& r, T s, T mu, bool bc, cx<T> Ai, cx<T> Ci, cx<T> Bi,
-                        cx<T> Aj, cx<T> Cj, cx<T> Bj, cx<T> sv, cx<T> s4q, cx<T> ss, cx<T>& SA,
-                        cx<T>& SCp, cx<T>& SB) {
+QMU_HD void mu_pair_add_dq(const PairReal<T>& r, T s, T mu, bool bc, cx<T> Ai, cx<T> Ci,
+                           cx<T> Bi, cx<T> Adi, cx<T> Cdi, cx<T> Bdi, cx<T> Aj, cx<T> Cj,
+                           cx<T> Bj, cx<T> sv, cx<T> s4q, cx<T> ss, cx<T>& SA, cx<T>& SCp,
+                           cx<T>& SB) {
     const T h = r.h;
     if (!bc) {
         // Sigma = 1, no t-terms
@@ -158,7 +161,7 @@ QMU_HD void mu_pair_add(const PairReal<T>& r, T s, T mu, bool bc, cx<T> Ai, cx<T
     }
     const cx<T> spl = {s, T(2) * mu};  // p~_4 + q~_4
     const cx<T> aA = (Aj + Ai) * T(0.5), aC = (Cj + Ci) * T(0.5), aAC = aA + aC;
-    const cx<T> eA = Aj - Ai, eC = Cj - Ci, eB = Bj - Bi;
+    const cx<T> eA = Aj - Adi, eC = Cj - Cdi, eB = Bj - Bdi;
     const cx<T> w = {r.pq2 + h * s, T(2) * mu * h};  // p~^2 - q~^2
     const cx<T> iw = cinv(w);
     const cx<T> dA = -(eA * iw), dC = -(eC * iw), dB = -(eB * iw);  // (F_q - F_p)/(q~^2 - p~^2)
@@ -179,6 +182,13 @@ QMU_HD void mu_pair_add(const PairReal<T>& r, T s, T mu, bool bc, cx<T> Ai, cx<T
     const cx<T> tC_sv = hs * ((dC + dA) * r.b7 + eC * r.v8) - eA * (T(0.5) * h * r.b9) -
                         aAC * (h * r.v8);
     SCp = SCp + ss * T1 + s4q * (U - V) + sv * tC_sv;
+}
+
+template <class T>
+QMU_HD void mu_pair_add(const PairReal<T>& r, T s, T mu, bool bc, cx<T> Ai, cx<T> Ci, cx<T> Bi,
+                        cx<T> Aj, cx<T> Cj, cx<T> Bj, cx<T> sv, cx<T> s4q, cx<T> ss, cx<T>& SA,
+                        cx<T>& SCp, cx<T>& SB) {
+    mu_pair_add_dq<T>(r, s, mu, bc, Ai, Ci, Bi, Ai, Ci, Bi, Aj, Cj, Bj, sv, s4q, ss, SA, SCp, SB);
 }
 
 }  // namespace qmu

@@ -16,7 +16,8 @@ from . import qdse as Q
 
 EXPORTS = ("qdse_mu_grid_create", "qdse_mu_grid_create_product", "qdse_mu_solve",
            "qdse_mu_grid_info", "qdse_mu_sweep", "qdse_mu_set_profiling", "qdse_mu_profile",
-           "qdse_mu_grid_destroy", "qdse_mu_last_error")
+           "qdse_mu_set_ray_quotient", "qdse_mu_solve_continued", "qdse_mu_grid_destroy",
+           "qdse_mu_last_error")
 
 _lib = None
 
@@ -34,9 +35,12 @@ def load_library() -> ctypes.CDLL:
         "qdse_mu_grid_create_product": (ip, [ip, vp, ip, vp, ip, vp, ip, vp, vp, ip, vp, vp, dp,
                                              ip, vp, P(vp)]),
         "qdse_mu_solve": (ip, [vp, vp, ip, vp, dp, dp, dp, ip, dp, dp, dp, ip, vp, vp, vp, vp]),
+        "qdse_mu_solve_continued": (ip, [vp, vp, ip, vp, dp, dp, dp, ip, dp, dp, dp, ip, ip, vp,
+                                         vp, vp, vp, vp]),
         "qdse_mu_grid_info": (ip, [vp, llp, llp]),
         "qdse_mu_sweep": (ip, [vp, ip, vp, dp, dp, dp, ip, vp, vp, vp, vp]),
         "qdse_mu_set_profiling": (ip, [vp, ip]),
+        "qdse_mu_set_ray_quotient": (ip, [vp, dp]),
         "qdse_mu_profile": (ip, [vp, P(dp), P(ctypes.c_longlong)]),
         "qdse_mu_grid_destroy": (None, [vp]),
         "qdse_mu_last_error": (ctypes.c_char_p, []),
@@ -103,6 +107,27 @@ class MuGrid:
                                            status.ctypes.data, Q._current_stream()))
         return iters, status
 
+    def solve_continued(self, mu: Sequence[float], D: float, m: float, F, max_rounds: int = 4,
+                        alpha: float = 1.0, tol: float = 1e-10, max_iter: int = 500,
+                        vertex: int = Q.QDSE_VERTEX_BC, cf: float = 4.0 / 3.0,
+                        refine: "MuGrid" = None, switch_tol: float = 1e-5):
+        """qdse_mu_solve_continued: as solve(), then rounds in which each unconverged mu restarts
+        from its nearest converged neighbour.  Returns (iters, status, rounds)."""
+        import torch
+        mu = _host(mu)
+        n_mu = len(mu)
+        assert F.is_cuda and F.dtype == torch.complex128 and F.is_contiguous()
+        assert tuple(F.shape) == (n_mu, 3, self.n_ext)
+        iters = np.zeros(n_mu, dtype=np.int32)
+        status = np.zeros(n_mu, dtype=np.int32)
+        rounds = np.zeros(n_mu, dtype=np.int32)
+        self._raise(self.lib.qdse_mu_solve_continued(
+            self.ptr, refine.ptr if refine is not None else None, n_mu, mu.ctypes.data, float(D),
+            float(m), float(cf), vertex, float(alpha), float(tol), float(switch_tol),
+            int(max_iter), int(max_rounds), F.data_ptr(), iters.ctypes.data, status.ctypes.data,
+            rounds.ctypes.data, Q._current_stream()))
+        return iters, status, rounds
+
     def info(self) -> dict:
         n, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._raise(self.lib.qdse_mu_grid_info(self.ptr, ctypes.byref(n), ctypes.byref(b)))
@@ -121,6 +146,11 @@ class MuGrid:
         self._raise(self.lib.qdse_mu_sweep(self.ptr, n_mu, mu.ctypes.data, float(D), float(m),
                                            float(cf), vertex, F_ext.data_ptr(), F_int.data_ptr(),
                                            F_out.data_ptr(), Q._current_stream()))
+
+    def set_ray_quotient(self, eta: float):
+        """Reading M8 of the BC vertex's difference quotients (include/qdse_mu.h): eta in GeV^2,
+        0 turns it off.  Product grids only."""
+        self._raise(self.lib.qdse_mu_set_ray_quotient(self.ptr, float(eta)))
 
     def set_profiling(self, on: bool):
         self._raise(self.lib.qdse_mu_set_profiling(self.ptr, int(bool(on))))

@@ -223,3 +223,108 @@ def test_mu_solve_reports_non_convergence_and_non_finite_values(QM):
     flat = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, *gpu_rule(w), w.omega, 0)
     with pytest.raises(QM.Q.QdseError):
         flat.solve([0.1], w.D, w.m, F)
+
+
+def _ray_setup(QM, precision):
+    """The paper's interaction (D = 0.55, omega = 0.678) on the 12 x 8 product grid with 16 cosine
+    nodes: the case where the exact quotient runs away at mu = 0 (reading M8's oracle pin)."""
+    w = I.mu_workload(n_r=12, n_4=8, n_z=16, n_mu=1, D=0.55, omega=0.678)
+    pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
+    g = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, precision, product=True)
+    g.set_ray_quotient(0.002)
+    start = np.array([np.ones(len(w.p_abs))] * 3, dtype=np.complex128)
+    return w, pa, p4a, g, start
+
+
+def test_mu_ray_quotient_iterates_match_the_oracle(QM):
+    """Reading M8 on the GPU (eta = 0.002 GeV^2): exactly 12 sweeps of four chemical potentials,
+    from mu = 0 (beta = 1 on every pair) through mu = 0.2 (the blend gone from most pairs), every
+    element against the oracle's solve(ray_eta=0.002) to 1e-11 of max |F - x0|."""
+    w, pa, p4a, g, start = _ray_setup(QM, 0)
+    mu_list = [0.0, 0.01, 0.05, 0.2]
+    F = torch.from_numpy(np.stack([start] * len(mu_list))).cuda()
+    iters, status = g.solve(mu_list, 0.55, w.m, F, tol=0.0, max_iter=12, vertex=0)
+    assert list(iters) == [12] * len(mu_list)
+    got = F.cpu().numpy()
+    x0 = np.array([1.0, 1.0, w.m])[:, None]
+    for b, mu in enumerate(mu_list):
+        ref, _, _ = OM.solve(pa, p4a, w.q_abs, w.q4, *oracle_rule(w), 0.55, 0.678, w.m, mu,
+                             start, tol=0.0, max_iter=12, ray_eta=0.002)
+        err = (np.abs(got[b] - ref).max(axis=1) / np.abs(ref - x0).max(axis=1)).max()
+        assert err < 1e-11, (mu, err)
+
+
+def test_mu_ray_quotient_converges_at_mu_zero_like_the_oracle(QM):
+    """With reading M8 the mu = 0 solve converges (the exact quotient runs away there): the GPU's
+    FP64 fixed point equals the oracle's to 1e-10 with the same sweep count within one, and the
+    mixed solve (FP32 sweeps to 1e-5, then FP64) reaches the same point to 1e-9."""
+    w, pa, p4a, g, start = _ray_setup(QM, 0)
+    F = torch.from_numpy(np.stack([start])).cuda()
+    iters, status = g.solve([0.0], 0.55, w.m, F, tol=1e-10, max_iter=80, vertex=0)
+    ref, it, ok = OM.solve(pa, p4a, w.q_abs, w.q4, *oracle_rule(w), 0.55, 0.678, w.m, 0.0, start,
+                           tol=1e-10, max_iter=80, ray_eta=0.002)
+    assert ok and list(status) == [0] and abs(int(iters[0]) - it) <= 1
+    got = F.cpu().numpy()[0]
+    x0 = np.array([1.0, 1.0, w.m])[:, None]
+    assert (np.abs(got - ref).max(axis=1) / np.abs(ref - x0).max(axis=1)).max() < 1e-10
+    _, _, _, g32, _ = _ray_setup(QM, 3)
+    Fm = torch.from_numpy(np.stack([start])).cuda()
+    itm, stm = g32.solve([0.0], 0.55, w.m, Fm, tol=1e-10, max_iter=200, vertex=0, refine=g,
+                         switch_tol=1e-5)
+    assert list(stm) == [0]
+    gm = Fm.cpu().numpy()[0]
+    assert (np.abs(gm - ref).max(axis=1) / np.abs(ref - x0).max(axis=1)).max() < 1e-9
+
+
+def test_mu_ray_quotient_off_is_the_plain_sweep_and_bad_settings_are_refused(QM):
+    """eta = 0 restores the exact quotient bitwise; a negative or non-finite eta and a grid made
+    without the product form are refused."""
+    w, pa, p4a, g, start = _ray_setup(QM, 0)
+    plain = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, 0, product=True)
+    g.set_ray_quotient(0.0)
+    F1 = torch.from_numpy(np.stack([start] * 2)).cuda()
+    F2 = F1.clone()
+    g.solve([0.1, 0.3], 0.55, w.m, F1, tol=0.0, max_iter=5, vertex=0)
+    plain.solve([0.1, 0.3], 0.55, w.m, F2, tol=0.0, max_iter=5, vertex=0)
+    assert torch.equal(F1, F2)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(QM.Q.QdseError):
+            g.set_ray_quotient(bad)
+    flat = QM.MuGrid(w.p_abs, w.p4, w.q_abs, w.q4, *gpu_rule(w), w.omega, 0)
+    with pytest.raises(QM.Q.QdseError):
+        flat.set_ray_quotient(0.002)
+
+
+def test_mu_continuation_restarts_failed_mu_from_converged_neighbours(QM):
+    """qdse_mu_solve_continued (rainbow vertex, FP64, 12 x 8 grid): the starts of mu = 0.1 and 0.2
+    hold NaN, so the first solve ends QDSE_ERR_NONFINITE there.  The next round restarts 0.1 from
+    0 and 0.2 from 0.3 (the nearest converged mu) and both converge, to the oracle's fixed point
+    from the plain start to 1e-10; the two that converged at once are bitwise the plain solve's.
+    max_rounds = 1 is qdse_mu_solve itself."""
+    w, pa, p4a, g, start = _solve_setup(QM, 0)
+    mu_list = [0.0, 0.1, 0.2, 0.3]
+    bad = start.copy()
+    bad[1, 5] = np.nan
+    starts = np.stack([start, bad, bad, start])
+    F = torch.from_numpy(starts).cuda()
+    iters, status, rounds = g.solve_continued(mu_list, w.D, w.m, F, max_rounds=3, tol=1e-12,
+                                              max_iter=200, vertex=1)
+    assert list(status) == [0, 0, 0, 0] and list(rounds) == [0, 1, 1, 0]
+    F1 = torch.from_numpy(starts).cuda()
+    it1, st1 = g.solve(mu_list, w.D, w.m, F1, tol=1e-12, max_iter=200, vertex=1)
+    assert list(st1) == [0, QM.Q.QDSE_ERR_NONFINITE, QM.Q.QDSE_ERR_NONFINITE, 0]
+    assert torch.equal(F[0], F1[0]) and torch.equal(F[3], F1[3])
+    assert iters[0] == it1[0] and iters[1] > it1[1]
+    got = F.cpu().numpy()
+    x0 = np.array([1.0, 1.0, w.m])[:, None]
+    for b in (1, 2):
+        ref, _, ok = _oracle_solve(w, pa, p4a, w.D, mu_list[b], start, tol=1e-12, max_iter=200,
+                                   vertex=OM.RL)
+        assert ok
+        err = (np.abs(got[b] - ref).max(axis=1) / np.abs(ref - x0).max(axis=1)).max()
+        assert err < 1e-10, (mu_list[b], err)
+    F2 = torch.from_numpy(starts).cuda()
+    it2, st2, r2 = g.solve_continued(mu_list, w.D, w.m, F2, max_rounds=1, tol=1e-12,
+                                     max_iter=200, vertex=1)
+    assert list(st2) == list(st1) and list(it2) == list(it1) and not r2.any()
+    assert torch.equal(F2[0], F1[0]) and torch.equal(F2[3], F1[3])
