@@ -37,13 +37,15 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scan",
                     choices=["scan", "large", "small", "adjoint", "mu", "mu-small", "mu-solve",
-                             "table1"],
+                             "table1", "mscan"],
                     help="scan: 4096-instance mass/interaction scan (default); large/small: one "
                          "N = 512 / N = 64 instance; adjoint: 1024 scan instances at N_q = 256, "
                          "N_theta = 64, forward solve + condensate gradient by the adjoint; mu: "
                          "finite-mu batched sweep, 256 mu on the full grid; mu-small: a small "
                          "case of it; mu-solve: finite-mu solve of 32 mu; table1: Sec. IV "
-                         "Table 1 (with --impl reference, the four CPU algorithms)")
+                         "Table 1 (with --impl reference, the four CPU algorithms); mscan: "
+                         "1024-instance current-mass scan on one shared kernel matrix, solved "
+                         "with the tensor-core Picard sweep and with the per-instance sweep")
     ap.add_argument("--n-inst", type=int, default=4096)
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--fp64", default="sample", choices=["sample", "full", "none"],
@@ -64,6 +66,8 @@ def parse():
     ap.add_argument("--mu-ray-eta", type=float, default=0.002,
                     help="eta (GeV^2) of the ray-blended difference quotient in --workload "
                          "mu-solve; 0 = the exact quotient")
+    ap.add_argument("--mu-max-sweeps", type=int, default=1000,
+                    help="sweep cap per round of --workload mu-solve")
     ap.add_argument("--mu-rounds", type=int, default=4,
                     help="continuation rounds of --workload mu-solve (1 = no continuation)")
     return ap.parse_args()
@@ -748,6 +752,136 @@ def run_table1(args):
 
 
 # ------------------------------------------------------------------------------------------------
+def run_mscan(args):
+    """A current-mass scan sharing one kernel matrix (N_q = 512, N_theta = 128, D = 0.55,
+    omega = 0.678, m ~ U[0, 0.2]): one step = the mixed solve of every instance to 1e-10 from
+    A = 1, B = 0.3, kernel precompute included.  Timed twice: with the tensor-core Picard sweep
+    (shared_kernels = 1, the line's value) and with the per-instance ring sweep (the same solve,
+    reported beside it).  The tensor-core sweep's roofline: its TF32 tensor FLOPs per launch
+    (3 products x 2 N^2 x 11 functions x the batch, the far field being a dense product) over its
+    CUDA-event time in a separate profiled run, against the measured bf16 peak x 0.5 (the TF32
+    share of the nominal dense rates).  Single GPU; other ranks idle."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_03667_gb300 import inputs
+    from paper_2012_03667_gb300 import qdse as Q
+    n_inst = args.n_inst if args.n_inst != 4096 else 1024
+    batch = inputs.mscan_batch(n_inst, seed=inputs.SCAN_SEED + rank)
+    b0 = batch[0]
+    g = Q.Grid(b0.n_p, b0.n_theta, b0.s_min, b0.s_max)
+    prm = [[b.D, b.omega, b.m, 0.0] for b in batch]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    arms = {}
+    for shared in (1, 0):
+        ctx = Q.Context(g, n_inst, precision=Q.QDSE_MIXED, tol=1e-10, max_iter=args.max_iter,
+                        shared_kernels=shared)
+        A = torch.ones(ctx.n_total, dtype=torch.float64, device=dev)
+        B = torch.full((ctx.n_total,), 0.3, dtype=torch.float64, device=dev)
+        st = torch.zeros(n_inst, dtype=torch.int32, device=dev)
+        it = torch.zeros(n_inst, dtype=torch.int32, device=dev)
+
+        def step():
+            A.fill_(1.0)
+            B.fill_(0.3)
+            ctx.qdse_solve(prm, A, B, it, st)
+
+        for _ in range(args.warmup):
+            step()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                step()
+                launches += ctx.qdse_last_stats()["kernel_launches"]
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        stats = ctx.qdse_last_stats()
+        sol = (A.cpu().numpy(), B.cpu().numpy())
+        stv = st.cpu().numpy()
+        ctx.qdse_set_profiling(True)
+        step()
+        prof = ctx.qdse_profile()
+        ctx.qdse_set_profiling(False)
+        arms[shared] = {"ms": ms, "ok": int((stv == 0).sum()), "status": stv, "sol": sol,
+                        "mean_sweeps": float(it.float().mean().item()), "stats": stats,
+                        "prof": prof, "launches": launches, "clocks": clk.summary()}
+        ctx.close()
+    if rank != 0:
+        return
+    tc, ring = arms[1], arms[0]
+    same = bool(np.array_equal(tc["status"], ring["status"]))
+    ok_both = (tc["status"] == 0) & (ring["status"] == 0)
+    x_err = 0.0
+    if ok_both.any():
+        a1, b1 = tc["sol"]
+        a0, b0_ = ring["sol"]
+        x_err = float(max(np.abs(a1 - a0).max() / np.abs(a0).max(),
+                          np.abs(b1 - b0_).max() / np.abs(b0_).max()))
+    # the tensor-core sweep launches (prep + product) are the profiled "sweep" events beyond the
+    # ring's; its time per launch is taken from a qdse_iterate run in which every instance sweeps
+    peak_bf16 = 1920.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak_bf16 = float(json.load(f).get("bf16_tflops", peak_bf16))
+        kind = "measured"
+    except Exception:
+        kind = "fallback"
+    ctx = Q.Context(g, n_inst, precision=Q.QDSE_MIXED, tol=1e-10, shared_kernels=1)
+    A = torch.ones(ctx.n_total, dtype=torch.float64, device=dev)
+    B = torch.full((ctx.n_total,), 0.3, dtype=torch.float64, device=dev)
+    ctx.qdse_iterate(prm, A, B, 3)
+    ctx.qdse_set_profiling(True)
+    ctx.qdse_iterate(prm, A, B, 10)
+    pr = ctx.qdse_profile()
+    ctx.qdse_set_profiling(False)
+    ctx.close()
+    # sweep events: per tick one for the tensor-core launches and one for the (empty) ring launch
+    tc_ms = pr["sweep"]["ms"] / 10
+    flops = 3 * 2.0 * b0.n_p * b0.n_p * 11 * n_inst
+    achieved = flops / (tc_ms / 1e3) / 1e12
+    peak = 0.5 * peak_bf16
+    line = {"metric": "shared-kernel mass-scan solves per second (BC vertex, 1e-10, tensor-core "
+                      "FP32 Picard sweep + FP64 refinement)",
+            "value": tc["ok"] * args.steps / (tc["ms"] / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tc["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3+f32+f64", "data": "synthetic",
+            "config": {"workload": f"current-mass scan, {n_inst} instances sharing one kernel "
+                                   f"matrix: N_q = {b0.n_p}, N_theta = {b0.n_theta}, "
+                                   f"D = {b0.D}, omega = {b0.omega}, m ~ U[0, 0.2] GeV",
+                       "tol": 1e-10, "max_sweeps": args.max_iter,
+                       "l2": "operands re-read from L2 by every CTA; the 3 MB kernel planes "
+                             "and the batch's column functions stay L2-resident"},
+            "converged": tc["ok"], "mean_sweeps": tc["mean_sweeps"],
+            "gpu_launches": tc["launches"],
+            "per_instance_sweep": {"value": ring["ok"] * args.steps / (ring["ms"] / 1e3),
+                                   "ms_per_step": ring["ms"] / args.steps,
+                                   "converged": ring["ok"], "mean_sweeps": ring["mean_sweeps"],
+                                   "device_ms": {k: round(v["ms"], 3)
+                                                 for k, v in ring["prof"].items()}},
+            "tensor_over_per_instance": ring["ms"] / tc["ms"],
+            "same_statuses": same, "max_rel_diff_of_solutions": x_err,
+            "device_ms": {k: round(v["ms"], 3) for k, v in tc["prof"].items()},
+            "roofline": {"kernel": "k_tc_prep + k_tc_sweep (3xTF32 far field + FP32 near band)",
+                         "bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": f"{kind} bf16 burst x 0.5 (TF32)",
+                         "ms_per_launch": tc_ms, "flops_per_launch": flops,
+                         "timed_in": "qdse_iterate, every instance in the Picard phase, CUDA "
+                                     "events around every launch (includes the empty "
+                                     "per-instance sweep launch of each tick)"},
+            "clocks": tc["clocks"]}
+    print(json.dumps(line))
+
+
 def run_adjoint(args):
     """Gradients of the chiral condensate -<qq> of every instance with respect to (m, D, w, mu):
     one step = forward mixed-precision solve to 1e-12 (kernel precompute included) + condensate
@@ -996,7 +1130,7 @@ def run_mu_reference(args):
 def run_mu_solve(args):
     """One step = solving the finite-mu equation (Ball-Chiu vertex) for 32 chemical potentials on
     the full grid from A = C = 1, B = 0.3: FP32 sweeps to a change of 1e-5, then FP64 sweeps on an
-    FP64 table of the same points to 1e-10, at most 200 sweeps per round; the BC difference
+    FP64 table of the same points to 1e-10, at most --mu-max-sweeps per round; the BC difference
     quotients ray-blended (eta = --mu-ray-eta); then up to --mu-rounds - 1 continuation rounds in
     which each unconverged mu restarts from its nearest converged neighbour.  Interaction: the paper's Sec. IV
     values D = 0.55, omega = 0.678 (with the Ball-Chiu vertex at omega = 0.5 the Nambu solution
@@ -1030,7 +1164,8 @@ def run_mu_solve(args):
     def step():
         F.copy_(torch.from_numpy(start).to(dev))
         res["iters"], res["status"], res["rounds"] = g32.solve_continued(
-            mu, w.D, w.m, F, max_rounds=args.mu_rounds, tol=1e-10, max_iter=200, vertex=0,
+            mu, w.D, w.m, F, max_rounds=args.mu_rounds, tol=1e-10, max_iter=args.mu_max_sweeps,
+            vertex=0,
             refine=g64, switch_tol=1e-5)
 
     for _ in range(args.warmup):
@@ -1057,7 +1192,7 @@ def run_mu_solve(args):
                                    "external, |q| 128 x q4 256 internal, 64 angles, "
                                    f"D = {w.D}, omega = {w.omega}, m = 0.005, start A = C = 1, "
                                    "B = 0.3",
-                       "max_sweeps_per_round": 200, "ray_eta": args.mu_ray_eta,
+                       "max_sweeps_per_round": args.mu_max_sweeps, "ray_eta": args.mu_ray_eta,
                        "rounds": args.mu_rounds},
             "converged": ok, "mu": [round(float(x), 5) for x in mu],
             "sweeps": [int(x) for x in res["iters"]],
@@ -1079,6 +1214,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "adjoint":
         run_adjoint(a)
+    elif a.workload == "mscan":
+        run_mscan(a)
     elif a.workload == "mu-solve":
         run_mu_solve(a)
     elif a.workload.startswith("mu"):

@@ -111,12 +111,23 @@ typedef struct {
                           QDSE_ERR_NOT_CONVERGED at once.  It never changes which instances
                           converge, nor their results (up to a hash collision, chance below
                           1e-10 per batch); A and B of a stopped instance hold its last iterate */
+    int shared_kernels; /* 1: every instance shares the grid and omega (a scan of m or D; D and m
+                          may differ), so all share one kernel matrix: the FP32 Picard sweeps of
+                          the batch then run as one product on the tensor cores (tcgen05, TF32
+                          operands, FP32 accumulation) over the far field |i - j| > 32, with the
+                          near band summed in the difference form in FP32 (not in the paper;
+                          the refinement phases are unchanged).  The kernel matrices are
+                          precomputed and stored once for the whole batch.  Needs qdse_create
+                          (one grid),
+                          COLLOCATED, the BC vertex and QDSE_MIXED or QDSE_FP32; a call whose
+                          instances differ in omega fails with QDSE_ERR_ARG.  0: per-instance
+                          sweeps                                                                */
     void* stream;      /* cudaStream_t for all device work; NULL = legacy default stream         */
 } qdse_options;
 
 /* Defaults: QDSE_MIXED, BC vertex, cf = 4/3, tol = 1e-10, alpha = 1, max_iter = 20000,
- * no time limit, kernels rebuilt on every call, no no-progress stop, cycle stop on, default
- * stream. */
+ * no time limit, kernels rebuilt on every call, no no-progress stop, cycle stop on, per-instance
+ * sweeps, default stream. */
 qdse_options qdse_default_options(void);
 
 /* Create a context for n_inst instances that share one grid (*g).  Builds the radial and angular
@@ -127,6 +138,9 @@ qdse_options qdse_default_options(void);
  * a launch that advances each instance (relaxed step, convergence test, next node vectors).
  * Environment variables read here select alternatives that compute the same quantities:
  * QDSE_SWEEP=groups the register-only sweep kernel (the same sums in another order),
+ * QDSE_SWEEP=slab the ring sweep with its bookkeeping per slab of 8 row groups (bitwise the same
+ * results), QDSE_RING=8x3 or 6x4 ring shapes with fewer warps and more tile slots each (bitwise
+ * the same results),
  * QDSE_FUSED_UPDATE=1 the ring sweep advancing each instance itself as soon as its last row group
  * is swept (one launch per tick, bitwise the same results, slower on GB300),
  * QDSE_PRECOMPUTE=fp64 the kernel matrices in FP64 arithmetic instead of double-float arithmetic on

@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqdse.so")
 SOURCES = ["api.cu", "k_sweep.cu", "k_precompute.cu", "k_adjoint.cu", "grid.cpp", "noalloc.cu",
-           "k_mu.cu"]
-HEADERS = ["qdse_internal.h", "mu_pair.cuh", "f2.cuh", os.path.join("..", "..", "include", "qdse.h"),
+           "k_mu.cu", "k_tc.cu"]
+HEADERS = ["qdse_internal.h", "mu_pair.cuh", "f2.cuh", "tc_sm100.cuh", os.path.join("..", "..", "include", "qdse.h"),
            os.path.join("..", "..", "include", "qdse_mu.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -79,6 +79,11 @@ qdse_status check_options(const qdse_options* o, std::string& why) {
     if (std::isnan(o->time_limit)) { why = "options.time_limit is NaN"; return QDSE_ERR_ARG; }
     if (o->stall_window < 0) { why = "options.stall_window must be >= 0"; return QDSE_ERR_ARG; }
     if (o->stop_cycles != 0 && o->stop_cycles != 1) { why = "options.stop_cycles must be 0 or 1"; return QDSE_ERR_ARG; }
+    if (o->shared_kernels != 0 && o->shared_kernels != 1) { why = "options.shared_kernels must be 0 or 1"; return QDSE_ERR_ARG; }
+    if (o->shared_kernels) {
+        if (o->vertex != QDSE_VERTEX_BC) { why = "options.shared_kernels needs the BC vertex"; return QDSE_ERR_ARG; }
+        if (o->precision != QDSE_MIXED && o->precision != QDSE_FP32) { why = "options.shared_kernels needs QDSE_MIXED or QDSE_FP32"; return QDSE_ERR_ARG; }
+    }
     return QDSE_OK;
 }
 
@@ -121,6 +126,7 @@ void free_ctx(qdse_ctx* c) {
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->h_count) cudaFreeHost(c->h_count);
     if (c->h_inst_pinned) cudaFreeHost(c->h_inst_pinned);
+    tc_free(c);
     delete c;
 }
 
@@ -139,6 +145,9 @@ qdse_status set_params(qdse_ctx* c, const qdse_params* p, bool& rebuild) {
             return fail(c, QDSE_ERR_UNSUPPORTED, "params[" + std::to_string(b) +
                                                      "]: the vacuum solver needs mu = 0");
         if (c->k_omega[b] != q.omega) rebuild = true;
+        if (c->tc && q.omega != p[0].omega)
+            return fail(c, QDSE_ERR_ARG, "params[" + std::to_string(b) +
+                                             "]: shared kernels need one omega for every instance");
     }
     for (int b = 0; b < c->n_inst; ++b) {
         const HostInst& h = c->hinst[b];
@@ -168,6 +177,7 @@ qdse_status ensure_kernels(qdse_ctx* c, const qdse_params* p, bool rebuild) {
     if (!rebuild) return QDSE_OK;
     QCHECK(c, launch_precompute(c, false), "precompute kernels");
     QCHECK(c, launch_group_bands(c), "group bands");
+    if (c->tc) QCHECK(c, launch_tc_extract(c), "tensor-core kernel planes");
     for (int b = 0; b < c->n_inst; ++b) c->k_omega[b] = p[b].omega;
     c->k_valid_for = 1;
     c->kw_valid = 0;
@@ -191,6 +201,7 @@ Ctl make_ctl(const qdse_ctx* c) {
     t.stall_copies = c->stall_copies;
     t.stall_window = c->opt.stall_window;
     t.stop_cycles = c->opt.stop_cycles;
+    t.tc_picard = c->tc;
     return t;
 }
 
@@ -212,6 +223,12 @@ cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
     cudaError_t e = cudaSuccess;
     if (last) e = cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
+    if (!otf && c->tc) {
+        // FP32 Picard rows of the whole batch on the tensor cores; the sweep below takes the
+        // row groups of every other phase
+        e = launch_tc_sweep(c);
+        if (e != cudaSuccess) return e;
+    }
     if (otf) {
         e = launch_sweep_otf(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, 1);
     } else if (c->sweep_kind == 2) {
@@ -357,6 +374,10 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     for (int b = 0; b < (ragged ? n_inst : 1); ++b)
         if (check_grid(g[b], why) != QDSE_OK)
             return fail(nullptr, QDSE_ERR_ARG, "instance " + std::to_string(b) + ": " + why);
+    if (o->shared_kernels && (ragged || g[0].grid_mode != QDSE_COLLOCATED))
+        return fail(nullptr, QDSE_ERR_ARG,
+                    "options.shared_kernels needs one COLLOCATED grid for every instance "
+                    "(qdse_create)");
 
     qdse_ctx* c = new (std::nothrow) qdse_ctx();
     if (!c) return fail(nullptr, QDSE_ERR_OOM, "host allocation");
@@ -374,11 +395,12 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         h.x_off = x;
         h.ld = (h.g.n_p + 3) & ~3;
         h.v_off = v;
-        h.k_off = k;
+        // shared kernels: every instance reads the one kernel block of instance 0
+        h.k_off = o->shared_kernels ? 0 : k;
         x += h.g.n_p;
         v += h.ld;
         ng += (h.g.n_p + kRows - 1) / kRows;
-        k += 3LL * h.g.n_p * h.ld;
+        if (!o->shared_kernels || b == 0) k += 3LL * h.g.n_p * h.ld;
         if (!t_of.count(h.g.n_theta)) {
             t_of[h.g.n_theta] = t;
             t += h.g.n_theta;
@@ -401,7 +423,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     std::vector<int> sta(N), row_inst(N);
     // precompute tiles: collocated grids only the upper triangle (J >= I), staggered all
     std::vector<int4> tiles;
-    for (int b = 0; b < n_inst; ++b) {
+    for (int b = 0; b < (o->shared_kernels ? 1 : n_inst); ++b) {
         const HostInst& h = c->hinst[b];
         const int T = (h.g.n_p + kTile - 1) / kTile;
         for (int I = 0; I < T; ++I)
@@ -619,6 +641,10 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         // QDSE_FUSED_UPDATE=1: the ring sweep advances each instance itself (one launch per tick;
         // the same arithmetic in the same order as the separate update launch, but measured
         // slower: the update's dependent loads by one warp, among the sweep's 12 warps per SM)
+        // QDSE_RING=8x3 / 6x4: fewer warps per block, each with more tile slots in flight and its
+        // copying side further ahead (the default is 12 warps x 2 slots)
+        const char* rs = std::getenv("QDSE_RING");
+        c->ring_shape = (rs && std::string(rs) == "8x3") ? 1 : (rs && std::string(rs) == "6x4") ? 2 : 0;
         const char* fu = std::getenv("QDSE_FUSED_UPDATE");
         c->fused_update = (fu && std::string(fu) == "1") ? 1 : 0;
         // kernel matrices: double-float on the FP32 pipe by default; QDSE_PRECOMPUTE=fp64
@@ -628,6 +654,18 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         // test of the sweep's bounded waits (tests only): every tile wait runs out
         const char* st = std::getenv("QDSE_TEST_STALL");
         c->stall_copies = (st && std::string(st) == "1") ? 1 : 0;
+    }
+    if (o->shared_kernels) {
+        // one grid for every instance (checked above), collocated
+        c->tc = 1;
+        c->tc_n = c->hinst[0].g.n_p;
+        c->fused_update = 0;  // the update launch advances the instances the product swept
+        e = tc_setup(c);
+        if (e != cudaSuccess) {
+            qdse_status s = cuda_fail(nullptr, e, "set up the tensor-core sweep");
+            free_ctx(c);
+            return s;
+        }
     }
     // zero the padding of the node vectors once; descriptors get their layout now and their
     // parameters on every call
@@ -668,6 +706,7 @@ qdse_options qdse_default_options(void) {
     o.reuse_kernels = 0;
     o.stall_window = 0;
     o.stop_cycles = 1;
+    o.shared_kernels = 0;
     o.stream = nullptr;
     return o;
 }
@@ -898,6 +937,7 @@ qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, con
     if (rebuild || !c->kw_valid) {
         QCHECK(c, launch_precompute(c, true), "precompute kernels and omega derivatives");
         QCHECK(c, launch_group_bands(c), "group bands");
+        if (c->tc) QCHECK(c, launch_tc_extract(c), "tensor-core kernel planes");
         for (int b = 0; b < c->n_inst; ++b) c->k_omega[b] = p[b].omega;
         c->k_valid_for = 1;
         c->kw_valid = 1;

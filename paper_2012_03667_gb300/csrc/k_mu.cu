@@ -255,35 +255,37 @@ __device__ __forceinline__ void load_point<double>(const double* p, qmu::cx<doub
 // F_p + beta (F_ray - F_p) in place of F_p, with F_ray the interpolation (reading M6) of F where q~'s
 // ray crosses p~'s real 4-radius, (|q|, q_4) sqrt(P^2 + p_4^2)/sqrt(Q^2 + q_4^2), and
 // beta = exp(-(2 mu |q_4 - p_4|/eta)^2).  The ray point depends on the pair only; beta on the
-// pair and mu.  Pairs with beta below kRayMin keep F_p (the difference is below 1e-17 of F).
+// pair and mu.  Pairs with beta below exp(-39.2) keep F_p (the difference is below 1e-17 of F).
 struct RayArgs {
     const double* pax;   // external product grid: |p| axis [n_pr]
     const double* p4ax;  // p_4 axis [n_p4]
     int n_pr, n_p4;
     double eta;          // GeV^2
 };
-constexpr double kRayMin = 1e-17;
+constexpr float kRayCut = 39.2f;  // beta = exp(-u^2) is kept while u^2 < 39.2
 
 // (lower index, upper index, weight of the upper node) of x on an ascending axis: held at the first
-// or last node outside it (the rule of reading M6, as in bracket() on the host).
-__device__ __forceinline__ void ray_bracket(const double* __restrict__ axis, int n, double x,
-                                            int& i0, int& i1, double& wgt) {
+// or last node outside it (the rule of reading M6, as in bracket() on the host).  In the sweep's
+// precision T: FP32 sweeps only bring an FP32-accurate iterate to the FP64 phase.
+template <class T>
+__device__ __forceinline__ void ray_bracket(const double* __restrict__ axis, int n, T x, int& i0,
+                                            int& i1, T& wgt) {
     int lo = -1, hi = n;  // axis[lo] <= x < axis[hi] (lo = -1: below the first node)
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (axis[mid] <= x) lo = mid;
+        if (T(axis[mid]) <= x) lo = mid;
         else hi = mid;
     }
     if (lo < 0) {
         i0 = i1 = 0;
-        wgt = 0.0;
+        wgt = T(0);
     } else if (lo >= n - 1) {
         i0 = i1 = n - 1;
-        wgt = 0.0;
+        wgt = T(0);
     } else {
         i0 = lo;
         i1 = lo + 1;
-        wgt = (x - axis[lo]) / (axis[lo + 1] - axis[lo]);
+        wgt = (x - T(axis[lo])) / (T(axis[lo + 1]) - T(axis[lo]));
     }
 }
 
@@ -335,18 +337,19 @@ k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
         const T s = T(row.p4 + q4f);
         // reading M8: the ray point's corners and weights (reading M6), once per pair
         int e00 = 0, e10 = 0, e01 = 0, e11 = 0, rconj = 0;
-        double ra = 0.0, rb = 0.0;
+        T ra = T(0), rb = T(0), dq4 = T(0);
         if (RAY) {
-            const double Q = qr[r];
-            const double lam = sqrt(row.P * row.P + row.p4 * row.p4) / sqrt(Q * Q + q4f * q4f);
+            const T Q = T(qr[r]), Pp = T(row.P), p4 = T(row.p4), q4 = T(q4f);
+            const T lam = sqrt(Pp * Pp + p4 * p4) / sqrt(Q * Q + q4 * q4);
             int i0, i1, k0, k1;
-            ray_bracket(ray.pax, ray.n_pr, Q * lam, i0, i1, ra);
-            ray_bracket(ray.p4ax, ray.n_p4, fabs(q4f * lam), k0, k1, rb);
+            ray_bracket<T>(ray.pax, ray.n_pr, Q * lam, i0, i1, ra);
+            ray_bracket<T>(ray.p4ax, ray.n_p4, fabs(q4 * lam), k0, k1, rb);
+            dq4 = T(2) * T(fabs(row.p4 - q4f)) / T(ray.eta);
             e00 = i0 * ray.n_p4 + k0;
             e10 = i1 * ray.n_p4 + k0;
             e01 = i0 * ray.n_p4 + k1;
             e11 = i1 * ray.n_p4 + k1;
-            rconj = q4f * lam < 0.0;
+            rconj = q4f < 0.0;
         }
 #pragma unroll
         for (int t = 0; t < TB; ++t) {
@@ -357,26 +360,26 @@ k_mu_sweep(const MuRow* __restrict__ rows, const double* __restrict__ qr,
                 const C Ai{d[0], d[1]}, Ci{d[2], d[3]}, Bi{d[4], d[5]};
                 C Ad = Ai, Cd = Ci, Bd = Bi;
                 if (RAY) {
-                    const double u = 2.0 * (double)d[6] * fabs(row.p4 - q4f) / ray.eta;
-                    const double beta = exp(-u * u);
-                    if (beta > kRayMin) {
+                    const T u = d[6] * dq4;
+                    if (u * u < kRayCut) {  // beta = exp(-u^2) above exp(-39.2), about 1e-17
+                        const T beta = exp(-u * u);
                         const int b = list ? list[b0 + t] : b0 + t;
-                        const double w00 = (1.0 - ra) * (1.0 - rb), w10 = ra * (1.0 - rb);
-                        const double w01 = (1.0 - ra) * rb, w11 = ra * rb;
+                        const T w00 = (T(1) - ra) * (T(1) - rb), w10 = ra * (T(1) - rb);
+                        const T w01 = (T(1) - ra) * rb, w11 = ra * rb;
                         C* dst[3] = {&Ad, &Cd, &Bd};
                         const C own[3] = {Ai, Ci, Bi};
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const double* Fc = F_ext + ((size_t)b * 3 + c) * 2 * n_ext;
-                            double xr = Fc[2 * e00] * w00 + Fc[2 * e10] * w10;
-                            double xi = Fc[2 * e00 + 1] * w00 + Fc[2 * e10 + 1] * w10;
-                            xr = xr + Fc[2 * e01] * w01;
-                            xi = xi + Fc[2 * e01 + 1] * w01;
-                            xr = xr + Fc[2 * e11] * w11;
-                            xi = xi + Fc[2 * e11 + 1] * w11;
+                            T xr = T(Fc[2 * e00]) * w00 + T(Fc[2 * e10]) * w10;
+                            T xi = T(Fc[2 * e00 + 1]) * w00 + T(Fc[2 * e10 + 1]) * w10;
+                            xr = xr + T(Fc[2 * e01]) * w01;
+                            xi = xi + T(Fc[2 * e01 + 1]) * w01;
+                            xr = xr + T(Fc[2 * e11]) * w11;
+                            xi = xi + T(Fc[2 * e11 + 1]) * w11;
                             if (rconj) xi = -xi;
-                            *dst[c] = C{own[c].re + T(beta) * (T(xr) - own[c].re),
-                                        own[c].im + T(beta) * (T(xi) - own[c].im)};
+                            *dst[c] = C{own[c].re + beta * (xr - own[c].re),
+                                        own[c].im + beta * (xi - own[c].im)};
                         }
                     }
                 }

@@ -871,12 +871,14 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         s.cyc_at = 0;
         state[b] = s;
         w.ilist[atomicAdd(w.lcount + 0, 1)] = b;
-        const int ng = (I.n + kRows - 1) / kRows;
-        const int gb = atomicAdd(w.lcount + 3, ng);
-        for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
-        const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
-        const int sb = atomicAdd(w.lcount + 6, ns);
-        for (int t = 0; t < ns; ++t) w.slist[sb + t] = I.s_off + t;
+        if (!(ctl->tc_picard && phase0 == PH_PICARD32)) {  // else the tensor-core sweep has it
+            const int ng = (I.n + kRows - 1) / kRows;
+            const int gb = atomicAdd(w.lcount + 3, ng);
+            for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
+            const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
+            const int sb = atomicAdd(w.lcount + 6, ns);
+            for (int t = 0; t < ns; ++t) w.slist[sb + t] = I.s_off + t;
+        }
     }
     for (int t = threadIdx.x; t < (I.n + kRows - 1) / kRows; t += blockDim.x) g.gphase[I.g_off + t] = phase0;
     for (int t = threadIdx.x; t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
@@ -1323,8 +1325,9 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             w.ilist[(size_t)next_list * w.n_inst + atomicAdd(w.lcount + next_list, 1)] = b;
         }
     }
-    if (!done) {
-        // ... and so do its row groups and slabs
+    if (!done && !(C.tc_picard && next == PH_PICARD32)) {
+        // ... and so do its row groups and slabs (FP32 Picard rows of a shared-kernel batch go
+        // to the tensor-core sweep instead)
         const int ng = (I.n + kRows - 1) / kRows;
         const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
         const int gb = T.bcast(T.leader() ? atomicAdd(w.lcount + 3 + next_list, ng) : 0);
@@ -1412,9 +1415,6 @@ __global__ void __launch_bounds__(256, kTickBlocksPerSM) k_tick(const DevInst* _
 constexpr int kTileCols = 128;                         // columns per tile (4 per lane)
 constexpr int kVecOff = 3 * kRows * kTileCols;         // slot floats before the node vectors
 constexpr int kTileFloats = (3 * kRows + 5) * kTileCols;
-constexpr int kRcRing = 3;    // row-constant entries per warp (groups k .. k + 2 in use)
-constexpr int kDescRing = 5;  // descriptor entries per warp (up to group k + 4)
-constexpr int kIdRing = 8;    // list-id entries per warp (up to group k + 6)
 constexpr long long kRingWaitBudget = 2000000000LL;    // clock cycles (about 1 s)
 static_assert((kTileFloats * sizeof(float)) % 16 == 0, "tile slots must stay 16-byte aligned");
 static_assert(kRows == 4, "the queue's row-constant copies are laid out for groups of 4 rows");
@@ -1429,25 +1429,38 @@ struct RingRows {         // a group's row constants
     float tc[4][kRows];   // tangent: dA_i, dB_i, stencil of the direction (A, B)
     float td[2][4];       // tangent: du1, du2 at the group's own nodes
 };
-struct RingQueue {        // one warp's rings
-    RingDesc desc[kDescRing];
-    RingRows rows[kRcRing];
-    int id[kIdRing];
+// One warp's rings when its copying side may run AHEAD groups ahead of its computing side (group
+// ck): row constants of groups ck .. ck + AHEAD, descriptors up to ck + AHEAD + 2, list ids up to
+// ck + AHEAD + 4.
+template <int AHEAD>
+struct RingQueue {
+    static constexpr int kRc = AHEAD + 1, kDesc = AHEAD + 3, kId = AHEAD + 6;
+    RingDesc desc[kDesc];
+    RingRows rows[kRc];
+    int id[kId];
+    int pad[(4 - kId % 4) % 4];
 };
 static_assert(sizeof(RingDesc) % 16 == 0 && sizeof(RingRows) % 16 == 0 &&
-                  sizeof(RingQueue) % 16 == 0,
+                  sizeof(RingQueue<2>) % 16 == 0 && sizeof(RingQueue<3>) % 16 == 0 &&
+                  sizeof(RingQueue<4>) % 16 == 0,
               "ring entries must stay 16-byte aligned");
 
-template <int WARPS, int SLOTS>
+// A ring shape: WARPS computing warps per block, SLOTS tile slots per warp, and the copying side at
+// most AHEAD groups ahead of the computing side.
+template <int WARPS, int SLOTS, int AHEAD>
 struct RingCfg {
-    static constexpr int kWarps = WARPS, kSlots = SLOTS;
+    static constexpr int kWarps = WARPS, kSlots = SLOTS, kAhead = AHEAD;
+    using Queue = RingQueue<AHEAD>;
     static constexpr size_t kTileBytes = (size_t)WARPS * SLOTS * kTileFloats * sizeof(float);
     static constexpr size_t kBarBytes = (size_t)WARPS * SLOTS * 8;
-    static constexpr size_t kSmem = kTileBytes + kBarBytes + (size_t)WARPS * sizeof(RingQueue);
+    static constexpr size_t kSmem = kTileBytes + kBarBytes + (size_t)WARPS * sizeof(Queue);
     static_assert(kSmem <= 227 * 1024, "ring sweep shared memory");
     static_assert(kBarBytes % 16 == 0, "queue must start 16-byte aligned");
+    static_assert(AHEAD >= 2 && AHEAD <= 4, "cp_wait covers 0 .. 4 pending groups");
 };
-using RingSweep = RingCfg<12, 2>;
+using RingSweep = RingCfg<12, 2, 2>;  // the default shape
+using RingDeep = RingCfg<8, 3, 3>;
+using RingDeeper = RingCfg<6, 4, 4>;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -1507,11 +1520,13 @@ __device__ __forceinline__ void cp16(void* dst, const void* src) {
                  : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most n (0, 1 or 2) of this thread's most recent copy groups are pending
+// wait until at most n (0 .. 4) of this thread's most recent copy groups are pending
 __device__ __forceinline__ void cp_wait(int n) {
     if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
     else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (n == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (n == 3) asm volatile("cp.async.wait_group 3;" ::: "memory");
+    else asm volatile("cp.async.wait_group 4;" ::: "memory");
 }
 
 // A narrow tile (at most 32 * 4 / SPLIT columns, typically the last of a band) of a full group's
@@ -1588,7 +1603,8 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * S * kTileFloats;
     unsigned long long* bars =
         reinterpret_cast<unsigned long long*>(smem + Cfg::kTileBytes) + warp * S;
-    RingQueue& q = reinterpret_cast<RingQueue*>(smem + Cfg::kTileBytes + Cfg::kBarBytes)[warp];
+    using Queue = typename Cfg::Queue;
+    Queue& q = reinterpret_cast<Queue*>(smem + Cfg::kTileBytes + Cfg::kBarBytes)[warp];
     if (lane == 0) {
         for (int k = 0; k < S; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[k]))
@@ -1661,12 +1677,12 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
     auto produce = [&](int ck) -> bool {
         if (!ptiles) {
             const int k = pk + 1;
-            if (k >= nmine || k - ck > 2) return false;
+            if (k >= nmine || k - ck > Cfg::kAhead) return false;
             pk = k;
             cp_wait(1);  // group k's descriptor and phase, group k + 2's list id
             __syncwarp();
-            const RingDesc& e = q.desc[k % kDescRing];
-            RingRows& rw = q.rows[k % kRcRing];
+            const RingDesc& e = q.desc[k % Queue::kDesc];
+            RingRows& rw = q.rows[k % Queue::kRc];
             const int ph = e.phase;
             const int o = e.d.x_off + e.d.i0, nr = e.d.nr, ib = e.d.v_off + e.d.i0;
             pjhi = e.d.jhi;
@@ -1690,8 +1706,8 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
             } else if (lane < 6 * kRows + 7) {
                 // descriptor (4 x 16 bytes) and phase of group k + 2
                 if (k + 2 < nmine) {
-                    const int part = lane - 6 * kRows - 2, id = q.id[(k + 2) % kIdRing];
-                    RingDesc& n2 = q.desc[(k + 2) % kDescRing];
+                    const int part = lane - 6 * kRows - 2, id = q.id[(k + 2) % Queue::kId];
+                    RingDesc& n2 = q.desc[(k + 2) % Queue::kDesc];
                     if (part < 4) cp16(reinterpret_cast<int4*>(&n2.d) + part,
                                        reinterpret_cast<const int4*>(g.gdesc + id) + part);
                     else cp4(&n2.phase, g.gphase + id);
@@ -1712,7 +1728,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
             if (k + 4 < nmine) {
                 const int c = claim();  // list id of group k + 4
                 if (c < 0) nmine = k + 4;
-                else if (lane == 0) cp4(&q.id[(k + 4) % kIdRing], ids + c);
+                else if (lane == 0) cp4(&q.id[(k + 4) % Queue::kId], ids + c);
             }
             cp_commit();
             return true;
@@ -1773,9 +1789,9 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         fill(ck);
         cp_wait(pk - ck);  // group ck's row constants
         __syncwarp();
-        const GroupDesc& d = q.desc[ck % kDescRing].d;
-        const int phase = q.desc[ck % kDescRing].phase;
-        const RingRows& e = q.rows[ck % kRcRing];
+        const GroupDesc& d = q.desc[ck % Queue::kDesc].d;
+        const int phase = q.desc[ck % Queue::kDesc].phase;
+        const RingRows& e = q.rows[ck % Queue::kRc];
         if (phase != PH_PICARD32 && phase != PH_TANGENT32) {
             const GroupDesc dc = d;
             tick_group(dc, phase, lane, inst[dc.b], ctl, g, w, Khi, Klo, A, B, ntot);
@@ -2351,20 +2367,33 @@ cudaError_t launch_group_params(qdse_ctx* c) {
     return cudaGetLastError();
 }
 
+template <typename Cfg>
+static cudaError_t configure_ring_shape() {
+    return cudaFuncSetAttribute(k_tick_ring<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg::kSmem);
+}
+
 cudaError_t configure_tick_ring() {
-    return cudaFuncSetAttribute(k_tick_ring<RingSweep>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RingSweep::kSmem);
+    cudaError_t e = configure_ring_shape<RingSweep>();
+    if (e == cudaSuccess) e = configure_ring_shape<RingDeep>();
+    if (e == cudaSuccess) e = configure_ring_shape<RingDeeper>();
+    return e;
+}
+
+template <typename Cfg>
+static void launch_ring_shape(qdse_ctx* c, double* A, double* B) {
+    const int sms = c->n_sms > 0 ? c->n_sms : 152;
+    const int blocks = std::max(1, std::min((c->n_groups + Cfg::kWarps - 1) / Cfg::kWarps, sms));
+    k_tick_ring<Cfg><<<blocks, Cfg::kWarps * 32, Cfg::kSmem, c->stream>>>(
+        c->d_inst, c->d_state, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
+        (int)(c->tick % 3), c->d_count, c->d_sweeps, c->fused_update, c->d_err);
 }
 
 cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B) {
     prof_begin(c, PK_SWEEP);
-    const int sms = c->n_sms > 0 ? c->n_sms : 152;
-    const int blocks =
-        std::max(1, std::min((c->n_groups + RingSweep::kWarps - 1) / RingSweep::kWarps, sms));
-    k_tick_ring<RingSweep><<<blocks, RingSweep::kWarps * 32, RingSweep::kSmem, c->stream>>>(
-        c->d_inst, c->d_state, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, A, B, c->n_total,
-        (int)(c->tick % 3), c->d_count, c->d_sweeps, c->fused_update, c->d_err);
+    if (c->ring_shape == 1) launch_ring_shape<RingDeep>(c, A, B);
+    else if (c->ring_shape == 2) launch_ring_shape<RingDeeper>(c, A, B);
+    else launch_ring_shape<RingSweep>(c, A, B);
     if (c->fused_update) c->tick++;  // otherwise launch_update advances the tick
     c->launches++;
     prof_end(c);

@@ -111,6 +111,8 @@ struct Ctl {              // solver controls shared by every instance of a call
                           // it copies per tile, so each tile wait runs out (QDSE_TEST_STALL=1)
     int stall_window;     // no-progress stop of the Picard phases (0 = off)
     int stop_cycles;      // end a Picard phase whose iterate repeats exactly (0 = off)
+    int tc_picard;        // 1: FP32 Picard rows are swept by the tensor-core product (k_tc.cu),
+                          // so instances in that phase put no row groups on the active lists
 };
 
 // Work arrays (device).  Component counts in brackets, each of length n_total.
@@ -312,6 +314,13 @@ struct qdse_ctx {
     int sweep_kind = 0;       // FP32 sweep: 2 slab (bulk copies through shared memory, slabs of
                               // row groups), 1 ring (the same per row group), 0 register-only
     int precompute_kind = 1;  // kernel matrices: 1 double-float on the FP32 pipe (default), 0 FP64
+    int ring_shape = 0;       // ring sweep: 0 = 12 warps x 2 slots, 1 = 8 x 3, 2 = 6 x 4
+    // shared kernels (options.shared_kernels): the tensor-core Picard sweep of k_tc.cu
+    int tc = 0, tc_n = 0, tc_ld = 0, tc_nbt = 0;
+    float* tc_Kf = nullptr;   // [2][3 n][tc_ld] far-field planes, TF32 high and low parts
+    float* tc_Kn = nullptr;   // [3][n][17] near band
+    float* tc_V = nullptr;    // [tc_nbt][2][176][tc_ld] column functions of the batch (TF32 parts)
+    alignas(64) unsigned char tc_map[3][128];  // tensor maps: planes, functions (112 and 32 rows)
     int fused_update = 0;     // ring sweep: 1 advances each instance inside the sweep launch (one
                               // launch per tick), 0 in a separate k_update launch (the default)
     int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
@@ -365,6 +374,10 @@ cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_tick_slab(qdse_ctx* c, double* A, double* B);
 cudaError_t configure_tick_slab();
 cudaError_t configure_tick_ring();
+cudaError_t tc_setup(qdse_ctx* c);
+void tc_free(qdse_ctx* c);
+cudaError_t launch_tc_extract(qdse_ctx* c);
+cudaError_t launch_tc_sweep(qdse_ctx* c);
 cudaError_t launch_group_bands(qdse_ctx* c);
 cudaError_t launch_group_params(qdse_ctx* c);
 cudaError_t launch_update(qdse_ctx* c, double* A, double* B);

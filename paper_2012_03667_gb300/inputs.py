@@ -71,6 +71,16 @@ def scan_batch(n_inst: int = 4096, seed: int = SCAN_SEED,
     return out
 
 
+def mscan_batch(n_inst: int = 1024, seed: int = SCAN_SEED, n: int = 512, n_theta: int = 128,
+                D: float = 0.55, omega: float = 0.678,
+                m_range=(0.0, 0.2)) -> List[Instance]:
+    """A current-mass scan that shares one kernel matrix: one grid (N_q = n, N_theta) and the
+    paper's Sec. IV interaction for every instance, m ~ U[0, 0.2] GeV from SplitMix64(seed)."""
+    rng = SplitMix64(seed ^ 0x6D5343414E)
+    return [Instance(n, n_theta, D, omega, m_range[0] + (m_range[1] - m_range[0]) * rng.uniform())
+            for _ in range(n_inst)]
+
+
 def adjoint_batch(n_inst: int = 1024, seed: int = SCAN_SEED) -> List[Instance]:
     """The adjoint workload: the scan generator restricted to N_q = 256, N_theta = 64."""
     return scan_batch(n_inst, seed, n_choices=(256,), theta_choices=(64,))

@@ -49,7 +49,7 @@ class qdse_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("alpha", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("time_limit", ctypes.c_double), ("reuse_kernels", ctypes.c_int),
                 ("stall_window", ctypes.c_int), ("stop_cycles", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("shared_kernels", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class QdseError(RuntimeError):
@@ -163,13 +163,15 @@ class Context:
     def __init__(self, grid, n_inst: int = 1, precision: int = QDSE_MIXED,
                  vertex: int = QDSE_VERTEX_BC, cf: float = 4.0 / 3.0, tol: float = 1e-10,
                  alpha: float = 1.0, max_iter: int = 20000, time_limit: float = 0.0,
-                 reuse_kernels: int = 0, stall_window: int = 0, stop_cycles: int = 1):
+                 reuse_kernels: int = 0, stall_window: int = 0, stop_cycles: int = 1,
+                 shared_kernels: int = 0):
         self.lib = load_library()
         self.ptr = ctypes.c_void_p()
         o = self.lib.qdse_default_options()
         o.precision, o.vertex, o.cf, o.tol, o.alpha = precision, vertex, cf, tol, alpha
         o.max_iter, o.time_limit, o.reuse_kernels = max_iter, time_limit, reuse_kernels
         o.stall_window, o.stop_cycles = stall_window, stop_cycles
+        o.shared_kernels = shared_kernels
         try:
             o.stream = _current_stream()
         except Exception:

@@ -80,7 +80,7 @@ def test_default_options(lib):
     assert o.precision == Q.QDSE_MIXED and o.vertex == Q.QDSE_VERTEX_BC
     assert o.cf == pytest.approx(4 / 3) and o.tol == 1e-10 and o.alpha == 1.0
     assert o.max_iter == 20000 and o.reuse_kernels == 0 and o.stall_window == 0
-    assert o.stop_cycles == 1
+    assert o.stop_cycles == 1 and o.shared_kernels == 0
 
 
 @pytest.mark.parametrize("grid,msg", [
@@ -103,7 +103,8 @@ def test_create_rejects_bad_grids(lib, grid, msg):
 @pytest.mark.parametrize("field,value", [("precision", 9), ("vertex", 3), ("cf", 0.0),
                                          ("tol", -1.0), ("alpha", 0.0), ("alpha", 1.5),
                                          ("max_iter", 0), ("tol", float("inf")),
-                                         ("stall_window", -1), ("stop_cycles", 2)])
+                                         ("stall_window", -1), ("stop_cycles", 2),
+                                         ("shared_kernels", 2)])
 def test_create_rejects_bad_options(lib, field, value):
     o = lib.qdse_default_options()
     setattr(o, field, value)
@@ -111,6 +112,31 @@ def test_create_rejects_bad_options(lib, field, value):
     p = ctypes.c_void_p()
     assert lib.qdse_create(ctypes.byref(g), 1, ctypes.byref(o), ctypes.byref(p)) == Q.QDSE_ERR_ARG
     assert not p
+
+
+@pytest.mark.parametrize("field,value,grid_mode,msg", [
+    ("vertex", Q.QDSE_VERTEX_RL, 0, "BC vertex"),
+    ("precision", Q.QDSE_FP64, 0, "QDSE_MIXED"),
+    ("precision", Q.QDSE_FP64_PRE, 0, "QDSE_MIXED"),
+    (None, None, 1, "COLLOCATED"),
+])
+def test_shared_kernels_needs_bc_mixed_and_one_collocated_grid(lib, field, value, grid_mode, msg):
+    """The tensor-core sweep of a shared-kernel batch covers the BC vertex on one collocated grid
+    with FP32 Picard sweeps; anything else is refused before any device work."""
+    o = lib.qdse_default_options()
+    o.shared_kernels = 1
+    if field:
+        setattr(o, field, value)
+    g = Q.qdse_grid(64, 32, 1e-4, 1e4, grid_mode)
+    p = ctypes.c_void_p()
+    assert lib.qdse_create(ctypes.byref(g), 4, ctypes.byref(o), ctypes.byref(p)) == Q.QDSE_ERR_ARG
+    assert not p and msg in lib.qdse_last_error(None).decode()
+    if field is None:
+        return
+    o.vertex, o.precision = Q.QDSE_VERTEX_BC, Q.QDSE_MIXED
+    two = (Q.qdse_grid * 2)(Q.qdse_grid(64, 32, 1e-4, 1e4, 0), Q.qdse_grid(64, 32, 1e-4, 1e4, 0))
+    assert lib.qdse_create_ragged(two, 2, ctypes.byref(o), ctypes.byref(p)) == Q.QDSE_ERR_ARG
+    assert "qdse_create" in lib.qdse_last_error(None).decode()
 
 
 def test_create_rejects_null_and_empty(lib):

@@ -120,3 +120,18 @@ def test_slab_and_ring_sweeps_end_bitwise_equal(monkeypatch):
     assert np.array_equal(s1, s0) and np.array_equal(i1, i0)
     assert np.array_equal(A1, A0, equal_nan=True) and np.array_equal(B1, B0, equal_nan=True)
     assert (s1 == 0).sum() > 40
+
+
+@pytest.mark.parametrize("shape", ["8x3", "6x4"])
+def test_ring_shapes_end_bitwise_equal(shape, monkeypatch):
+    """Ring shapes differ only in which warp takes a row group and how far its copies run ahead;
+    each group's tile arithmetic is the same, so a ragged batch of the scan ends bitwise equal to
+    the default 12 x 2 shape, with the same statuses and sweep counts."""
+    batch = inputs.scan_batch(160)
+    res = []
+    for s in (shape, "12x2"):
+        monkeypatch.setenv("QDSE_RING", s)
+        res.append(_solve_scan(batch, 1, max_iter=2500))
+    (A1, B1, s1, i1, _, _), (A0, B0, s0, i0, _, _) = res
+    assert np.array_equal(s1, s0) and np.array_equal(i1, i0)
+    assert np.array_equal(A1, A0, equal_nan=True) and np.array_equal(B1, B0, equal_nan=True)
