@@ -870,7 +870,7 @@ def run_mscan(args):
             "tensor_over_per_instance": ring["ms"] / tc["ms"],
             "same_statuses": same, "max_rel_diff_of_solutions": x_err,
             "device_ms": {k: round(v["ms"], 3) for k, v in tc["prof"].items()},
-            "roofline": {"kernel": "k_tc_prep + k_tc_sweep (3xTF32 far field + FP32 near band)",
+            "roofline": {"kernel": "k_tc_any + k_tc_prep + k_tc_gemm (3xTF32 far field) + k_tc_combine (FP32 near band)",
                          "bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_kind": f"{kind} bf16 burst x 0.5 (TF32)",

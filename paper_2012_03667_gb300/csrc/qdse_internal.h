@@ -316,11 +316,13 @@ struct qdse_ctx {
     int precompute_kind = 1;  // kernel matrices: 1 double-float on the FP32 pipe (default), 0 FP64
     int ring_shape = 0;       // ring sweep: 0 = 12 warps x 2 slots, 1 = 8 x 3, 2 = 6 x 4
     // shared kernels (options.shared_kernels): the tensor-core Picard sweep of k_tc.cu
-    int tc = 0, tc_n = 0, tc_ld = 0, tc_nbt = 0;
+    int tc = 0, tc_n = 0, tc_ld = 0, tc_bp = 0, tc_ldg = 0;
     float* tc_Kf = nullptr;   // [2][3 n][tc_ld] far-field planes, TF32 high and low parts
     float* tc_Kn = nullptr;   // [3][n][17] near band
-    float* tc_V = nullptr;    // [tc_nbt][2][176][tc_ld] column functions of the batch (TF32 parts)
-    alignas(64) unsigned char tc_map[3][128];  // tensor maps: planes, functions (112 and 32 rows)
+    float* tc_V = nullptr;    // [2][11 tc_bp][tc_ld] column functions of the batch (TF32 parts)
+    float* tc_G = nullptr;    // [11 tc_bp][tc_ldg] far-field products
+    int* tc_any = nullptr;    // [tc_bp / 128] blocks of instances with one in the Picard phase
+    alignas(64) unsigned char tc_map[2][128];  // tensor maps: column functions, kernel planes
     int fused_update = 0;     // ring sweep: 1 advances each instance inside the sweep launch (one
                               // launch per tick), 0 in a separate k_update launch (the default)
     int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
