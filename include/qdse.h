@@ -108,7 +108,9 @@ typedef struct {
                           approximation sweep is a fixed function of the iterate, so an instance
                           whose iterate repeats exactly within a Picard phase (compared through a
                           64-bit hash of every point's value) cycles forever and ends with
-                          QDSE_ERR_NOT_CONVERGED at once.  It never changes which instances
+                          QDSE_ERR_NOT_CONVERGED at once, unless that sweep's change already
+                          meets the phase's tolerance (a repeat with change 0 is a fixed point,
+                          and it ends the phase as usual).  It never changes which instances
                           converge, nor their results (up to a hash collision, chance below
                           1e-10 per batch); A and B of a stopped instance hold its last iterate */
     int shared_kernels; /* 1: every instance shares the grid and omega (a scan of m or D; D and m

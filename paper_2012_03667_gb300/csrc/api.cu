@@ -202,6 +202,7 @@ Ctl make_ctl(const qdse_ctx* c) {
     t.stall_window = c->opt.stall_window;
     t.stop_cycles = c->opt.stop_cycles;
     t.tc_picard = c->tc;
+    t.slab_lists = c->sweep_kind == 2;
     return t;
 }
 

@@ -172,6 +172,18 @@ struct BlockTeam {
         __syncthreads();
         return v;
     }
+    // the leader's a and b to every thread (one exchange)
+    __device__ void bcast2(int& a, int& b) const {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            reinterpret_cast<int*>(sh)[0] = a;
+            reinterpret_cast<int*>(sh)[1] = b;
+        }
+        __syncthreads();
+        a = reinterpret_cast<const int*>(sh)[0];
+        b = reinterpret_cast<const int*>(sh)[1];
+        __syncthreads();
+    }
 };
 
 // The set of threads that updates one instance inside the ring sweep: one warp (the one that swept
@@ -185,6 +197,10 @@ struct WarpTeam {
     __device__ bool any(bool v) const { return __any_sync(0xffffffffu, v) != 0; }
     __device__ bool leader() const { return (threadIdx.x & 31) == 0; }
     __device__ int bcast(int v) const { return __shfl_sync(0xffffffffu, v, 0); }
+    __device__ void bcast2(int& a, int& b) const {
+        a = __shfl_sync(0xffffffffu, a, 0);
+        b = __shfl_sync(0xffffffffu, b, 0);
+    }
     __device__ void maxf_or(float& a, int& f) const {
         a = warp_maxf(a);
         f = __any_sync(0xffffffffu, f != 0) ? 1 : 0;
@@ -875,15 +891,18 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
             const int ng = (I.n + kRows - 1) / kRows;
             const int gb = atomicAdd(w.lcount + 3, ng);
             for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
-            const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
-            const int sb = atomicAdd(w.lcount + 6, ns);
-            for (int t = 0; t < ns; ++t) w.slist[sb + t] = I.s_off + t;
+            if (ctl->slab_lists) {
+                const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
+                const int sb = atomicAdd(w.lcount + 6, ns);
+                for (int t = 0; t < ns; ++t) w.slist[sb + t] = I.s_off + t;
+            }
         }
     }
     for (int t = threadIdx.x; t < (I.n + kRows - 1) / kRows; t += blockDim.x) g.gphase[I.g_off + t] = phase0;
-    for (int t = threadIdx.x; t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
-         t += blockDim.x)
-        w.sphase[I.s_off + t] = phase0;
+    if (ctl->slab_lists)
+        for (int t = threadIdx.x; t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
+             t += blockDim.x)
+            w.sphase[I.s_off + t] = phase0;
     if (threadIdx.x == 0) w.ticket[b] = 0;
     prepare_phase(phase0, I, g, w, ntot, A, B);
 }
@@ -917,16 +936,16 @@ __device__ __forceinline__ unsigned long long point_hash64(double a, double b, i
 // has gone round once.  Equal hashes of different iterates (a 64-bit collision) would end an
 // instance early; over a batch of thousands of instances and thousands of sweeps that chance is
 // below 1e-10.  Returns the period found (0: none).
+// match: bit k set when entry k of the ring (k < min(nh, kHashRing)) equals h.
 __device__ __forceinline__ int cycle_check(DevState& s, unsigned long long h,
-                                           unsigned long long* ring) {
+                                           unsigned long long* ring, unsigned match) {
     int period = 0;
-    const int valid = min(s.nh, kHashRing);
-    for (int k = 0; k < valid && !period; ++k) {
-        if (ring[k] == h) {
-            // entry k holds hash number t with t % kHashRing == k, the latest such t < nh
-            const int t = s.nh - 1 - ((s.nh - 1 - k) % kHashRing);
-            period = s.nh - t;
-        }
+    if (match) {
+        // the first matching entry k holds hash number t with t % kHashRing == k, the latest such
+        // t < nh
+        const int k = __ffs(match) - 1;
+        const int t = s.nh - 1 - ((s.nh - 1 - k) % kHashRing);
+        period = s.nh - t;
     }
     if (!period && s.nh > 0 && h == s.href) period = s.nh - s.iref;
     ring[s.nh % kHashRing] = h;
@@ -973,9 +992,16 @@ __device__ __forceinline__ bool picard_cycle_reduced(const Team& T, DevState& s,
                                                      unsigned long long h,
                                                      unsigned long long* ring) {
     if (!C.stop_cycles || C.never_converge) return false;
+    // the first warp compares the recorded hashes in parallel (one round of loads)
+    unsigned match = 0;
+    if (T.tid() < 32) {
+        const int k = T.tid();
+        const bool m = k < min(s.nh, kHashRing) && ring[k] == h;
+        match = __ballot_sync(0xffffffffu, m);
+    }
     int period = 0;
     if (T.leader()) {
-        period = cycle_check(s, h, ring);
+        period = cycle_check(s, h, ring, match);
         if (period && !s.cyc_p) {
             s.cyc_p = period;
             s.cyc_at = s.iters;
@@ -1146,20 +1172,24 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
             cycled = picard_cycle(T, s, C, hsh, w.hring + (size_t)b * kHashRing);
         }
         const bool stalled = track_progress(s, C);
+        // a change within the tolerance ends the phase even when the iterate repeated (a repeat
+        // with change 0 is a fixed point, not a cycle)
+        const bool fp32_done = C.final_phase == PH_PICARD32 && !C.never_converge &&
+                               s.change <= C.tol;
+        const bool to_fp64 = C.final_phase != PH_PICARD32 &&
+                             (s.change <= C.sw_tol || s.iters >= C.max_fp32);
         if (bad) {
             done = true;
             status = QDSE_ERR_NONFINITE;
+        } else if (fp32_done) {
+            // FP32-only solves finish here; mixed solves always finish in FP64
+            done = true;
+            status = QDSE_OK;
+        } else if (to_fp64) {
+            next = PH_RESID64;  // hand the FP32 iterate to the FP64 refinement
         } else if (stalled || cycled) {
             done = true;
             status = QDSE_ERR_NOT_CONVERGED;
-        } else if (C.final_phase == PH_PICARD32) {
-            // FP32-only solves finish here; mixed solves always finish in FP64
-            if (!C.never_converge && s.change <= C.tol) {
-                done = true;
-                status = QDSE_OK;
-            }
-        } else if (s.change <= C.sw_tol || s.iters >= C.max_fp32) {
-            next = PH_RESID64;  // hand the FP32 iterate to the FP64 refinement
         }
     } else if (s.phase == PH_PICARD64 || s.phase == PH_RESID64) {
         // relaxed Picard step (or the residual of one) and its R7 relative change
@@ -1303,9 +1333,10 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         }
     }
     for (int t = T.tid(); t < (I.n + kRows - 1) / kRows; t += T.size()) g.gphase[I.g_off + t] = next;
-    for (int t = T.tid(); t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
-         t += T.size())
-        w.sphase[I.s_off + t] = next;
+    if (C.slab_lists)
+        for (int t = T.tid(); t < (I.n + kRows * kSlabGroups - 1) / (kRows * kSlabGroups);
+             t += T.size())
+            w.sphase[I.s_off + t] = next;
     if (T.leader()) {
         if (next != s.phase) {  // a new phase starts its own progress and cycle records
             s.cbest = INFINITY;
@@ -1330,12 +1361,17 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         // to the tensor-core sweep instead)
         const int ng = (I.n + kRows - 1) / kRows;
         const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
-        const int gb = T.bcast(T.leader() ? atomicAdd(w.lcount + 3 + next_list, ng) : 0);
-        const int sb = T.bcast(T.leader() ? atomicAdd(w.lcount + 6 + next_list, ns) : 0);
+        int gb = 0, sb = 0;
+        if (T.leader()) {  // both reservations in flight at once
+            gb = atomicAdd(w.lcount + 3 + next_list, ng);
+            if (C.slab_lists) sb = atomicAdd(w.lcount + 6 + next_list, ns);
+        }
+        T.bcast2(gb, sb);
         for (int t = T.tid(); t < ng; t += T.size())
             w.glist[(size_t)next_list * w.n_groups + gb + t] = I.g_off + t;
-        for (int t = T.tid(); t < ns; t += T.size())
-            w.slist[(size_t)next_list * w.n_slabs + sb + t] = I.s_off + t;
+        if (C.slab_lists)
+            for (int t = T.tid(); t < ns; t += T.size())
+                w.slist[(size_t)next_list * w.n_slabs + sb + t] = I.s_off + t;
     }
     T.sync();
 }

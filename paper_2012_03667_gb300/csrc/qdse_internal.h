@@ -111,6 +111,7 @@ struct Ctl {              // solver controls shared by every instance of a call
                           // it copies per tile, so each tile wait runs out (QDSE_TEST_STALL=1)
     int stall_window;     // no-progress stop of the Picard phases (0 = off)
     int stop_cycles;      // end a Picard phase whose iterate repeats exactly (0 = off)
+    int slab_lists;       // 1: keep the slab lists and slab phases (the slab sweep reads them)
     int tc_picard;        // 1: FP32 Picard rows are swept by the tensor-core product (k_tc.cu),
                           // so instances in that phase put no row groups on the active lists
 };

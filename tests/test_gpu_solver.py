@@ -135,3 +135,31 @@ def test_ring_shapes_end_bitwise_equal(shape, monkeypatch):
     (A1, B1, s1, i1, _, _), (A0, B0, s0, i0, _, _) = res
     assert np.array_equal(s1, s0) and np.array_equal(i1, i0)
     assert np.array_equal(A1, A0, equal_nan=True) and np.array_equal(B1, B0, equal_nan=True)
+
+
+def test_fp32_only_solve_ends_at_a_fixed_point_or_a_found_cycle():
+    """FP32-only Picard to tol = 0 cannot stop on the change unless an iterate repeats exactly:
+    every instance of a small batch at the paper's interaction ends before the sweep cap, either
+    QDSE_OK at an exact FP32 fixed point (its repeat, period 1, is a fixed point and not a stop) or
+    QDSE_ERR_NOT_CONVERGED with the cycle its rounding fell into (period >= 2, found at the sweep
+    that ended it).  This runs the cycle stop's detection on real iterates."""
+    batch = [inputs.Instance(n, 32, 0.55, 0.678, m) for n in (64, 96, 128)
+             for m in (0.0, 0.005, 0.05)]
+    grids = [Q.Grid(b.n_p, b.n_theta, b.s_min, b.s_max) for b in batch]
+    ctx = Q.Context(grids, precision=Q.QDSE_FP32, tol=0.0, max_iter=20000, stop_cycles=1)
+    n = ctx.n_total
+    A = torch.ones(n, dtype=torch.float64, device="cuda")
+    B = torch.full((n,), 0.3, dtype=torch.float64, device="cuda")
+    st = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    it = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    ctx.qdse_solve([[b.D, b.omega, b.m, 0.0] for b in batch], A, B, it, st)
+    st, it = st.cpu().numpy(), it.cpu().numpy()
+    s = ctx.qdse_last_instance_stats()
+    ctx.close()
+    assert np.all(it < 20000)
+    for k in range(len(batch)):
+        if st[k] == Q.QDSE_OK:
+            assert s["cycle_period"][k] in (0, 1)  # 1: the repeat of the fixed point itself
+        else:
+            assert st[k] == Q.QDSE_ERR_NOT_CONVERGED
+            assert s["cycle_period"][k] >= 2 and s["cycle_found_at"][k] == it[k]
