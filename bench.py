@@ -61,6 +61,10 @@ def parse():
                     help="cycle stop of the Picard phases (options.stop_cycles; 1 = on)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default FP32 sweep kernel instead of choosing among the five "
+                         "by one timed solve each (qdse_autotune, before the warm-up, outside the "
+                         "timed region)")
     ap.add_argument("--mu-d", type=float, default=0.55, help="D of --workload mu-solve")
     ap.add_argument("--mu-omega", type=float, default=0.678, help="omega of --workload mu-solve")
     ap.add_argument("--mu-ray-eta", type=float, default=0.002,
@@ -285,6 +289,16 @@ def run_ours(args):
         B.fill_(0.3)
         ctx.qdse_solve(prm, A, B, iters, status)
 
+    tune = None
+    if not args.no_autotune:
+        # the FP32 sweep kernel for this batch, chosen by one timed solve with each candidate
+        # (one-time set-up of the context, like the kernel configuration: outside the steps)
+        A.fill_(1.0)
+        B.fill_(0.3)
+        choice, tms = ctx.qdse_autotune(prm, A, B, 0)
+        tune = {"chosen": Q.Context.SWEEP_KERNELS[choice],
+                "solve_ms_per_candidate": {k: (round(v, 1) if v > 0 else None)
+                                           for k, v in zip(Q.Context.SWEEP_KERNELS, tms)}}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -384,6 +398,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(2 * nt * 8 + 4 * n_inst),
                     "steps": e2e_steps, "same_result_as_device_path": same_as_device},
             "gpu_launches": launches, "accuracy": gate, "fp64_arms": arms,
+            "sweep_kernel": tune,
             "roofline": {"kernel": "k_tick_ring (batched FP32 sweep)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
@@ -931,6 +946,21 @@ def run_adjoint(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     ok = int(((st.cpu().numpy() == 0) & (ist.cpu().numpy() == 0)).sum())
+    # the step's split: the forward solve, then the cotangent + adjoint solve (one more step)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    A.fill_(1.0)
+    B.fill_(0.3)
+    ctx.set_options(tol=1e-12, max_iter=args.max_iter)
+    evs[0].record(stream)
+    ctx.qdse_solve(prm, A, B, None, st)
+    evs[1].record(stream)
+    ctx.qdse_condensate_vjp(A, B, cbar, gA, gB)
+    ctx.set_options(tol=1e-12, max_iter=20000)
+    ctx.qdse_adjoint(prm, A, B, gA, gB, gp, None, ist)
+    evs[2].record(stream)
+    torch.cuda.synchronize()
+    split = {"forward_solve_ms": evs[0].elapsed_time(evs[1]),
+             "adjoint_ms": evs[1].elapsed_time(evs[2])}
     if rank != 0:
         return
     line = {"metric": "condensate gradients d(-<qq>)/d(m, D, w, mu) per second "
@@ -942,7 +972,7 @@ def run_adjoint(args):
             "config": {"workload": f"adjoint: {n} scan instances, N_q = 256, N_theta = 64, "
                                    "BC vertex, mu = 0",
                        "l2": "inputs larger than L2: the kernel pools are re-read each sweep"},
-            "gradients_ok": ok, "clocks": clk.summary()}
+            "gradients_ok": ok, "step_split": split, "clocks": clk.summary()}
     print(json.dumps(line))
 
 

@@ -270,6 +270,23 @@ qdse_status qdse_last_instance_stats(const qdse_ctx* ctx, long long* out, long l
  * each launch is bracketed by two events on the context's stream. */
 qdse_status qdse_set_profiling(qdse_ctx* ctx, int on);
 
+/* Choose the FP32 sweep kernel for this context's batch by timing (not in the paper).  Five
+ * kernels compute the FP32 sweeps with bitwise-identical results and differ only in how the row
+ * groups reach the SMs: 0 the shared-memory ring with 12 warps x 2 tile slots per block (the
+ * default), 1 the ring with 8 x 3, 2 the ring with 6 x 4, 3 the slab sweep (bookkeeping per slab of
+ * 8 row groups), 4 the register-only row-group kernel.  Which is fastest depends on the batch: on
+ * the band widths, and on how fast its active set thins out as instances finish (a kernel that is
+ * fastest with every instance active can be slower over a whole solve).  So each candidate solves
+ * the batch once from the start A0, B0 (device double[n_total], not modified) with the params p
+ * and the context's options, its sweeps capped at max_sweeps when max_sweeps > 0 (0: the context's
+ * max_iter), timed by CUDA events; the fastest is kept for every later call on ctx.
+ * choice (host int, or NULL): the index kept; ms (host double[5], or NULL): each candidate's solve
+ * time (-1 if it did not run).  Contexts in QDSE_FP64 precision, with shared_kernels or with the
+ * fused update keep their sweep (choice = the current one).  Allocates two scratch copies of the
+ * iterate for the trials.  Returns QDSE_OK, QDSE_ERR_ARG, QDSE_ERR_CUDA or QDSE_ERR_TIMEOUT. */
+qdse_status qdse_autotune(qdse_ctx* ctx, const qdse_params* p, const double* A0, const double* B0,
+                          int max_sweeps, int* choice, double* ms);
+
 /* Device time of the last call's launches by kind, from the events recorded while profiling was
  * on: ms[4] and launches[4] (host arrays) for 0 = kernel precompute, 1 = sweeps (all sweep,
  * residual and transposed-sweep kernels), 2 = per-instance updates, 3 = other.  Synchronises. */

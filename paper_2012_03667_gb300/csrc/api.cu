@@ -301,7 +301,7 @@ qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool
         QCHECK(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "order the solve stream");
         c->stream = c->gstream;
     }
-    const int path = (c->opt.precision == QDSE_FP64) ? -2 : c->sweep_kind;
+    const int path = (c->opt.precision == QDSE_FP64) ? -2 : 4 * c->sweep_kind + c->ring_shape;
     int chunk = 4;
     qdse_status st = QDSE_OK;
     while (true) {
@@ -635,6 +635,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         const bool ring_ok = configure_tick_ring() == cudaSuccess;
         cudaGetLastError();
         const bool slab_ok = configure_tick_slab() == cudaSuccess;
+        c->slab_ok = slab_ok ? 1 : 0;
         cudaGetLastError();
         c->sweep_kind = ring_ok ? 1 : 0;
         if (k && std::string(k) == "slab" && slab_ok) c->sweep_kind = 2;
@@ -768,6 +769,95 @@ qdse_status qdse_set_options(qdse_ctx* c, const qdse_options* o) {
     if (check_options(o, why) != QDSE_OK) return fail(c, QDSE_ERR_ARG, why);
     c->opt = *o;
     c->stream = (cudaStream_t)o->stream;
+    return QDSE_OK;
+}
+
+qdse_status qdse_autotune(qdse_ctx* c, const qdse_params* p, const double* A0, const double* B0,
+                          int max_sweeps, int* choice, double* ms) {
+    if (!c) return QDSE_ERR_ARG;
+    c->err.clear();
+    if (max_sweeps < 0) return fail(c, QDSE_ERR_ARG, "max_sweeps must be >= 0");
+    if (check_ptr(c, A0, "A") || check_ptr(c, B0, "B")) return QDSE_ERR_ARG;
+    struct Cand {
+        int kind, shape;
+    };
+    const Cand cands[kTuneCandidates] = {{1, 0}, {1, 1}, {1, 2}, {2, 0}, {0, 0}};
+    int current = 0;
+    for (int k = 0; k < kTuneCandidates; ++k)
+        if (cands[k].kind == c->sweep_kind && cands[k].shape == c->ring_shape) current = k;
+    if (ms)
+        for (int k = 0; k < kTuneCandidates; ++k) ms[k] = -1.0;
+    // FP64-only contexts and the tensor-core sweep have no per-instance FP32 sweep to choose
+    if (c->opt.precision == QDSE_FP64 || c->tc || c->fused_update) {
+        if (choice) *choice = current;
+        return QDSE_OK;
+    }
+    reset_stats(c);
+    bool rebuild = false;
+    qdse_status s = set_params(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    s = ensure_kernels(c, p, rebuild);
+    if (s != QDSE_OK) return s;
+    const size_t bytes = sizeof(double) * (size_t)c->n_total;
+    double *A = nullptr, *B = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void**)&A, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B, bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int kind0 = c->sweep_kind, shape0 = c->ring_shape;
+    int best = current;
+    float best_ms = 0.f;
+    bool timed = false;
+    s = QDSE_OK;
+    for (int k = 0; k < kTuneCandidates && e == cudaSuccess && s == QDSE_OK; ++k) {
+        if (cands[k].kind == 2 && !c->slab_ok) continue;
+        c->sweep_kind = cands[k].kind;
+        c->ring_shape = cands[k].shape;
+        // one solve of the batch, as qdse_solve runs it (capped at max_sweeps when > 0)
+        Ctl ctl = make_ctl(c);
+        if (max_sweeps > 0) ctl.max_iter = std::min(ctl.max_iter, max_sweeps);
+        const int phase0 = (c->opt.precision == QDSE_MIXED || c->opt.precision == QDSE_FP32)
+                               ? PH_PICARD32
+                               : PH_PICARD64;
+        e = cudaMemcpyAsync(A, A0, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B, B0, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = launch_init_state(c, ctl, A, B, phase0);
+        if (e != cudaSuccess) break;
+        bool to = false;
+        s = run_ticks(c, A, B, -1, to);
+        if (s != QDSE_OK || to) {
+            if (s == QDSE_OK) s = fail(c, QDSE_ERR_TIMEOUT, "time limit reached while tuning");
+            break;
+        }
+        e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) break;
+        if (ms) ms[k] = t;
+        if (!timed || t < best_ms) {
+            best = k;
+            best_ms = t;
+            timed = true;
+        }
+    }
+    if (A) cudaFree(A);
+    if (B) cudaFree(B);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->sweep_kind = kind0;
+    c->ring_shape = shape0;
+    if (c->gexec) {  // the captured ticks hold the trial's arrays and kernel
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (s != QDSE_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    c->sweep_kind = cands[best].kind;
+    c->ring_shape = cands[best].shape;
+    if (choice) *choice = best;
     return QDSE_OK;
 }
 

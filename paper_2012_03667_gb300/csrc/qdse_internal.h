@@ -189,6 +189,7 @@ struct Grid {              // FP64 grid arrays on the device (global point index
                            // precompute (see k_precompute.cu)
 };
 
+constexpr int kTuneCandidates = 5;  // qdse_autotune: ring 12x2, 8x3, 6x4, slab, register-only
 constexpr int kRows = 4;   // external points per warp in the batched sweeps (1, 2 or 4)
 constexpr int kTickBlocksPerSM = kRows >= 4 ? 2 : 3;  // resident 256-thread sweep blocks per SM
 constexpr int kTile = 32;  // kernel precompute tile edge
@@ -316,6 +317,7 @@ struct qdse_ctx {
                               // row groups), 1 ring (the same per row group), 0 register-only
     int precompute_kind = 1;  // kernel matrices: 1 double-float on the FP32 pipe (default), 0 FP64
     int ring_shape = 0;       // ring sweep: 0 = 12 warps x 2 slots, 1 = 8 x 3, 2 = 6 x 4
+    int slab_ok = 0;          // the slab sweep could be configured on this device
     // shared kernels (options.shared_kernels): the tensor-core Picard sweep of k_tc.cu
     int tc = 0, tc_n = 0, tc_ld = 0, tc_bp = 0, tc_ldg = 0;
     float* tc_Kf = nullptr;   // [2][3 n][tc_ld] far-field planes, TF32 high and low parts

@@ -31,7 +31,7 @@ EXPORTS = ("qdse_default_options", "qdse_create", "qdse_create_ragged", "qdse_de
            "qdse_iterate", "qdse_solve", "qdse_solve_host", "qdse_residual", "qdse_jvp",
            "qdse_vjp", "qdse_adjoint", "qdse_condensate", "qdse_condensate_vjp",
            "qdse_last_stats", "qdse_last_work", "qdse_last_instance_stats",
-           "qdse_set_profiling", "qdse_profile", "qdse_sweep_fp64_noalloc")
+           "qdse_set_profiling", "qdse_profile", "qdse_autotune", "qdse_sweep_fp64_noalloc")
 
 
 class qdse_grid(ctypes.Structure):
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "qdse_last_instance_stats": (ip, [vp, vp, vp]),
         "qdse_set_profiling": (ip, [vp, ip]),
         "qdse_profile": (ip, [vp, P(dp), P(ctypes.c_longlong)]),
+        "qdse_autotune": (ip, [vp, vp, vp, vp, ip, P(ip), P(dp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -295,6 +296,19 @@ class Context:
 
     def qdse_set_profiling(self, on: bool):
         self._raise(self.lib.qdse_set_profiling(self.ptr, int(bool(on))))
+
+    SWEEP_KERNELS = ("ring 12x2", "ring 8x3", "ring 6x4", "slab", "register-only groups")
+
+    def qdse_autotune(self, params, A, B, max_sweeps: int = 0):
+        """qdse_autotune: solve the batch once from the start A, B (not modified) with each of the
+        five FP32 sweep kernels (sweeps capped at max_sweeps when > 0) and keep the fastest.
+        Returns (index, solve ms per candidate)."""
+        self._sync_stream()
+        choice = ctypes.c_int(-1)
+        ms = (ctypes.c_double * 5)()
+        self._raise(self.lib.qdse_autotune(self.ptr, make_params(params), _ptr(A), _ptr(B),
+                                           int(max_sweeps), ctypes.byref(choice), ms))
+        return choice.value, list(ms)
 
     def qdse_profile(self) -> dict:
         ms = (ctypes.c_double * 4)()

@@ -155,6 +155,7 @@ def test_create_rejects_null_and_empty(lib):
 def test_null_context_is_rejected(lib):
     assert lib.qdse_solve(None, None, None, None, None, None) == Q.QDSE_ERR_ARG
     assert lib.qdse_sizes(None, None, None) == Q.QDSE_ERR_ARG
+    assert lib.qdse_autotune(None, None, None, None, 5, None, None) == Q.QDSE_ERR_ARG
     lib.qdse_destroy(None)  # accepted
 
 

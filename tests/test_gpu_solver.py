@@ -163,3 +163,28 @@ def test_fp32_only_solve_ends_at_a_fixed_point_or_a_found_cycle():
         else:
             assert st[k] == Q.QDSE_ERR_NOT_CONVERGED
             assert s["cycle_period"][k] >= 2 and s["cycle_found_at"][k] == it[k]
+
+
+def test_autotune_keeps_a_kernel_with_bitwise_the_same_solves():
+    """qdse_autotune solves a ragged batch of the scan once with each of the five FP32 sweep kernels
+    (capped at 300 sweeps) and keeps the fastest; the full solve that follows is bitwise the solve
+    of a context left at the default kernel (the candidates differ only in how row groups reach
+    the SMs), and the start is not modified."""
+    batch = inputs.scan_batch(160)
+    grids = [Q.Grid(b.n_p, b.n_theta, b.s_min, b.s_max) for b in batch]
+    prm = [[b.D, b.omega, b.m, 0.0] for b in batch]
+    tuned = Q.Context(grids, precision=Q.QDSE_MIXED, tol=1e-10, max_iter=2500)
+    n = tuned.n_total
+    A0 = torch.ones(n, dtype=torch.float64, device="cuda")
+    B0 = torch.full((n,), 0.3, dtype=torch.float64, device="cuda")
+    choice, ms = tuned.qdse_autotune(prm, A0, B0, 300)
+    assert 0 <= choice < 5 and ms[choice] > 0 and ms[choice] == min(m for m in ms if m > 0)
+    assert torch.all(A0 == 1.0) and torch.all(B0 == 0.3)
+    st = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    it = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    tuned.qdse_solve(prm, A0, B0, it, st)
+    got = (A0.cpu().numpy(), B0.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy())
+    tuned.close()
+    A, B, s0, i0, _, _ = _solve_scan(batch, 1, max_iter=2500)
+    assert np.array_equal(got[2], s0) and np.array_equal(got[3], i0)
+    assert np.array_equal(got[0], A, equal_nan=True) and np.array_equal(got[1], B, equal_nan=True)
