@@ -225,9 +225,13 @@ qdse_status qdse_vjp(qdse_ctx* ctx, const qdse_params* p, const double* A, const
  * with dF/dm = e_B, dF/dD = (F(x*) - x0)/D, dF/domega from the omega-derivative of the angular
  * kernels, and dF/dmu = 0 (mu does not enter the vacuum equation).  A, B, gA, gB: device
  * double[n_total]; g_params: device double[4 n_inst].  The transposed fixed-point solve uses the
- * context's tolerance and max_iter; lambda_out (device double[2 n_total]: lambda_A then
- * lambda_B) may be NULL.  inst_status (device int[n_inst] or NULL) reports convergence of the
- * transposed solve.  Synchronises the stream. */
+ * context's tolerance and max_iter.  A QDSE_MIXED or QDSE_FP32 context on a collocated batch
+ * solves it by defect correction: FP64 residuals r = J^T lambda + g - lambda on the double-float
+ * kernels, each followed by FP32 transposed sweeps for the correction delta = J^T delta + r; other
+ * contexts (and staggered grids) use plain FP64 successive approximation.  Both reach the same FP64
+ * fixed point.  lambda_out (device double[2 n_total]: lambda_A then lambda_B) may be NULL.
+ * inst_status (device int[n_inst] or NULL) reports convergence of the transposed solve.
+ * Synchronises the stream. */
 qdse_status qdse_adjoint(qdse_ctx* ctx, const qdse_params* p, const double* A, const double* B,
                          const double* gA, const double* gB, double* g_params,
                          double* lambda_out, int* inst_status);

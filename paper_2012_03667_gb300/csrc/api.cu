@@ -1039,16 +1039,26 @@ qdse_status qdse_adjoint(qdse_ctx* c, const qdse_params* p, const double* A, con
     QCHECK(c, launch_residual_fp64(c, A, B, c->work.xn64, c->work.xn64 + c->n_total, c->d_rel, 0,
                                    c->d_Khi, c->d_Klo),
            "fixed-point check");
-    QCHECK(c, launch_adjoint_init(c, c->work.lam, gA, gB, c->d_rel, 1e-6), "adjoint init");
+    // mixed precision (FP32 inner sweeps, FP64 residuals) for MIXED/FP32 contexts on collocated
+    // grids; plain FP64 successive approximation otherwise
+    const bool mixed = (c->opt.precision == QDSE_MIXED || c->opt.precision == QDSE_FP32) &&
+                       !c->any_staggered;
+    QCHECK(c, launch_adjoint_init(c, c->work.lam, gA, gB, c->d_rel, 1e-6,
+                                  mixed ? PH_RESID64 : PH_PICARD64),
+           "adjoint init");
     QCHECK(c, launch_adjoint_prep(c, A, B), "adjoint prep");
     const auto t0 = std::chrono::steady_clock::now();
     bool timed_out = false;
     int chunk = 4;
     while (true) {
         for (int t = 0; t < chunk; ++t) {
-            QCHECK(c, launch_adjoint_sweep(c, A, B, gA, gB), "transposed sweep");
             if (t == chunk - 1)
                 QCHECK(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream), "memset");
+            if (mixed) {
+                QCHECK(c, launch_adjoint_mixed_tick(c, gA, gB, c->d_count), "mixed adjoint tick");
+                continue;
+            }
+            QCHECK(c, launch_adjoint_sweep(c, A, B, gA, gB), "transposed sweep");
             QCHECK(c, launch_adjoint_update(c, c->work.lam, c->work.lamn, c->d_count), "adjoint update");
         }
         QCHECK(c, cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "poll");

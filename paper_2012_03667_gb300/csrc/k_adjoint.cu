@@ -5,7 +5,7 @@
 // and g = dL/dx (implicit function theorem; no unrolled iterations are stored).  The transposed
 // fixed point is solved by the same successive approximation, sweep by sweep.
 //
-// J^T w for a collocated grid is computed row by row (k_vjp_row; staggered grids: k_vjp_stag_rows
+// J^T w for a collocated grid is computed row by row (k_vjp_row_t; staggered grids: k_vjp_stag_rows
 // and k_vjp_stag_assemble below): with alpha_i = w^A_i kappa D/P_i and
 // beta_i = w^B_i kappa D, entry l collects
 //   (own)     sum_j alpha_l dT^A_lj/dx_l + beta_l dT^B_lj/dx_l          (row l of the kernels)
@@ -98,19 +98,25 @@ __global__ void k_vjp_prep(const DevInst* __restrict__ inst, const Ctl* __restri
 }
 
 // (J^T w)_l for a collocated grid.  One warp per point l.  If add_g, writes J^T w + g.
-__global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ inst,
-                                                 const Ctl* __restrict__ ctl, Grid g, Work w,
-                                                 const float* __restrict__ Khi,
-                                                 const float* __restrict__ Klo,
-                                                 const DevState* __restrict__ state,
-                                                 double* JA, double* JB, const double* gA,
-                                                 const double* gB, int ntot, int add_g,
-                                                 int only_active) {
+// T = double: FP64 arithmetic on the double-float kernels (hi + lo); T = float: FP32 arithmetic on
+// the FP32 kernels (hi), for the inner sweeps of the mixed-precision adjoint.  want_phase >= 0:
+// only the instances in that phase (the mixed adjoint runs both kinds in one tick).
+template <typename T>
+__global__ void __launch_bounds__(256) k_vjp_row_t(const DevInst* __restrict__ inst,
+                                                   const Ctl* __restrict__ ctl, Grid g, Work w,
+                                                   const float* __restrict__ Khi,
+                                                   const float* __restrict__ Klo,
+                                                   const DevState* __restrict__ state,
+                                                   double* JA, double* JB, const double* gA,
+                                                   const double* gB, int ntot, int add_g,
+                                                   int only_active, int want_phase) {
+    constexpr bool LO = sizeof(T) == 8;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= ntot) return;
     const int bi = g.row_inst[r];
     if (only_active && state[bi].phase == PH_DONE) return;
+    if (want_phase >= 0 && state[bi].phase != want_phase) return;
     const DevInst I = inst[bi];
     if (I.mode != QDSE_COLLOCATED) return;  // k_vjp_stag_rows / k_vjp_stag_assemble
     const int l = r - I.x_off;
@@ -124,50 +130,50 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
     const double* al = w.dvec64 + o;
     const double* be = w.dvec64 + ntot + o;
     const double* sp = g.sp + o;
-    const double Pl = sp[l], Al = va[l], Bl = vb[l];
-    const double Q = g.sq[r];
-    const double d = Q * Al * Al + Bl * Bl;
-    const double el = g.W[r] / d;
-    const double ca = -2.0 * el * Q * Al / d, cb = -2.0 * el * Bl / d;
-    const double alpha_l = al[l], beta_l = be[l];
-    double gAl = 0.0, gBl = 0.0;
+    const T Pl = T(sp[l]), Al = T(va[l]), Bl = T(vb[l]);
+    const T Q = T(g.sq[r]);
+    const T d = Q * Al * Al + Bl * Bl;
+    const T el = T(g.W[r]) / d;
+    const T ca = T(-2) * el * Q * Al / d, cb = T(-2) * el * Bl / d;
+    const T alpha_l = T(al[l]), beta_l = T(be[l]);
+    T gAl = T(0), gBl = T(0);
     // K_lm vanishes outside row l's band, and K_ml = K_lm: both parts only need the band
     const int2 bd = g.band[r];
     const int mlo = bd.x, mhi = min(bd.y, I.n);
     if (ctl->vertex == QDSE_VERTEX_BC) {
         for (int m = mlo + lane; m < mhi; m += 32) {
             const long long o0 = row.off(0, m), o1 = row.off(1, m), o2 = row.off(2, m);
-            const double K0 = (double)Khi[o0] + (double)Klo[o0];
-            double KT = (double)Khi[o1] + (double)Klo[o1];
-            const double K3 = (double)Khi[o2] + (double)Klo[o2];
-            if (m == l) KT = 0.0;
+            const T K0 = LO ? T((double)Khi[o0] + (double)Klo[o0]) : T(Khi[o0]);
+            T KT = LO ? T((double)Khi[o1] + (double)Klo[o1]) : T(Khi[o1]);
+            const T K3 = LO ? T((double)Khi[o2] + (double)Klo[o2]) : T(Khi[o2]);
+            if (m == l) KT = T(0);
             // own part: l plays the row index, m the partner
-            const double u1 = v1[m], u2 = v2[m], u3 = v3[m];
-            gAl += alpha_l * (0.5 * (Pl * u2 + u3) * KT + 0.5 * u2 * K3) +
-                   beta_l * (-u1 * KT + 1.5 * u1 * K0);
+            const T u1 = T(v1[m]), u2 = T(v2[m]), u3 = T(v3[m]);
+            gAl += alpha_l * (T(0.5) * (Pl * u2 + u3) * KT + T(0.5) * u2 * K3) +
+                   beta_l * (-u1 * KT + T(1.5) * u1 * K0);
             gBl += alpha_l * (u1 * KT) + beta_l * (u2 * KT);
             // partner part: m plays the row index i, l the partner; K_ml = K_lm, KT_ml = -KT_lm
-            const double KTi = -KT;
-            const double Ai = va[m], Bi = vb[m], Pi = sp[m], ai = al[m], bi = be[m];
-            const double PpQ = Pi + Q;
-            const double TAe = (-Bl * (Bl - Bi) - 0.5 * PpQ * Al * (Al - Ai)) * KTi +
-                               0.5 * Al * (Ai + Al) * K3;
-            const double TBe = (Al * Bi - Bl * Ai) * KTi + 1.5 * Bl * (Ai + Al) * K0;
-            const double dTA_da = el * (-0.5 * PpQ * (2.0 * Al - Ai) * KTi + 0.5 * (Ai + 2.0 * Al) * K3);
-            const double dTA_db = -el * (2.0 * Bl - Bi) * KTi;
-            const double dTB_da = el * (Bi * KTi + 1.5 * Bl * K0);
-            const double dTB_db = el * (-Ai * KTi + 1.5 * (Ai + Al) * K0);
+            const T KTi = -KT;
+            const T Ai = T(va[m]), Bi = T(vb[m]), Pi = T(sp[m]), ai = T(al[m]), bi = T(be[m]);
+            const T PpQ = Pi + Q;
+            const T TAe = (-Bl * (Bl - Bi) - T(0.5) * PpQ * Al * (Al - Ai)) * KTi +
+                          T(0.5) * Al * (Ai + Al) * K3;
+            const T TBe = (Al * Bi - Bl * Ai) * KTi + T(1.5) * Bl * (Ai + Al) * K0;
+            const T dTA_da = el * (T(-0.5) * PpQ * (T(2) * Al - Ai) * KTi + T(0.5) * (Ai + T(2) * Al) * K3);
+            const T dTA_db = -el * (T(2) * Bl - Bi) * KTi;
+            const T dTB_da = el * (Bi * KTi + T(1.5) * Bl * K0);
+            const T dTB_db = el * (-Ai * KTi + T(1.5) * (Ai + Al) * K0);
             gAl += ai * (dTA_da + TAe * ca) + bi * (dTB_da + TBe * ca);
             gBl += ai * (dTA_db + TAe * cb) + bi * (dTB_db + TBe * cb);
         }
     } else {
         for (int m = mlo + lane; m < mhi; m += 32) {
             const long long o0 = row.off(0, m), o2 = row.off(2, m);
-            const double K0 = (double)Khi[o0] + (double)Klo[o0];
-            const double K3 = (double)Khi[o2] + (double)Klo[o2];
-            const double ai = al[m], bi = be[m];
-            gAl += ai * (el + Al * ca) * K3 + bi * 3.0 * Bl * ca * K0;
-            gBl += ai * Al * cb * K3 + bi * 3.0 * (el + Bl * cb) * K0;
+            const T K0 = LO ? T((double)Khi[o0] + (double)Klo[o0]) : T(Khi[o0]);
+            const T K3 = LO ? T((double)Khi[o2] + (double)Klo[o2]) : T(Khi[o2]);
+            const T ai = T(al[m]), bi = T(be[m]);
+            gAl += ai * (el + Al * ca) * K3 + bi * T(3) * Bl * ca * K0;
+            gBl += ai * Al * cb * K3 + bi * T(3) * (el + Bl * cb) * K0;
         }
     }
 #pragma unroll
@@ -181,18 +187,18 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
         const int i0 = l - 2 < 0 ? 0 : l - 2, i1 = l + 2 > I.n - 1 ? I.n - 1 : l + 2;
         for (int i = i0; i <= i1; ++i) {
             const long long od = KRow(I, i).off(1, i);
-            const double KTd = (double)Khi[od] + (double)Klo[od];
-            const double ai = al[i], bi = be[i];
-            const double u1 = v1[i], u2 = v2[i], Pi = sp[i];
-            const double dA = w.dia64[o + i], dB = w.dia64[ntot + o + i];
+            const T KTd = LO ? T((double)Khi[od] + (double)Klo[od]) : T(Khi[od]);
+            const T ai = T(al[i]), bi = T(be[i]);
+            const T u1 = T(v1[i]), u2 = T(v2[i]), Pi = T(sp[i]);
+            const T dA = T(w.dia64[o + i]), dB = T(w.dia64[ntot + o + i]);
             const int sidx = l - g.sta[o + i];
             if (sidx >= 0 && sidx <= 2) {
-                const double c = g.stc[3 * (size_t)(o + i) + sidx];
+                const T c = T(g.stc[3 * (size_t)(o + i) + sidx]);
                 gAl += KTd * (ai * (-Pi * u2 * c) + bi * (u1 * c));
                 gBl += KTd * (ai * (-u1 * c) + bi * (-u2 * c));
             }
             if (i == l) {
-                const double eA = -2.0 * el * Pi * Al / d, eB = -2.0 * el * Bl / d;
+                const T eA = T(-2) * el * Pi * Al / d, eB = T(-2) * el * Bl / d;
                 gAl += KTd * (ai * (-Bl * eA * dB - Pi * (el + Al * eA) * dA) +
                               bi * (Bl * eA * dA - (el + Al * eA) * dB));
                 gBl += KTd * (ai * (-(el + Bl * eB) * dB - Pi * Al * eB * dA) +
@@ -200,12 +206,13 @@ __global__ void __launch_bounds__(256) k_vjp_row(const DevInst* __restrict__ ins
             }
         }
     }
+    double outA = (double)gAl, outB = (double)gBl;
     if (add_g) {
-        gAl += gA[r];
-        gBl += gB[r];
+        outA += gA[r];
+        outB += gB[r];
     }
-    JA[r] = gAl;
-    JB[r] = gBl;
+    JA[r] = outA;
+    JB[r] = outB;
 }
 
 // J^T w on a staggered grid, where the internal nodes q_j are not the external points and the
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(256) k_vjp_stag_rows(const DevInst* __restrict
     const int bi = g.row_inst[r];
     if (only_active && state[bi].phase == PH_DONE) return;
     const DevInst I = inst[bi];
-    if (I.mode == QDSE_COLLOCATED) return;  // k_vjp_row
+    if (I.mode == QDSE_COLLOCATED) return;  // k_vjp_row_t
     const int i = r - I.x_off, o = I.x_off;
     const KRow row(I, i);
     const double Pi = g.sp[r], Ai = A[r], Bi = B[r];
@@ -363,11 +370,120 @@ __global__ void k_adjoint_update(const DevInst* __restrict__ inst, DevState* sta
     }
 }
 
+// The mixed-precision adjoint: lambda = J^T lambda + g solved by defect correction, as the forward
+// refinement solves x = F(x).  An instance alternates between
+//   PH_RESID64   (FP64 transposed sweep on the double-float kernels): lamn = J^T lambda + g,
+//                r = lamn - lambda; done when max|r| / max|lamn| <= tol (lambda <- lamn), else
+//                delta = r and the inner solve starts;
+//   PH_TANGENT32 (FP32 transposed sweep on the FP32 kernels): lamn = J32^T delta + r,
+//                delta <- delta + alpha (lamn - delta) until its relative change is <= inner_tol
+//                (or max_inner sweeps); then lambda <- lambda + delta and back to PH_RESID64.
+// J32 differs from J by FP32 rounding (about 1e-7 relative), so each outer step shrinks the
+// residual by about max(inner_tol / (1 - rho), 1e-6): the FP64 fixed point is reached after a few
+// FP64 sweeps instead of one per Picard step.  The weights alpha_i, beta_i of the next sweep
+// (dvec64) are those of lambda for PH_RESID64 and of delta for PH_TANGENT32.
+__global__ void k_adjoint_update_mixed(const DevInst* __restrict__ inst, DevState* state,
+                                       const Ctl* __restrict__ ctl, Grid g, Work w, int ntot,
+                                       int* count, unsigned long long* ctr) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    DevState s = state[b];
+    if (s.phase == PH_DONE) return;
+    const DevInst I = inst[b];
+    const double al = ctl->alpha;
+    double dmax = 0.0, cmax = 0.0, bad = 0.0;
+    const bool resid = (s.phase == PH_RESID64);
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int k = c * ntot + gj;
+            const double ln = w.lamn[k];
+            if (resid) {
+                const double r = ln - w.lam[k];
+                w.r64[k] = r;
+                dmax = fmax(dmax, fabs(ln));
+                cmax = fmax(cmax, fabs(r));
+                if (!isfinite(ln)) bad = 1.0;
+            } else {
+                const double d = w.d64[k];
+                const double dn = d + al * (ln - d);
+                w.d64[k] = dn;
+                dmax = fmax(dmax, fabs(dn));
+                cmax = fmax(cmax, fabs(dn - d));
+                if (!isfinite(dn)) bad = 1.0;
+            }
+        }
+    }
+    dmax = block_max_a(dmax, sh);
+    cmax = block_max_a(cmax, sh);
+    bad = block_max_a(bad, sh);
+    const double change = dmax > 0.0 ? cmax / dmax : 0.0;
+    int next = s.phase, status = s.status;
+    bool done = false;
+    if (bad != 0.0) {
+        done = true;
+        status = QDSE_ERR_NONFINITE;
+    } else if (resid) {
+        if (change <= ctl->tol) {
+            done = true;
+            status = QDSE_OK;
+        } else {
+            next = PH_TANGENT32;  // delta = r
+        }
+    } else if (change <= ctl->inner_tol || s.inner + 1 >= ctl->max_inner) {
+        next = PH_RESID64;  // lambda += delta
+    }
+    if (!done && s.iters + 1 >= ctl->max_iter) {
+        done = true;
+        status = QDSE_ERR_NOT_CONVERGED;
+    }
+    // the new lambda or delta, and the weights of the next sweep
+    const double scale = ctl->kappa * I.D;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        const int gj = I.x_off + j;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int k = c * ntot + gj;
+            if (resid) {
+                if (done && status == QDSE_OK) w.lam[k] = w.lamn[k];
+                else if (next == PH_TANGENT32) w.d64[k] = w.r64[k];
+            } else if (next == PH_RESID64 || done) {
+                w.lam[k] += w.d64[k];
+            }
+        }
+        const double* src = (next == PH_TANGENT32) ? w.d64 : w.lam;
+        w.dvec64[gj] = src[gj] * scale / g.sp[gj];
+        w.dvec64[ntot + gj] = src[ntot + gj] * scale;
+    }
+    if (threadIdx.x == 0) {
+        if (ctr) {
+            const unsigned long long n = (unsigned long long)I.n;
+            atomicAdd(ctr + (resid ? 1 : 0), 1ull);
+            atomicAdd(ctr + 2, (resid ? 24ull : 12ull) * g.nnz[blockIdx.x] + 96ull * n);
+            atomicAdd(ctr + 3, n * n * (unsigned long long)I.nt);
+        }
+        s.iters += 1;
+        if (resid) {
+            s.n64 += 1;
+            s.change = change;
+            s.inner = 0;
+        } else {
+            s.inner += 1;
+            s.dnorm = change;
+        }
+        s.phase = done ? PH_DONE : next;
+        s.status = status;
+        state[b] = s;
+        if (!done && count) atomicAdd(count, 1);
+    }
+}
+
 // lambda = g to start; instances whose state is not a fixed point (relative residual rel above
 // not_fixed; the implicit function theorem does not apply there) are marked finished at once.
 __global__ void k_adjoint_init(const DevInst* __restrict__ inst, DevState* state, Work w,
                                const double* gA, const double* gB, int ntot, const double* rel,
-                               double not_fixed) {
+                               double not_fixed, int phase0) {
     const DevInst I = inst[blockIdx.x];
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
         const int gj = I.x_off + j;
@@ -376,7 +492,7 @@ __global__ void k_adjoint_init(const DevInst* __restrict__ inst, DevState* state
     }
     if (threadIdx.x == 0) {
         DevState s{};
-        s.phase = PH_PICARD64;
+        s.phase = phase0;
         s.status = QDSE_ERR_NOT_CONVERGED;
         s.change = INFINITY;
         if (rel && !(rel[blockIdx.x] <= not_fixed)) s.phase = PH_DONE;
@@ -499,9 +615,9 @@ cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const doub
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof_begin(c, PK_SWEEP);
-    k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(c->d_inst, c->d_ctl, c->grid, c->work,
-                                                            c->d_Khi, c->d_Klo, c->d_state, JA,
-                                                            JB, gA, gB, c->n_total, add_g, 0);
+    k_vjp_row_t<double><<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, JA, JB, gA, gB,
+        c->n_total, add_g, 0, -1);
     c->launches++;
     prof_end(c);
     e = cudaGetLastError();
@@ -510,11 +626,11 @@ cudaError_t launch_vjp(qdse_ctx* c, const double* A, const double* B, const doub
 }
 
 cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB,
-                                const double* rel, double not_fixed) {
+                                const double* rel, double not_fixed, int phase0) {
     (void)lam;
     prof_begin(c, PK_OTHER);
     k_adjoint_init<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->work, gA, gB,
-                                                     c->n_total, rel, not_fixed);
+                                                     c->n_total, rel, not_fixed, phase0);
     c->launches++;
     prof_end(c);
     return cudaGetLastError();
@@ -533,14 +649,45 @@ cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B) {
 cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* A, const double* B, const double* gA,
                                  const double* gB) {
     prof_begin(c, PK_SWEEP);
-    k_vjp_row<<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
+    k_vjp_row_t<double><<<(c->n_total + 7) / 8, 256, 0, c->stream>>>(
         c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, c->work.lamn,
-        c->work.lamn + c->n_total, gA, gB, c->n_total, 1, 1);
+        c->work.lamn + c->n_total, gA, gB, c->n_total, 1, 1, -1);
     c->launches++;
     prof_end(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_vjp_staggered(c, A, B, c->work.lamn, c->work.lamn + c->n_total, 1, gA, gB, 1);
+}
+
+// One tick of the mixed-precision adjoint: the FP64 transposed sweep of the instances in
+// PH_RESID64 (plus g), the FP32 one of those in PH_TANGENT32 (plus r), then the update.
+cudaError_t launch_adjoint_mixed_tick(qdse_ctx* c, const double* gA, const double* gB,
+                                      int* n_active) {
+    const int blocks = (c->n_total + 7) / 8;
+    prof_begin(c, PK_SWEEP);
+    k_vjp_row_t<double><<<blocks, 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, c->work.lamn,
+        c->work.lamn + c->n_total, gA, gB, c->n_total, 1, 1, PH_RESID64);
+    c->launches++;
+    prof_end(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(c, PK_SWEEP);
+    k_vjp_row_t<float><<<blocks, 256, 0, c->stream>>>(
+        c->d_inst, c->d_ctl, c->grid, c->work, c->d_Khi, c->d_Klo, c->d_state, c->work.lamn,
+        c->work.lamn + c->n_total, c->work.r64, c->work.r64 + c->n_total, c->n_total, 1, 1,
+        PH_TANGENT32);
+    c->launches++;
+    prof_end(c);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(c, PK_UPDATE);
+    k_adjoint_update_mixed<<<c->n_inst, 256, 0, c->stream>>>(c->d_inst, c->d_state, c->d_ctl,
+                                                             c->grid, c->work, c->n_total,
+                                                             n_active, c->d_sweeps);
+    c->launches++;
+    prof_end(c);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active) {

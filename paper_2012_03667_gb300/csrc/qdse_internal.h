@@ -403,6 +403,8 @@ cudaError_t launch_condensate_vjp(qdse_ctx* c, const double* A, const double* B,
                                   const double* cbar, double* gA, double* gB);
 cudaError_t launch_adjoint_update(qdse_ctx* c, double* lam, const double* lam_new, int* n_active);
 cudaError_t launch_adjoint_prep(qdse_ctx* c, const double* A, const double* B);
+cudaError_t launch_adjoint_mixed_tick(qdse_ctx* c, const double* gA, const double* gB,
+                                      int* n_active);
 cudaError_t launch_adjoint_sweep(qdse_ctx* c, const double* A, const double* B, const double* gA,
                                  const double* gB);
 cudaError_t launch_finish_timeout(qdse_ctx* c, double* A, double* B, double* change_out,
@@ -412,7 +414,7 @@ cudaError_t launch_prep64(qdse_ctx* c, const double* A, const double* B, const d
 cudaError_t launch_rel64(qdse_ctx* c, const double* A, const double* B, const double* FA,
                          const double* FB, double* rel);
 cudaError_t launch_adjoint_init(qdse_ctx* c, double* lam, const double* gA, const double* gB,
-                                const double* rel, double not_fixed);
+                                const double* rel, double not_fixed, int phase0);
 cudaError_t launch_adjoint_grads(qdse_ctx* c, const double* A, const double* B,
                                  const double* lam, const double* F, const double* Fw,
                                  double* g_params, int* inst_status);

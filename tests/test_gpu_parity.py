@@ -360,6 +360,37 @@ def test_adjoint_matches_oracle_adjoint_at_the_adjoint_workload_shape(inst):
     assert got[3] == 0.0
 
 
+def test_mixed_precision_adjoint_matches_the_fp64_adjoint_with_few_fp64_sweeps():
+    """The MIXED context's adjoint (FP32 inner transposed sweeps, FP64 residuals of
+    lambda = J^T lambda + g) against the FP64_PRE context's plain FP64 successive approximation,
+    on a small batch at the adjoint workload's shape: the same lambda and parameter gradients to
+    1e-10, every instance converged, and far fewer FP64 sweeps (the FP32 ones do the iterating)."""
+    batch = [inputs.Instance(256, 64, D, om, m) for D, om, m in
+             ((0.55, 0.678, 0.02), (0.6, 0.55, 0.08), (0.55, 0.6, 0.05), (0.5, 0.6, 0.1))]
+    grids = [grid(b) for b in batch]
+    prms = [[b.D, b.omega, b.m, 0.0] for b in batch]
+    fwd = Q.Context(grids, precision=Q.QDSE_FP64_PRE, tol=1e-14, max_iter=40000)
+    A = dev(np.ones(fwd.n_total)); B = dev(np.full(fwd.n_total, 0.3))
+    st = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+    fwd.qdse_solve(prms, A, B, None, st)
+    assert np.all(host(st) == 0)
+    rng = np.random.default_rng(11)
+    gA = dev(rng.normal(size=fwd.n_total)); gB = dev(rng.normal(size=fwd.n_total))
+    out = {}
+    for precision in (Q.QDSE_FP64_PRE, Q.QDSE_MIXED):
+        ctx = Q.Context(grids, precision=precision, tol=1e-13, max_iter=40000)
+        gp = dev(np.zeros(4 * len(batch))); lam = dev(np.zeros(2 * ctx.n_total))
+        ist = torch.zeros(len(batch), dtype=torch.int32, device="cuda")
+        ctx.qdse_adjoint(prms, A, B, gA, gB, gp, lam, ist)
+        assert np.all(host(ist) == 0), precision
+        out[precision] = (host(lam), host(gp), ctx.qdse_last_stats())
+    (l64, g64, s64), (lmx, gmx, smx) = out[Q.QDSE_FP64_PRE], out[Q.QDSE_MIXED]
+    assert rel(lmx, l64) < 1e-10
+    np.testing.assert_allclose(gmx.reshape(-1, 4)[:, :3], g64.reshape(-1, 4)[:, :3], rtol=1e-9)
+    assert smx["fp64_sweeps"] * 5 < s64["fp64_sweeps"], (smx, s64)
+    assert smx["fp32_sweeps"] > 0
+
+
 def test_adjoint_on_a_staggered_grid_matches_oracle_adjoint():
     """The paper's own grid mode (Eqs. pqrelationship, chazhiresult): the transposed fixed point and
     the parameter gradients against the oracle's dense-LU adjoint of the staggered sweep."""
