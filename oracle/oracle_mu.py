@@ -13,7 +13,9 @@ convergence test) and M8 (the optional ray-blended difference quotient) are stat
 ``interpolate``, ``solve`` and ``solve``'s ``ray_eta`` below.  The quadrature weights the oracle
 sums with (reading M5's measure and the cosine rule) are formed here from the node arrays alone
 (``measure``, ``angular_weights``: interpolatory rules from the moment equations), independently
-of the weights the library is given.
+of the weights the library is given.  Finite temperature (Sec. V names it as future work) is the
+same sweep and solve on a grid whose fourth components are Matsubara frequencies, with the
+Matsubara sum as the q_4 rule (readings T1, T2 in ``matsubara_measure``).
 """
 from __future__ import annotations
 
@@ -125,6 +127,26 @@ def measure(q_abs, q4, lo, hi):
 def angular_weights(z):
     """Weights of int_{-1}^{1} dz on the cosine nodes z (interpolatory rule)."""
     return interpolatory_weights(z)
+
+
+def matsubara_measure(q_abs, q4, T, lo, hi):
+    """Reading T1 (finite temperature, announced in Sec. V without equations): in the imaginary-time
+    formalism the quark's fourth momentum takes the fermion Matsubara values q_4 = (2n + 1) pi T
+    and int dq_4/(2 pi) becomes T sum_n, so reading M5's dq_4 becomes 2 pi T per frequency.  The
+    weights w_q of int |q|^2 d|q| dq_4 on the product grid q_abs x q4 (row-major, point
+    r * len(q4) + f) are then w(|q|_r) |q|_r^2 * 2 pi T, the radial rule in ln x on [lo, hi]
+    (log_rule).  Every q4 must be an odd multiple of pi T (both signs); reading T2 truncates the
+    sum to the frequencies given."""
+    q_abs = np.asarray(q_abs, dtype=np.float64)
+    q4 = np.asarray(q4, dtype=np.float64)
+    if not T > 0.0:
+        raise ValueError("temperature must be positive")
+    k = q4 / (np.pi * T)
+    odd = np.round((k - 1.0) / 2.0) * 2.0 + 1.0
+    if not np.allclose(k, odd, rtol=0.0, atol=1e-9):
+        raise ValueError("q4 nodes are not fermion Matsubara frequencies of T")
+    wr = log_rule(q_abs, lo, hi) * q_abs ** 2
+    return np.outer(wr, np.full(len(q4), 2.0 * np.pi * T)).ravel()
 
 
 def vertex(q, q4, p, p4, fq, fp, vertex=BC):

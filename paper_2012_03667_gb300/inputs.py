@@ -122,6 +122,7 @@ class MuWorkload:
     m: float
     lo: float
     hi: float
+    T: float = 0.0  # > 0: q4 and p4 are fermion Matsubara frequencies of this temperature
 
 
 def _log_gl_nodes(n: int, lo: float, hi: float) -> np.ndarray:
@@ -150,6 +151,26 @@ def mu_workload(n_r: int = 128, n_4: int = 128, n_z: int = 64, n_mu: int = 256,
     rng = SplitMix64(seed ^ 0x6D75)
     mu = np.array([mu_range[0] + (mu_range[1] - mu_range[0]) * rng.uniform() for _ in range(n_mu)])
     return MuWorkload(PR.ravel(), P4.ravel(), qr, q4, z, mu, D, omega, m, lo, hi)
+
+
+def matsubara_workload(T: float, n_r: int = 128, n_4: int = 32, n_z: int = 64, n_mu: int = 16,
+                       seed: int = SCAN_SEED, lo: float = 1e-2, hi: float = 1e2,
+                       mu_range: Tuple[float, float] = (0.0, 0.3), D: float = 0.55,
+                       omega: float = 0.678, m: float = 0.005) -> MuWorkload:
+    """A finite-temperature workload: |q| on n_r Gauss-Legendre nodes log-mapped onto [lo, hi] GeV,
+    q_4 on the 2 n_4 fermion Matsubara frequencies +-(2n + 1) pi T (n < n_4), n_z Gauss-Legendre
+    cosine nodes.  External points: |p| staggered between the internal |q| as in mu_workload
+    (|p|_1 = lo, ln |p|_i = (ln q_{i-1} + ln q_i)/2) times the n_4 positive frequencies, so an
+    external point never coincides with an internal one.  mu ~ U[mu_range] from
+    SplitMix64(seed ^ 0x54), in draw order.  Nodes only: each side forms its own weights."""
+    qr = _log_gl_nodes(n_r, lo, hi)
+    wn = (2.0 * np.arange(n_4) + 1.0) * np.pi * T
+    q4 = np.concatenate([-wn[::-1], wn])
+    PR, P4 = np.meshgrid(np.concatenate([[lo], np.sqrt(qr[:-1] * qr[1:])]), wn, indexing="ij")
+    z, _ = np.polynomial.legendre.leggauss(n_z)
+    rng = SplitMix64(seed ^ 0x54)
+    mu = np.array([mu_range[0] + (mu_range[1] - mu_range[0]) * rng.uniform() for _ in range(n_mu)])
+    return MuWorkload(PR.ravel(), P4.ravel(), qr, q4, z, mu, D, omega, m, lo, hi, T)
 
 
 def mu_iterate(v_abs: np.ndarray, v4: np.ndarray, mu: float, m: float = 0.005) -> np.ndarray:

@@ -7,6 +7,8 @@ This module forms them for grids whose |q| and |q_4| nodes are Gauss-Legendre no
   - the finite-mu measure d^4q/(2 pi)^4 = 2 pi/(2 pi)^4 dq_4 |q|^2 d|q| dz (the azimuth gives 2 pi;
     the constant is applied by the library) gives the internal point (|q|_r, q_4f) the weight
     w(|q|_r) |q|_r^2 w(|q_4f|), q_4 < 0 mirroring q_4 > 0.
+At temperature T the fourth components are the fermion Matsubara frequencies q_4 = (2n + 1) pi T and
+int dq_4/(2 pi) is T sum_n, so each frequency carries dq_4 = 2 pi T (matsubara_weights).
 Host-side set-up of the grid (like the vacuum grid of csrc/grid.cpp); none of the sweep.
 """
 from __future__ import annotations
@@ -42,3 +44,17 @@ def angular_weights(z) -> np.ndarray:
     if not np.allclose(z, t, rtol=0.0, atol=1e-14):
         raise ValueError("cosine nodes are not Gauss-Legendre nodes")
     return v
+
+
+def matsubara_weights(q_abs, q4, T: float, lo: float, hi: float) -> np.ndarray:
+    """Weights w_q[r * len(q4) + f] = w(|q|_r) |q|_r^2 2 pi T of the internal product grid at
+    temperature T, whose q4 are fermion Matsubara frequencies (2n + 1) pi T of either sign."""
+    q_abs = np.asarray(q_abs, dtype=np.float64)
+    q4 = np.asarray(q4, dtype=np.float64)
+    if not T > 0.0:
+        raise ValueError("temperature must be positive")
+    n = (np.abs(q4) / (np.pi * T) - 1.0) / 2.0
+    if not np.allclose(n, np.round(n), rtol=0.0, atol=1e-9) or np.any(np.round(n) < 0):
+        raise ValueError("q4 nodes are not fermion Matsubara frequencies of T")
+    return np.outer(log_gl_weights(q_abs, lo, hi) * q_abs ** 2,
+                    np.full(len(q4), 2.0 * np.pi * T)).ravel()

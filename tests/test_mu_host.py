@@ -86,3 +86,21 @@ def test_pair_arithmetic_matches_the_oracle(host, vertex):
                        vertex, fp32)
             err = (np.abs(got - ref).max(axis=1) / scale).max()
             assert err < tol, (mu, fp32, err)
+
+
+def test_matsubara_workload_and_weights_on_the_package_side():
+    """The finite-temperature workload's nodes are the fermion Matsubara frequencies (external p_4
+    the positive ones, internal q_4 both signs), its external |p| never equal an internal |q|, and
+    the package-side weights carry 2 pi T per frequency; frequencies of another T are refused."""
+    T = 0.1
+    w = I.matsubara_workload(T, n_r=8, n_4=4, n_z=8, n_mu=3)
+    assert np.allclose(np.unique(w.p4), (2 * np.arange(4) + 1) * np.pi * T, rtol=1e-15)
+    assert np.allclose(w.q4, np.concatenate([-np.unique(w.p4)[::-1], np.unique(w.p4)]))
+    assert np.abs(np.unique(w.p_abs)[:, None] - w.q_abs[None, :]).min() > 0
+    wq = MR.matsubara_weights(w.q_abs, w.q4, T, w.lo, w.hi).reshape(8, 8)
+    wr = MR.log_gl_weights(w.q_abs, w.lo, w.hi) * w.q_abs ** 2
+    assert np.allclose(wq, np.outer(wr, np.full(8, 2 * np.pi * T)), rtol=1e-15, atol=0)
+    with pytest.raises(ValueError):
+        MR.matsubara_weights(w.q_abs, w.q4 * 1.01, T, w.lo, w.hi)
+    with pytest.raises(ValueError):
+        MR.matsubara_weights(w.q_abs, w.q4, 0.0, w.lo, w.hi)
