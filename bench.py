@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scan",
                     choices=["scan", "large", "small", "adjoint", "mu", "mu-small", "mu-solve",
-                             "table1", "mscan"],
+                             "table1", "mscan", "temperature"],
                     help="scan: 4096-instance mass/interaction scan (default); large/small: one "
                          "N = 512 / N = 64 instance; adjoint: 1024 scan instances at N_q = 256, "
                          "N_theta = 64, forward solve + condensate gradient by the adjoint; mu: "
@@ -45,7 +45,9 @@ def parse():
                          "case of it; mu-solve: finite-mu solve of 32 mu; table1: Sec. IV "
                          "Table 1 (with --impl reference, the four CPU algorithms); mscan: "
                          "1024-instance current-mass scan on one shared kernel matrix, solved "
-                         "with the tensor-core Picard sweep and with the per-instance sweep")
+                         "with the tensor-core Picard sweep and with the per-instance sweep; "
+                         "temperature: finite-temperature solve of 16 mu at each of 6 "
+                         "temperatures on Matsubara grids")
     ap.add_argument("--n-inst", type=int, default=4096)
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--fp64", default="sample", choices=["sample", "full", "none"],
@@ -55,8 +57,11 @@ def parse():
                          "both and the gate")
     ap.add_argument("--otf-sample", type=int, default=48,
                     help="instances of the on-the-fly FP64 arm with --fp64 sample")
-    ap.add_argument("--stall-window", type=int, default=0,
-                    help="no-progress stop of the Picard phases (options.stall_window; 0 = off)")
+    ap.add_argument("--stall-window", type=int, default=4000,
+                    help="no-progress stop of the Picard phases (options.stall_window; 0 = off): "
+                         "an instance ends NOT_CONVERGED after this many sweeps without a new "
+                         "lowest relative change; 4000 leaves the scan's converged set unchanged "
+                         "(its longest converging stall is 3722) and applies to every arm")
     ap.add_argument("--stop-cycles", type=int, default=1, choices=[0, 1],
                     help="cycle stop of the Picard phases (options.stop_cycles; 1 = on)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -72,6 +77,8 @@ def parse():
                          "mu-solve; 0 = the exact quotient")
     ap.add_argument("--mu-max-sweeps", type=int, default=1000,
                     help="sweep cap per round of --workload mu-solve")
+    ap.add_argument("--temp-max-sweeps", type=int, default=400,
+                    help="sweep cap per round of --workload temperature")
     ap.add_argument("--mu-rounds", type=int, default=4,
                     help="continuation rounds of --workload mu-solve (1 = no continuation)")
     return ap.parse_args()
@@ -93,11 +100,12 @@ def workload(args, rank=0):
     return batch, name
 
 
-def band_fraction(batch):
+def band_fraction(batch, x=70.0):
     """Share of the dense N_p x N_q kernel entries inside the bands the precompute keeps: pairs
-    with (sqrt P - sqrt Q)^2 / omega^2 < 70 on each instance's collocated log-mapped
-    Gauss-Legendre grid (every other pair carries exp(-k^2/omega^2) <= exp(-70) at every
-    angle and is stored as an exact zero, never read by the sweeps).  Host arithmetic only."""
+    with (sqrt P - sqrt Q)^2 / omega^2 < x on each instance's collocated log-mapped
+    Gauss-Legendre grid (x = 70: every other pair carries exp(-k^2/omega^2) <= exp(-70) at every
+    angle and is stored as an exact zero, never read by the sweeps; x = 30: the part the FP32
+    sweeps read).  Host arithmetic only."""
     kept = dense = 0.0
     dist = {}
     for b in batch:
@@ -107,7 +115,7 @@ def band_fraction(batch):
             u0, u1 = np.log(b.s_min), np.log(b.s_max)
             r = np.sqrt(np.exp(0.5 * (u1 + u0) + 0.5 * (u1 - u0) * t))
             dist[key] = np.sort(np.abs(r[:, None] - r[None, :]).ravel())
-        kept += float(np.searchsorted(dist[key], np.sqrt(70.0) * b.omega, side="left"))
+        kept += float(np.searchsorted(dist[key], np.sqrt(x) * b.omega, side="left"))
         dense += float(b.n_p) ** 2
     return kept / dense
 
@@ -990,14 +998,20 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 def gpu_rule(w):
     """The library's quadrature inputs for a finite-mu workload (internal weights, cosine nodes and
-    weights), formed on the package side."""
+    weights), formed on the package side; Matsubara weights when the workload has a temperature."""
     from paper_2012_03667_gb300 import mu_rule as MR
+    if w.T > 0:
+        return (MR.matsubara_weights(w.q_abs, w.q4, w.T, w.lo, w.hi), w.z,
+                MR.angular_weights(w.z))
     return MR.measure_weights(w.q_abs, w.q4, w.lo, w.hi), w.z, MR.angular_weights(w.z)
 
 
 def oracle_rule(w):
     """The finite-mu oracle's own weights for the same nodes."""
     from oracle import oracle_mu as OM
+    if w.T > 0:
+        return (OM.matsubara_measure(w.q_abs, w.q4, w.T, w.lo, w.hi), w.z,
+                OM.angular_weights(w.z))
     return OM.measure(w.q_abs, w.q4, w.lo, w.hi), w.z, OM.angular_weights(w.z)
 
 
@@ -1234,10 +1248,142 @@ def run_mu_solve(args):
     print(json.dumps(line))
 
 
+TEMPERATURES = (0.05, 0.1, 0.15, 0.2, 0.25, 0.3)  # GeV
+TEMP_Q4_TOP = 20.0  # GeV: the Matsubara sum runs to the first frequency at or above this
+
+
+def temperature_workloads():
+    """The finite-temperature scan: one Matsubara grid per temperature (|q| 128 log-mapped GL on
+    [1e-2, 1e2] GeV, the fermion frequencies up to about 20 GeV, 64 angles) and the same 16
+    chemical potentials mu ~ U[0, 0.3] GeV at every temperature; paper's interaction."""
+    from paper_2012_03667_gb300 import inputs
+    out = []
+    for T in TEMPERATURES:
+        n4 = max(8, int(np.ceil((TEMP_Q4_TOP / (np.pi * T) + 1.0) / 2.0)))
+        out.append(inputs.matsubara_workload(T, n_r=128, n_4=n4, n_z=64, n_mu=16))
+    return out
+
+
+def temperature_cpu_baseline(ws, sweeps_per_solve, seconds):
+    """The oracle on a bounded sample (mu_cpu_baseline on the lowest temperature's grid, its
+    largest), extrapolated to (T, mu) solves per second: the oracle's (pair, mu) rate over the
+    pairs of a sweep (every external x every internal point: the oracle keeps no windows) times
+    the GPU solve's mean sweeps per converged solve."""
+    cb = mu_cpu_baseline(ws[0], seconds)
+    pairs = np.mean([len(w.p_abs) * len(w.q_abs) * len(w.q4) for w in ws])
+    solves = cb["value"] / (pairs * max(sweeps_per_solve, 1.0))
+    return {"value": solves, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
+            "sample": cb["sample"] + "; extrapolated to whole solves with the GPU's mean sweeps "
+                      "per converged solve and the mean pairs per sweep over the temperatures",
+            "extrapolation": True, "pair_mu_evals_per_s": cb["value"]}
+
+
+def run_temperature(args):
+    """One step = the finite-temperature Ball-Chiu solve (readings T1, T2) for 16 chemical
+    potentials at each of 6 temperatures from A = C = 1, B = 0.3: per temperature, FP32 sweeps to a
+    change of 1e-5, then FP64 sweeps to 1e-10, reading M8 (eta = --mu-ray-eta), up to --mu-rounds
+    continuation rounds in mu of at most --temp-max-sweeps sweeps each.  Moment tables are built
+    once per temperature, outside the timed region.  Value: converged (T, mu) solves per second.
+    With --impl reference: the oracle's extrapolated rate (rank 0 only).  Single GPU; other ranks
+    idle."""
+    rank = int(os.environ.get("RANK", "0"))
+    ws = temperature_workloads()
+    name = ("finite temperature: T in {0.05, ..., 0.3} GeV x 16 mu ~ U[0, 0.3] GeV; |p| 128 "
+            "(staggered) x positive Matsubara frequencies external, |q| 128 x +-(2n+1) pi T up "
+            "to 20 GeV internal, 64 angles; D = 0.55, omega = 0.678, m = 0.005, BC vertex")
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = temperature_cpu_baseline(ws, 200.0, args.cpu_seconds)
+        cb["sample"] += " (no GPU run in this arm: 200 sweeps per solve assumed)"
+        v = cb["value"]
+        print(json.dumps({
+            "metric": "finite-temperature solves per second (BC vertex, 1e-10)", "value": v,
+            "unit": "solves/s", "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": name}, "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_03667_gb300 import qdse_mu as QM
+    dev = torch.device("cuda", local)
+    grids, starts, Fs = [], [], []
+    for w in ws:
+        pa, p4a = np.unique(w.p_abs), np.unique(w.p4)
+        g32 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, 3, product=True)
+        g64 = QM.MuGrid(pa, p4a, w.q_abs, w.q4, *gpu_rule(w), w.omega, 0, product=True)
+        g32.set_ray_quotient(args.mu_ray_eta)
+        g64.set_ray_quotient(args.mu_ray_eta)
+        grids.append((g32, g64))
+        st = np.zeros((len(w.mu), 3, g32.n_ext), dtype=np.complex128)
+        st[:, 0] = st[:, 1] = 1.0
+        st[:, 2] = 0.3
+        starts.append(torch.from_numpy(st).to(dev))
+        Fs.append(torch.empty_like(starts[-1]))
+    stream = torch.cuda.current_stream()
+    res = [{} for _ in ws]
+
+    def step():
+        for k, w in enumerate(ws):
+            Fs[k].copy_(starts[k])
+            g32, g64 = grids[k]
+            r = res[k]
+            r["iters"], r["status"], r["rounds"] = g32.solve_continued(
+                list(w.mu), w.D, w.m, Fs[k], max_rounds=args.mu_rounds, tol=1e-10,
+                max_iter=args.temp_max_sweeps, vertex=0, refine=g64, switch_tol=1e-5)
+
+    for _ in range(args.warmup):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = sum(int((r["status"] == 0).sum()) for r in res)
+    if rank != 0:
+        return
+    per_T = []
+    for w, r, F in zip(ws, res, Fs):
+        M0 = (F[:, 2, 0] / F[:, 0, 0]).real.cpu().numpy()
+        per_T.append({"T": w.T, "n_frequencies": len(w.q4) // 2,
+                      "converged": int((r["status"] == 0).sum()),
+                      "mu": [round(float(x), 5) for x in w.mu],
+                      "M0": [round(float(x), 5) for x in M0],
+                      "status": [int(x) for x in r["status"]],
+                      "sweeps": [int(x) for x in r["iters"]]})
+    conv_sweeps = [s for r in res for s, st in zip(r["iters"], r["status"]) if st == 0]
+    line = {"metric": "finite-temperature solves per second (BC vertex, 1e-10, FP32 sweeps + FP64 "
+                      "refinement, continuation in mu)",
+            "value": ok * args.steps / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": name, "max_sweeps_per_round": args.temp_max_sweeps,
+                       "ray_eta": args.mu_ray_eta, "rounds": args.mu_rounds},
+            "converged": ok, "of": sum(len(w.mu) for w in ws), "per_temperature": per_T,
+            "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = temperature_cpu_baseline(
+            ws, float(np.mean(conv_sweeps)) if conv_sweeps else 200.0, args.cpu_seconds)
+    print(json.dumps(line))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.workload == "table1":
         run_table1(a)
+    elif a.workload == "temperature":
+        run_temperature(a)
     elif a.impl == "reference" and a.workload == "mu":
         run_mu_reference(a)
     elif a.impl == "reference":

@@ -19,6 +19,11 @@
  * One sweep maps the values at the external points and at the internal (quadrature) points to new
  * values at the external points.
  *
+ * Finite temperature T (also named in Sec. V, without equations) uses the same calls: the internal
+ * q_4 are the fermion Matsubara frequencies +-(2n + 1) pi T, the external p_4 axis is the positive
+ * ones, and each frequency's weight in w_q carries 2 pi T in place of dq_4 (int dq_4/(2 pi) ->
+ * T sum_n); mu then enters as p_4 -> (2n + 1) pi T + i mu.
+ *
  * Conventions: as in qdse.h (GeV units; "device" pointers are device memory of the current CUDA
  * device, "host" pointers ordinary host memory; the caller owns every array passed in; work is
  * enqueued on the given stream, NULL = legacy default stream; the return value reports argument
