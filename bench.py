@@ -372,7 +372,12 @@ def run_ours(args):
         hbm, kind = peaks()
         sweep_ms, sweep_n = prof["sweep"]["ms"], prof["sweep"]["launches"]
         achieved = work["sweep_bytes"] / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
-        ratio = traffic_ratio()
+        # the FP32 sweep of a ring shape is k_tick_ring plus k_tick_narrow (the row groups of at
+        # most 32 columns); the captured DRAM/algorithmic ratio is the ring kernel's alone, so it
+        # stands for the sweep only when the narrow list is off
+        narrow = (str(tune.get("chosen", "ring")).startswith("ring") if isinstance(tune, dict)
+                  else True) and os.environ.get("QDSE_NARROW", "1") != "0"
+        ratio = None if narrow else traffic_ratio()
         traffic = ratio * work["sweep_bytes"] / max(sweep_n, 1) if ratio else None
         shares = {k: v["ms"] for k, v in prof.items()}
         tot = sum(shares.values()) or 1.0
@@ -407,10 +412,14 @@ def run_ours(args):
                     "steps": e2e_steps, "same_result_as_device_path": same_as_device},
             "gpu_launches": launches, "accuracy": gate, "fp64_arms": arms,
             "sweep_kernel": tune,
-            "roofline": {"kernel": "k_tick_ring (batched FP32 sweep)", "bound": "hbm",
+            "roofline": {"kernel": ("k_tick_ring + k_tick_narrow (batched FP32 sweep)" if narrow
+                                    else "k_tick_ring (batched FP32 sweep)"), "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                          "traffic_unit": "bytes per launch (ncu ratio x algorithmic bytes)",
+                         "traffic_note": ("null: no ncu capture covers k_tick_narrow; the ring "
+                                          "kernel's own ratio is in profiles/"
+                                          "k_tick_ring_scan256.md") if narrow else None,
                          "peak_kind": kind, "launches": sweep_n,
                          "avg_launch_ms": sweep_ms / max(sweep_n, 1),
                          "alg_bytes_per_launch": work["sweep_bytes"] / max(sweep_n, 1),

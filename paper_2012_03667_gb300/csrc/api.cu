@@ -116,7 +116,8 @@ void free_ctx(qdse_ctx* c) {
                     c->grid.groups, c->grid.nnz, c->grid.gdesc, c->grid.gphase, c->work.ilist,
                     c->work.glist, c->work.lcount, c->d_tiles, c->d_rel, c->grid.ktd,
                     c->grid.W32, c->grid.wt32, c->grid.stc32, c->grid.expt, c->work.hring, c->work.ticket, c->work.col,
-                    c->work.slist, c->grid.slabs, c->work.sphase, c->work.claim};
+                    c->work.slist, c->grid.slabs, c->work.sphase, c->work.claim,
+                    c->work.nlist, c->grid.nfirst};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -184,6 +185,15 @@ qdse_status ensure_kernels(qdse_ctx* c, const qdse_params* p, bool rebuild) {
     return QDSE_OK;
 }
 
+// The narrow list applies to the ring sweep's separate-update form with the Ball-Chiu vertex
+// (the only path whose narrow tiles k_tick_narrow reproduces); the slab, register-only, fused and
+// tensor-core paths keep every row group on the group list.
+bool narrow_split(const qdse_ctx* c) {
+    return c->narrow_ok && c->sweep_kind == 1 && !c->fused_update && !c->tc &&
+           c->opt.vertex == QDSE_VERTEX_BC &&
+           (c->opt.precision == QDSE_MIXED || c->opt.precision == QDSE_FP32);
+}
+
 Ctl make_ctl(const qdse_ctx* c) {
     Ctl t{};
     t.kappa = c->opt.cf / (8.0 * kPi * kPi * kPi);
@@ -203,6 +213,7 @@ Ctl make_ctl(const qdse_ctx* c) {
     t.stop_cycles = c->opt.stop_cycles;
     t.tc_picard = c->tc;
     t.slab_lists = c->sweep_kind == 2;
+    t.narrow_split = narrow_split(c) ? 1 : 0;
     return t;
 }
 
@@ -238,6 +249,7 @@ cudaError_t launch_one_tick(qdse_ctx* c, double* A, double* B, bool last) {
         // the ring sweep advances every instance itself once its last row group is swept
         e = launch_tick_ring(c, A, B);
         if (e != cudaSuccess || c->fused_update) return e;
+        if (narrow_split(c)) e = launch_tick_narrow(c);
     } else {
         e = launch_tick(c, A, B);
     }
@@ -301,7 +313,9 @@ qdse_status run_ticks(qdse_ctx* c, double* A, double* B, long long n_ticks, bool
         QCHECK(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "order the solve stream");
         c->stream = c->gstream;
     }
-    const int path = (c->opt.precision == QDSE_FP64) ? -2 : 4 * c->sweep_kind + c->ring_shape;
+    const int path = (c->opt.precision == QDSE_FP64)
+                         ? -2
+                         : 4 * c->sweep_kind + c->ring_shape + (narrow_split(c) ? 16 : 0);
     int chunk = 4;
     qdse_status st = QDSE_OK;
     while (true) {
@@ -529,6 +543,7 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     CALLOC(c->grid.row_inst, N);
     CALLOC(c->grid.band, N);
     CALLOC(c->grid.nnz, n_inst);
+    CALLOC(c->grid.nfirst, n_inst);
     std::vector<float2> expt;
     exp_tables(expt);
     CALLOC(c->grid.expt, expt.size());
@@ -539,7 +554,8 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
     }
     CALLOC(c->work.ilist, 3 * (size_t)n_inst);
     CALLOC(c->work.glist, 3 * (size_t)ng);
-    CALLOC(c->work.lcount, 9);
+    CALLOC(c->work.nlist, 3 * (size_t)ng);
+    CALLOC(c->work.lcount, 12);
     c->n_slabs = (int)slabs.size();
     c->work.n_slabs = c->n_slabs;
     CALLOC(c->work.slist, 3 * (size_t)c->n_slabs);
@@ -649,6 +665,9 @@ qdse_status create_impl(const qdse_grid* g, int n_inst, bool ragged, const qdse_
         c->ring_shape = (rs && std::string(rs) == "8x3") ? 1 : (rs && std::string(rs) == "6x4") ? 2 : 0;
         const char* fu = std::getenv("QDSE_FUSED_UPDATE");
         c->fused_update = (fu && std::string(fu) == "1") ? 1 : 0;
+        // QDSE_NARROW=0: the ring sweep takes the narrow row groups too (bitwise the same results)
+        const char* nw = std::getenv("QDSE_NARROW");
+        c->narrow_ok = (nw && std::string(nw) == "0") ? 0 : 1;
         // kernel matrices: double-float on the FP32 pipe by default; QDSE_PRECOMPUTE=fp64
         // selects the FP64 kernel (the same entries to about 1e-14)
         const char* pk = std::getenv("QDSE_PRECOMPUTE");

@@ -715,6 +715,8 @@ __global__ void k_group_bands(const DevInst* __restrict__ inst, Grid g, int ngro
     const int lg = d.i0 / kRows;  // the group's index in its instance
     const int s_off = inst[d.b].s_off;
     g.slabs[s_off + lg / kSlabGroups].band[lg % kSlabGroups] = make_int2(lo, hi);
+    // the narrow tail: every full group after the last full group wider than kNarrowCols
+    if (d.nr == kRows && hi - lo > kNarrowCols) atomicMax(g.nfirst + d.b, lg + 1);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -889,8 +891,18 @@ __global__ void k_init_state(const DevInst* __restrict__ inst, DevState* state,
         w.ilist[atomicAdd(w.lcount + 0, 1)] = b;
         if (!(ctl->tc_picard && phase0 == PH_PICARD32)) {  // else the tensor-core sweep has it
             const int ng = (I.n + kRows - 1) / kRows;
-            const int gb = atomicAdd(w.lcount + 3, ng);
-            for (int t = 0; t < ng; ++t) w.glist[gb + t] = I.g_off + t;
+            int n0 = ng, n1 = ng;  // row groups [n0, n1) go on the narrow list
+            if (ctl->narrow_split && phase0 == PH_PICARD32) {
+                n1 = I.n / kRows;
+                n0 = min(g.nfirst[b], n1);
+            }
+            const int nn = n1 - n0;
+            const int gb = atomicAdd(w.lcount + 3, ng - nn);
+            const int nb = nn > 0 ? atomicAdd(w.lcount + 9, nn) : 0;
+            for (int t = 0; t < ng; ++t) {
+                if (t >= n0 && t < n1) w.nlist[nb + t - n0] = I.g_off + t;
+                else w.glist[gb + (t < n0 ? t : t - nn)] = I.g_off + t;
+            }
             if (ctl->slab_lists) {
                 const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
                 const int sb = atomicAdd(w.lcount + 6, ns);
@@ -1361,14 +1373,25 @@ __device__ void update_instance(const Team& T, int b, const DevInst* __restrict_
         // to the tensor-core sweep instead)
         const int ng = (I.n + kRows - 1) / kRows;
         const int ns = (ng + kSlabGroups - 1) / kSlabGroups;
-        int gb = 0, sb = 0;
+        int n0 = ng, n1 = ng;  // row groups [n0, n1) go on the narrow list
+        if (C.narrow_split && next == PH_PICARD32) {
+            n1 = I.n / kRows;
+            n0 = min(g.nfirst[b], n1);
+        }
+        const int nn = n1 - n0;
+        int gb = 0, sb = 0;  // sb: the slab lists' base, or the narrow list's (never both)
         if (T.leader()) {  // both reservations in flight at once
-            gb = atomicAdd(w.lcount + 3 + next_list, ng);
+            gb = atomicAdd(w.lcount + 3 + next_list, ng - nn);
             if (C.slab_lists) sb = atomicAdd(w.lcount + 6 + next_list, ns);
+            else if (nn > 0) sb = atomicAdd(w.lcount + 9 + next_list, nn);
         }
         T.bcast2(gb, sb);
-        for (int t = T.tid(); t < ng; t += T.size())
-            w.glist[(size_t)next_list * w.n_groups + gb + t] = I.g_off + t;
+        for (int t = T.tid(); t < ng; t += T.size()) {
+            if (t >= n0 && t < n1)
+                w.nlist[(size_t)next_list * w.n_groups + sb + t - n0] = I.g_off + t;
+            else
+                w.glist[(size_t)next_list * w.n_groups + gb + (t < n0 ? t : t - nn)] = I.g_off + t;
+        }
         if (C.slab_lists)
             for (int t = T.tid(); t < ns; t += T.size())
                 w.slist[(size_t)next_list * w.n_slabs + sb + t] = I.s_off + t;
@@ -1662,6 +1685,7 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         w.lcount[clr] = 0;
         w.lcount[3 + clr] = 0;
         w.lcount[6 + clr] = 0;
+        w.lcount[9 + clr] = 0;
     }
     __syncthreads();
     const int nact = w.lcount[3 + list];
@@ -1926,6 +1950,87 @@ __global__ void __launch_bounds__(Cfg::kWarps * 32, 1)
         if (lane == 0) atomicExch(err, 1);
         for (unsigned u = consumed; u < issued; ++u)
             ring_wait(smem_addr(&bars[u % S]), (u / S) & 1);
+    }
+}
+
+// The row groups of the narrow list (Ctl::narrow_split): full groups of a Ball-Chiu FP32 Picard
+// sweep whose band is at most kNarrowCols columns (high momenta, where (sqrt P - sqrt Q)^2 / w^2
+// < 70 spans few nodes).  On the scan they are a third of the groups and hold 4% of the kernel
+// entries, yet in the ring sweep each pays the whole per-group machinery (descriptor and row
+// constant copies, a tile wait, the warp totals) for at most 128 pairs.  Here one warp takes four
+// of them at once, eight lanes each, straight from global memory: lane cb of a group's eight
+// holds the 4-column block cb for all four rows, the same per-(row, block) partial sums as the
+// ring's narrow tile (narrow_tile32<4>), and the sums over the eight blocks run in the same tree,
+// ((0 + 4) + (2 + 6)) + ((1 + 5) + (3 + 7)), as the ring's warp totals, whose other levels only
+// add exact zeros.  So every output is bitwise the ring's.
+__global__ void __launch_bounds__(256, 2) k_tick_narrow(Grid g, Work w,
+                                                     const float* __restrict__ Khi, int ntot,
+                                                     int list, const int* err) {
+    // a bounded wait of this tick's ring sweep ran out: the solve stops
+    if (*reinterpret_cast<volatile const int*>(err)) return;
+    const int n = w.lcount[9 + list];
+    const int* ids = w.nlist + (size_t)list * w.n_groups;
+    const int lane = threadIdx.x & 31, seg = lane >> 3, cb = lane & 7;
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int k0 = 4 * wid; k0 < n; k0 += 4 * nw) {
+        const int k = k0 + seg;
+        const bool act = k < n;
+        GroupDesc d{};
+        if (act) d = g.gdesc[ids[k]];
+        const int o = d.x_off + d.i0;
+        float sA[kRows], sB[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) sA[r] = sB[r] = 0.f;
+        const int col = d.jlo + 4 * cb;
+        if (act && col < d.jhi) {
+            const float* vb = w.vec32 + vpos(d.v_off + col, 0);
+            const float4 a = ld4(vb), b = ld4(vb + 4), u1 = ld4(vb + 8), u2 = ld4(vb + 12),
+                         u3 = ld4(vb + 16);
+            const Cols4 H(u1, u2, u3);
+            const float* kc = Khi + d.kbase + (long long)(col >> 2) * (3 * kRows * 4);
+            const int sw = ((col >> 2) >> 1) & 3;  // kswz of a full group
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const float Ai = w.x32[o + r], Bi = w.x32[ntot + o + r], Pi = g.sp32[o + r];
+                const float4 K0 = ld4(kc + ((3 * r + 0) ^ sw) * 4);
+                const float4 KT = ld4(kc + ((3 * r + 1) ^ sw) * 4);
+                const float4 K3 = ld4(kc + ((3 * r + 2) ^ sw) * 4);
+                pair32(a.x, b.x, u1.x, u2.x, H.h1.x, H.h2.x, H.h3.x, K0.x, KT.x, K3.x, Ai, Bi, Pi, sA[r], sB[r]);
+                pair32(a.y, b.y, u1.y, u2.y, H.h1.y, H.h2.y, H.h3.y, K0.y, KT.y, K3.y, Ai, Bi, Pi, sA[r], sB[r]);
+                pair32(a.z, b.z, u1.z, u2.z, H.h1.z, H.h2.z, H.h3.z, K0.z, KT.z, K3.z, Ai, Bi, Pi, sA[r], sB[r]);
+                pair32(a.w, b.w, u1.w, u2.w, H.h1.w, H.h2.w, H.h3.w, K0.w, KT.w, K3.w, Ai, Bi, Pi, sA[r], sB[r]);
+            }
+        }
+        // totals over the group's eight lanes (shuffles stay inside each 8-lane segment)
+#pragma unroll
+        for (int m = 4; m >= 1; m >>= 1) {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                sA[r] += __shfl_xor_sync(0xffffffffu, sA[r], m);
+                sB[r] += __shfl_xor_sync(0xffffffffu, sB[r], m);
+            }
+        }
+        if (act) {
+            // lane cb stores value cb: A of row cb (cb < 4), else B of row cb - 4
+            const int rr = cb & (kRows - 1);
+            const bool isB = cb >= kRows;
+            float tot = 0.f;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r)
+                if (r == rr) tot = isB ? sB[r] : sA[r];
+            const float Pl = g.sp32[o + rr];
+            if (d.mode == QDSE_COLLOCATED) {
+                // removable limit q^2 -> p^2 of row i0 + rr, as in the ring sweep
+                const float KTd = g.ktd[o + rr], qA = w.dia32[o + rr], qB = w.dia32[ntot + o + rr];
+                const float x1 = w.vec32[vpos(d.v_off + d.i0 + rr, 2)];
+                const float x2 = w.vec32[vpos(d.v_off + d.i0 + rr, 3)];
+                tot += isB ? (x1 * qA - x2 * qB) * KTd : (-x1 * qB - Pl * x2 * qA) * KTd;
+            }
+            const float sc = d.sc32;
+            if (!isB) w.xn32[o + rr] = 1.f + __fdividef(sc * tot, Pl);
+            else w.xn32[ntot + o + rr] = d.m32 + sc * tot;
+        }
     }
 }
 
@@ -2253,6 +2358,7 @@ __global__ void __launch_bounds__(kUpdThreads, 6) k_update(const DevInst* __rest
         w.lcount[clr] = 0;
         w.lcount[3 + clr] = 0;
         w.lcount[6 + clr] = 0;
+        w.lcount[9 + clr] = 0;
     }
     __shared__ double sh[32];
     __shared__ float snew[2 * kMaxN];
@@ -2373,7 +2479,7 @@ static inline int row_blocks(int ntot) { return (ntot + 7) / 8; }
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0) {
     cudaError_t e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c->work.lcount, 0, 9 * sizeof(int), c->stream);
+    e = cudaMemsetAsync(c->work.lcount, 0, 12 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->work.claim, 0, 3 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
@@ -2387,6 +2493,8 @@ cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B,
 }
 
 cudaError_t launch_group_bands(qdse_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->grid.nfirst, 0, sizeof(int) * c->n_inst, c->stream);
+    if (e != cudaSuccess) return e;
     prof_begin(c, PK_OTHER);
     k_group_bands<<<(c->n_groups + 255) / 256, 256, 0, c->stream>>>(c->d_inst, c->grid,
                                                                      c->n_groups);
@@ -2431,6 +2539,17 @@ cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B) {
     else if (c->ring_shape == 2) launch_ring_shape<RingDeeper>(c, A, B);
     else launch_ring_shape<RingSweep>(c, A, B);
     if (c->fused_update) c->tick++;  // otherwise launch_update advances the tick
+    c->launches++;
+    prof_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick_narrow(qdse_ctx* c) {
+    prof_begin(c, PK_SWEEP);
+    const int sms = c->n_sms > 0 ? c->n_sms : 152;
+    const int blocks = std::max(1, std::min((c->n_groups + 31) / 32, 8 * sms));
+    k_tick_narrow<<<blocks, 256, 0, c->stream>>>(c->grid, c->work, c->d_Khi, c->n_total,
+                                                 (int)(c->tick % 3), c->d_err);
     c->launches++;
     prof_end(c);
     return cudaGetLastError();

@@ -114,6 +114,9 @@ struct Ctl {              // solver controls shared by every instance of a call
     int slab_lists;       // 1: keep the slab lists and slab phases (the slab sweep reads them)
     int tc_picard;        // 1: FP32 Picard rows are swept by the tensor-core product (k_tc.cu),
                           // so instances in that phase put no row groups on the active lists
+    int narrow_split;     // 1: full row groups of a Ball-Chiu FP32 Picard sweep whose band is at
+                          // most kNarrowCols columns go on the narrow list (k_tick_narrow), the
+                          // others on the group list (the ring sweep)
 };
 
 // Work arrays (device).  Component counts in brackets, each of length n_total.
@@ -139,10 +142,11 @@ struct Work {
     double* lamn;   // [2] adjoint sweep output
     // active lists: instances, row groups and slabs still running, three buffers (tick t reads
     // list t % 3, appends the survivors to (t + 1) % 3 and empties (t + 2) % 3);
-    // lcount = {instances[0..2], groups[0..2], slabs[0..2]}
+    // lcount = {instances[0..2], groups[0..2], slabs[0..2], narrow groups[0..2]}
     int* ilist;     // [3][n_inst]
     int* glist;     // [3][n_groups]
-    int* lcount;    // [9]: instances, groups, slabs (three buffers each)
+    int* lcount;    // [12]: instances, groups, slabs, narrow groups (three buffers each)
+    int* nlist;     // [3][n_groups] narrow row groups (Ctl::narrow_split)
     int* slist;     // [3][n_slabs] active slabs (same three-buffer scheme)
     int* sphase;    // [n_slabs] the phase of the slab's instance for the coming sweep
     int* claim;     // [3] slab claims of the tick that reads list t % 3 (the slab sweep)
@@ -182,6 +186,8 @@ struct Grid {              // FP64 grid arrays on the device (global point index
     int* gphase;           // per group: the phase of its instance for the coming sweep
     unsigned long long* nnz;  // per instance: sum over rows of the band widths (kernel entries a
                               // sweep must read per plane)
+    int* nfirst;           // per instance: the first row group from which every full group up to
+                           // the last full one is narrow (band of at most kNarrowCols columns)
     float* ktd;            // per external point: K_T at q = p (collocated grids; the entry the
                            // removable-limit term multiplies), 0 on staggered grids
     struct SlabRec* slabs; // per slab: the slab sweep's record (bands refreshed with the kernels)
@@ -193,6 +199,7 @@ constexpr int kTuneCandidates = 5;  // qdse_autotune: ring 12x2, 8x3, 6x4, slab,
 constexpr int kRows = 4;   // external points per warp in the batched sweeps (1, 2 or 4)
 constexpr int kTickBlocksPerSM = kRows >= 4 ? 2 : 3;  // resident 256-thread sweep blocks per SM
 constexpr int kTile = 32;  // kernel precompute tile edge
+constexpr int kNarrowCols = 32;  // narrow row group: a band of at most this many columns
 // Kernel pool layout.  The entries K_p(i, j) (plane p = 0, 1, 2 for K_0, K_T/(Q - P), K_3) of one
 // instance fill n * 3 * ld floats from k_off.  Rows come in groups of kRows (the last group may be
 // shorter, nr rows); a group's block starts at k_off + 3 i0 ld, and each 4-column block q of it
@@ -326,6 +333,7 @@ struct qdse_ctx {
     float* tc_G = nullptr;    // [11 tc_bp][tc_ldg] far-field products
     int* tc_any = nullptr;    // [tc_bp / 128] blocks of instances with one in the Picard phase
     alignas(64) unsigned char tc_map[2][128];  // tensor maps: column functions, kernel planes
+    int narrow_ok = 1;        // the narrow list may be used (QDSE_NARROW=0 at creation turns it off)
     int fused_update = 0;     // ring sweep: 1 advances each instance inside the sweep launch (one
                               // launch per tick), 0 in a separate k_update launch (the default)
     int4* d_tiles = nullptr;  // precompute tiles (instance, tile row, tile column)
@@ -376,6 +384,7 @@ void exp_tables(std::vector<float2>& out);
 cudaError_t launch_init_state(qdse_ctx* c, const Ctl& ctl, double* A, double* B, int phase0);
 cudaError_t launch_tick(qdse_ctx* c, double* A, double* B);
 cudaError_t launch_tick_ring(qdse_ctx* c, double* A, double* B);
+cudaError_t launch_tick_narrow(qdse_ctx* c);
 cudaError_t launch_tick_slab(qdse_ctx* c, double* A, double* B);
 cudaError_t configure_tick_slab();
 cudaError_t configure_tick_ring();

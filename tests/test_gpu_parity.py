@@ -134,6 +134,19 @@ def test_fp32_sweep_kernels_track_oracle_on_ragged_batch(kind, monkeypatch):
         assert rel(Ah[sl], Ao) < 2e-5 and rel(Bh[sl], Bo) < 2e-5, (kind, b)
 
 
+def test_narrow_group_sweep_is_bitwise_the_ring_on_a_ragged_batch(monkeypatch):
+    """The narrow-group kernel on the ragged batch (last groups of 1, 2 and 4 rows, odd sizes,
+    bands from a few columns up): three FP32 sweeps bitwise equal to the ring sweep alone."""
+    out = []
+    for narrow in ("0", "1"):
+        monkeypatch.setenv("QDSE_NARROW", narrow)
+        ctx = Q.Context([grid(i) for i in RAGGED32], precision=Q.QDSE_FP32)
+        A = dev(np.ones(ctx.n_total)); B = dev(np.full(ctx.n_total, 0.3))
+        ctx.qdse_iterate([[i.D, i.omega, i.m, 0.0] for i in RAGGED32], A, B, 3)
+        out.append((host(A), host(B)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_jvp_matches_complex_step_jacobian():
     inst = TINY
     rng = np.random.default_rng(9)

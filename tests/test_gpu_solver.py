@@ -211,3 +211,19 @@ def test_autotune_keeps_a_kernel_with_bitwise_the_same_solves():
     assert np.array_equal(got[2], s0) and np.array_equal(got[3], i0)
     assert np.array_equal(got[0], A, equal_nan=True) and np.array_equal(got[1], B, equal_nan=True)
 
+
+def test_narrow_group_sweep_gives_bitwise_the_ring_results(monkeypatch):
+    """Row groups whose band is at most 32 columns go to their own kernel (four groups per warp,
+    eight lanes each) instead of the ring sweep; against the ring alone (QDSE_NARROW=0) the mixed
+    solve of 256 scan instances to a cap of 400 sweeps ends bitwise the same: A, B, statuses,
+    sweep counts and per-instance records."""
+    batch = inputs.scan_batch(256)
+    monkeypatch.setenv("QDSE_NARROW", "0")
+    ref = _solve_scan(batch, 1, max_iter=400)
+    monkeypatch.delenv("QDSE_NARROW", raising=False)
+    got = _solve_scan(batch, 1, max_iter=400)
+    for a, b in zip(ref[:4], got[:4]):
+        assert np.array_equal(a, b)
+    for k in ("fp32_sweeps", "fp64_sweeps", "longest_stall", "phase"):
+        assert np.array_equal(ref[4][k], got[4][k]), k
+
