@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scan",
                     choices=["scan", "large", "small", "adjoint", "mu", "mu-small", "mu-solve",
-                             "table1", "mscan", "temperature"],
+                             "table1", "mscan", "temperature", "sweep-rate"],
                     help="scan: 4096-instance mass/interaction scan (default); large/small: one "
                          "N = 512 / N = 64 instance; adjoint: 1024 scan instances at N_q = 256, "
                          "N_theta = 64, forward solve + condensate gradient by the adjoint; mu: "
@@ -47,7 +47,8 @@ def parse():
                          "1024-instance current-mass scan on one shared kernel matrix, solved "
                          "with the tensor-core Picard sweep and with the per-instance sweep; "
                          "temperature: finite-temperature solve of 16 mu at each of 6 "
-                         "temperatures on Matsubara grids")
+                         "temperatures on Matsubara grids; sweep-rate: FP32 sweeps of the whole "
+                         "scan with every instance active")
     ap.add_argument("--n-inst", type=int, default=4096)
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--fp64", default="sample", choices=["sample", "full", "none"],
@@ -77,6 +78,8 @@ def parse():
                          "mu-solve; 0 = the exact quotient")
     ap.add_argument("--mu-max-sweeps", type=int, default=1000,
                     help="sweep cap per round of --workload mu-solve")
+    ap.add_argument("--sweeps", type=int, default=20,
+                    help="FP32 sweeps per step of --workload sweep-rate")
     ap.add_argument("--temp-max-sweeps", type=int, default=400,
                     help="sweep cap per round of --workload temperature")
     ap.add_argument("--mu-rounds", type=int, default=4,
@@ -87,7 +90,7 @@ def parse():
 # ------------------------------------------------------------------------------------------------
 def workload(args, rank=0):
     from paper_2012_03667_gb300 import inputs
-    if args.workload == "scan":
+    if args.workload in ("scan", "sweep-rate"):
         batch = inputs.scan_batch(args.n_inst, seed=inputs.SCAN_SEED + rank)
         name = (f"batched mass/interaction scan, {args.n_inst} instances, N_q in "
                 "{128,256,384,512}, N_theta in {32,64,128}, BC vertex")
@@ -1257,6 +1260,83 @@ def run_mu_solve(args):
     print(json.dumps(line))
 
 
+def run_sweep_rate(args):
+    """One step = --sweeps FP32 Picard sweeps of the whole 4096-instance scan with every instance
+    active (qdse_iterate on an FP32 context from A = 1, B = 0.3, the kernel precompute of the call
+    included): the first half of the headline
+    metric, BC-kernel evaluations per second of sweep, and the FP32 sweep's roofline with no
+    thin late ticks (algorithmic bytes from the library's counters over the summed CUDA-event time
+    of the sweep launches, ring and narrow-group kernels).  QDSE_NARROW=0 times the ring alone.
+    Single GPU; other ranks idle."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_03667_gb300 import qdse as Q
+    batch, name = workload(args, rank)
+    ctx = Q.Context([Q.Grid(b.n_p, b.n_theta, b.s_min, b.s_max) for b in batch],
+                    precision=Q.QDSE_FP32)
+    prm = [[b.D, b.omega, b.m, 0.0] for b in batch]
+    dev = torch.device("cuda", local)
+    A = torch.ones(ctx.n_total, dtype=torch.float64, device=dev)
+    B = torch.full((ctx.n_total,), 0.3, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        A.fill_(1.0)
+        B.fill_(0.3)
+        ctx.qdse_iterate(prm, A, B, args.sweeps)
+    torch.cuda.synchronize()
+    ctx.qdse_profile()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evals = 0.0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.qdse_iterate(prm, A, B, args.sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    work = ctx.qdse_last_work()  # the last step's sweeps
+    stats = ctx.qdse_last_stats()
+    # kernel time of the same sweeps, from a separate profiled step
+    ctx.qdse_set_profiling(True)
+    ctx.qdse_iterate(prm, A, B, args.sweeps)
+    torch.cuda.synchronize()
+    prof = ctx.qdse_profile()
+    ctx.qdse_set_profiling(False)
+    if rank != 0:
+        return
+    hbm, kind = peaks()
+    sweep_ms = prof["sweep"]["ms"]
+    achieved = work["sweep_bytes"] / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+    narrow = os.environ.get("QDSE_NARROW", "1") != "0"
+    evals = work["kernel_evals"] * args.steps
+    line = {"metric": "BC-kernel evals/s per sweep (FP32 Picard, every instance active)",
+            "value": evals / (ms / 1e3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name + f"; {args.sweeps} FP32 sweeps per step, every "
+                                          "instance active (qdse_iterate)",
+                       "l2": "inputs larger than L2: the kernel pool is re-read each sweep"},
+            "fp32_instance_sweeps_per_step": stats["fp32_sweeps"],
+            "value_sweep_only": (work["kernel_evals"] / (sweep_ms / 1e3)) if sweep_ms > 0 else None,
+            "value_note": "value: evaluations over the whole step (the kernel-matrix precompute "
+                          "that each qdse_iterate call runs, the sweeps and the updates); "
+                          "value_sweep_only: over the sweep launches alone",
+            "roofline": {"kernel": ("k_tick_ring + k_tick_narrow" if narrow else "k_tick_ring"),
+                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm if achieved else None, "traffic": None,
+                         "peak_kind": kind, "sweep_bytes_per_sweep": work["sweep_bytes"] /
+                         max(args.sweeps, 1), "sweep_ms_per_sweep": sweep_ms / max(args.sweeps, 1),
+                         "timed_in": "a separate profiled step (CUDA events around every launch)"},
+            "gpu_launches": stats["kernel_launches"] * args.steps,
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 TEMPERATURES = (0.05, 0.1, 0.15, 0.2, 0.25, 0.3)  # GeV
 TEMP_Q4_TOP = 20.0  # GeV: the Matsubara sum runs to the first frequency at or above this
 
@@ -1393,6 +1473,8 @@ if __name__ == "__main__":
         run_table1(a)
     elif a.workload == "temperature":
         run_temperature(a)
+    elif a.workload == "sweep-rate":
+        run_sweep_rate(a)
     elif a.impl == "reference" and a.workload == "mu":
         run_mu_reference(a)
     elif a.impl == "reference":
