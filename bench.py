@@ -420,9 +420,9 @@ def run_ours(args):
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                          "traffic_unit": "bytes per launch (ncu ratio x algorithmic bytes)",
-                         "traffic_note": ("null: no ncu capture covers k_tick_narrow; the ring "
-                                          "kernel's own ratio is in profiles/"
-                                          "k_tick_ring_scan256.md") if narrow else None,
+                         "traffic_note": ("null: no ncu capture covers k_tick_narrow (the ring "
+                                          "kernel's captured ratio applies with QDSE_NARROW=0)")
+                                         if narrow else None,
                          "peak_kind": kind, "launches": sweep_n,
                          "avg_launch_ms": sweep_ms / max(sweep_n, 1),
                          "alg_bytes_per_launch": work["sweep_bytes"] / max(sweep_n, 1),
