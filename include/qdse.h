@@ -136,9 +136,12 @@ qdse_options qdse_default_options(void);
  * nodes on the host in FP64, uploads them and allocates the kernel-matrix pool (6 n_p^2 floats
  * per instance) and workspaces on the current device.  *out receives the context (NULL on
  * failure).  Errors: QDSE_ERR_ARG (bad sizes/options), QDSE_ERR_OOM, QDSE_ERR_CUDA.
- * The FP32 sweeps of the batched solve use the shared-memory ring kernel, followed in every tick by
- * a launch that advances each instance (relaxed step, convergence test, next node vectors).
+ * The FP32 sweeps of the batched solve use the shared-memory ring kernel, with the row groups whose
+ * band is at most 32 columns (Ball-Chiu vertex, FP32 Picard phase) swept by a second kernel four to
+ * a warp, followed in every tick by a launch that advances each instance (relaxed step,
+ * convergence test, next node vectors).
  * Environment variables read here select alternatives that compute the same quantities:
+ * QDSE_NARROW=0 every row group in the ring kernel (bitwise the same results),
  * QDSE_SWEEP=groups the register-only sweep kernel (the same sums in another order),
  * QDSE_SWEEP=slab the ring sweep with its bookkeeping per slab of 8 row groups (bitwise the same
  * results), QDSE_RING=8x3 or 6x4 ring shapes with fewer warps and more tile slots each (bitwise
