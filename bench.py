@@ -1267,15 +1267,38 @@ def run_sweep_rate(args):
     metric, BC-kernel evaluations per second of sweep, and the FP32 sweep's roofline with no
     thin late ticks (algorithmic bytes from the library's counters over the summed CUDA-event time
     of the sweep launches, ring and narrow-group kernels).  QDSE_NARROW=0 times the ring alone.
-    Single GPU; other ranks idle."""
-    import torch
+    Single GPU; other ranks idle.  With --impl reference: the FP64 oracle's BC-kernel evaluations
+    per second of its sweeps on the host cores, one instance per (N_q, N_theta) pair of the scan
+    timed and weighted by the batch's mix of pairs (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
+    batch, name = workload(args, rank)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per, cores = oracle_shape_times(batch, args.cpu_seconds)
+        evals = sum(float(b.n_p) * b.n_p * b.n_theta for b in batch)
+        secs = sum(per[(b.n_p, b.n_theta)] for b in batch)
+        v = evals / secs
+        print(json.dumps({
+            "metric": "BC-kernel evals/s per sweep (FP32 Picard, every instance active)",
+            "value": v, "unit": "evals/s", "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": name + "; one sweep of every instance, sampled"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": "FP64 oracle sweeps of one instance per (N_q, N_theta) "
+                                       "pair, weighted by the batch's mix of pairs",
+                             "seconds_per_sweep": {f"{k[0]}x{k[1]}": t for k, t in
+                                                   sorted(per.items())}},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+    import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2012_03667_gb300 import qdse as Q
-    batch, name = workload(args, rank)
     ctx = Q.Context([Q.Grid(b.n_p, b.n_theta, b.s_min, b.s_max) for b in batch],
                     precision=Q.QDSE_FP32)
     prm = [[b.D, b.omega, b.m, 0.0] for b in batch]

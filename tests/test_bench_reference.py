@@ -51,3 +51,14 @@ def test_table_1_reference_arm_reproduces_the_papers_structure():
     assert t["2"] < t["1"] and t["4"] < t["2"]
     if d["cores"] > 1:
         assert t["3"] < t["1"]
+
+
+def test_sweep_rate_and_temperature_reference_arms():
+    """The oracle arms of the fixed-sweep rate (BC-kernel evaluations per second) and of the
+    finite-temperature scan keep the same contract, with the units of their GPU arms."""
+    d = _run("--impl", "reference", "--workload", "sweep-rate", "--cpu-seconds", "1")
+    _check_contract(d)
+    assert d["unit"] == "evals/s" and len(d["cpu_baseline"]["seconds_per_sweep"]) == 12
+    d = _run("--impl", "reference", "--workload", "temperature", "--cpu-seconds", "1")
+    _check_contract(d)
+    assert d["unit"] == "solves/s" and d["cpu_baseline"]["extrapolation"] is True
